@@ -1,0 +1,332 @@
+"""Benchmark: reciprocal evaluations per second of the tensor-core SKP path on GB300.
+
+One step = one reciprocal evaluation of the whole path (spread, SKP mode products,
+gather of potentials and forces, float64 energy and virial) for the water box
+(10^4 rigid 3-site molecules, 30,000 atoms, 67 A, B-spline order 4, K = 64).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6]
+                    [--workload water|small|mixed|large] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica on its
+own GPU (the path has no data-parallel split for one system); ``value`` is the
+evaluations of all ranks divided by the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "reciprocal evals/s + TFLOP/s at ≤1e-6 rel err: tensor-core SKP vs FP64 form"
+WORKLOAD_TEXT = {
+    "water": "water box: 10^4 rigid 3-site molecules (30,000 atoms), L=67 A, B-spline order 4, K=64, "
+             "beta=0.35/A, SKP tol 1e-8",
+    "small": "1000 charges +-1, L=20 A, order 4, K=32, beta=0.35/A, SKP tol 1e-8",
+    "mixed": "1e5 charges (+-1, +-0.5), L=100 A, order 6, K=96, beta=0.35/A, SKP tol 1e-8",
+    "large": "1e6 charges +-1, L=220 A, order 6, K=256, beta=0.35/A, SKP tol 1e-7",
+}
+DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16": "bf16", "bf16x3": "bf16",
+         "bf16x6": "bf16"}
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit())
+        mx = max((float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].strip().lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": mx, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _system(name):
+    from paper_2601_18838_gb300 import workloads
+    return getattr(workloads, name)()
+
+
+def cpu_baseline(s, budget_s: float = 20.0, max_evals: int = 5, gpu_out=None) -> dict:
+    """The float64 oracle (as it stands) on the host cores: full reciprocal evaluations of
+    the same workload, as many as fit in the budget (at least one)."""
+    from oracle import skp
+    t0 = time.perf_counter()
+    o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol)
+    t_build = time.perf_counter() - t0
+    n, t, ref = 0, 0.0, None
+    while n < max_evals and (n == 0 or t < budget_s):
+        a = time.perf_counter()
+        ref = skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+        t += time.perf_counter() - a
+        n += 1
+    res = {"value": n / t, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": f"{n} full float64 oracle evaluations (numpy) of the {s.name} workload "
+                     f"(SKP build {t_build:.1f} s not timed)"}
+    if gpu_out is not None:
+        import numpy as np
+        phi, F = gpu_out
+        res["accuracy_vs_oracle"] = {
+            "phi_rel_rms": float(np.linalg.norm(phi - ref["phi"]) / np.linalg.norm(ref["phi"])),
+            "F_rel": float(np.linalg.norm(F - ref["F"]) / np.linalg.norm(ref["F"])),
+        }
+    return res
+
+
+def run_reference(args):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    s = _system(args.workload)
+    from oracle import skp
+    o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol)
+    for _ in range(args.warmup):
+        skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+    dt = time.perf_counter() - t0
+    v = args.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD_TEXT[args.workload]},
+            "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{args.steps} full float64 oracle evaluations per timed region"},
+            "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water", choices=list(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default="bf16x6")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=5)
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if pg:
+        pg.barrier()
+    from paper_2601_18838_gb300 import Plan
+
+    s = _system(args.workload)
+    stream = torch.cuda.current_stream()
+    plan = Plan(s.box, s.K, s.order, s.beta, precision=args.precision, skp_tol=s.skp_tol, max_n=s.n)
+    R, skp_err = plan.build_skp()
+    info = plan.info()
+    x = torch.tensor(s.x, device=dev)
+    q = torch.tensor(s.q, device=dev)
+    out = {"energy": torch.empty(1, dtype=torch.float64, device=dev),
+           "forces": torch.empty((s.n, 3), dtype=torch.float64, device=dev),
+           "dEdq": torch.empty(s.n, dtype=torch.float64, device=dev),
+           "virial": torch.empty(1, dtype=torch.float64, device=dev)}
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
+
+    def step():
+        plan.energy_forces(x, q, forces=True, dEdq=True, virial=True, out=out)
+
+    def timed(nsteps, profile=False):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
+        plan.set_profiling(profile)
+        plan.get_profile(reset=True)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        for a, b in evs:
+            flush.zero_()
+            a.record(stream)
+            step()
+            b.record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        prof = plan.get_profile(reset=True)
+        plan.set_profiling(False)
+        return sum(a.elapsed_time(b) for a, b in evs), prof
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ms_total, _ = timed(args.steps)
+    clocks = clk.stop()
+    if pg:
+        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        ms_total = t.item()
+    ms_step = ms_total / args.steps
+    value = ws * args.steps / (ms_total * 1e-3)
+
+    # per-kernel timing (same steps, library events on the launching stream)
+    _, prof = timed(args.steps, profile=True)
+    K = s.K
+    useful = info["flops_useful"]
+    skp_ms = sum(prof[k][0] for k in ("skp_stage1", "skp_stage2", "skp_stage3")) / args.steps
+    skp_launches = sum(prof[k][1] for k in ("skp_stage1", "skp_stage2", "skp_stage3")) / args.steps
+    launches_per_step = sum(v[1] for v in prof.values()) / args.steps
+    peaks, peak_src = _peaks()
+    tensor = args.precision in ("bf16", "tf32", "bf16x3", "tf32x3", "bf16x6")
+    # algorithmic MMA flops of the split method per step: executed products of slices
+    mp_flops = info["flops_executed"]
+    per_launch_ms = skp_ms / max(skp_launches, 1)
+    achieved = mp_flops / (skp_ms * 1e-3) / 1e12 if skp_ms > 0 else None
+    peak = peaks.get("bf16_tflops_sustained", 1700.0)
+    if args.precision.startswith("tf32"):
+        peak = peak / 2.0   # dense tf32 rate is half the bf16 rate
+    roof = {"bound": "tensor", "kernel": "mp_tc_kernel (SKP mode products, tcgen05)",
+            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 1/2 (tf32 nominal ratio)" if args.precision.startswith("tf32") else ""),
+            "flops_per_step": mp_flops, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
+            "ms_per_launch": per_launch_ms}
+    if not tensor:
+        roof = None
+
+    # end to end through the public API with host buffers
+    xh = torch.tensor(s.x).pin_memory()
+    qh = torch.tensor(s.q).pin_memory()
+    Fh = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
+    ph = torch.empty(s.n, dtype=torch.float64).pin_memory()
+    Eh = torch.empty(2, dtype=torch.float64).pin_memory()
+    xd = torch.empty_like(x)
+    qd = torch.empty_like(q)
+
+    def e2e_step():
+        xd.copy_(xh, non_blocking=True)
+        qd.copy_(qh, non_blocking=True)
+        plan.energy_forces(xd, qd, forces=True, dEdq=True, virial=True, out=out)
+        Fh.copy_(out["forces"], non_blocking=True)
+        ph.copy_(out["dEdq"], non_blocking=True)
+        Eh[0:1].copy_(out["energy"], non_blocking=True)
+        Eh[1:2].copy_(out["virial"], non_blocking=True)
+
+    for _ in range(3):
+        e2e_step()
+    torch.cuda.synchronize()
+    e_ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        e2e_step()
+        b.record(stream)
+        b.synchronize()
+        e_ms += a.elapsed_time(b)
+    if pg:
+        t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        e_ms = t.item()
+    e2e = {"value": ws * args.steps / (e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": s.n * 32,
+           "d2h_bytes_per_step": s.n * 32 + 16}
+
+    # FP64 GPU form at the same SKP (the baseline the tensor path must beat)
+    fp64 = None
+    if args.fp64_steps > 0:
+        plan.set_precision("fp64")
+        step()
+        torch.cuda.synchronize()
+        f_ms, _ = timed(args.fp64_steps)
+        fp64 = {"value": args.fp64_steps / (f_ms * 1e-3), "unit": "evals/s", "ms_per_step": f_ms / args.fp64_steps,
+                "steps": args.fp64_steps}
+        plan.set_precision(args.precision)
+
+    line = None
+    if rank == 0:
+        step()
+        torch.cuda.synchronize()
+        gpu_out = (out["dEdq"].cpu().numpy(), out["forces"].cpu().numpy())
+        cb = None if args.no_cpu_baseline else cpu_baseline(s, gpu_out=gpu_out)
+        line = {
+            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": DTYPE.get(args.precision, args.precision), "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": args.precision,
+                       "skp_rank": R, "skp_r0": info["r0"], "skp_rel_err": skp_err,
+                       "l2": "flushed between steps (256 MB write outside the timed events)",
+                       "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
+            "tflops_useful": useful / (ms_step * 1e-3) / 1e12,
+            "roofline": roof, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "fp64_form": fp64, "clocks": clocks, "cpu_baseline": cb,
+            "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+        }
+        print(json.dumps(line), flush=True)
+    plan.close()
+    if pg:
+        pg.barrier()
+        pg.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

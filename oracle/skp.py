@@ -215,3 +215,26 @@ def reciprocal(x, q, box: float, K: int, n: int, beta: float, tol: float,
     E = 0.5 * float(np.dot(q, phi))
     W = spme.virial_trace(Q, E, K, n, box, beta)
     return dict(E=E, phi=phi, F=F, W=W, Q=Q, Phi=Phi, skp=skp)
+
+
+def generator(a: np.ndarray) -> np.ndarray:
+    """Real circulant generator g(d) = Re sum_m a(m) exp(2 i pi m d / K), d = 0..K-1."""
+    K = a.size
+    d = np.arange(K)
+    return np.real(np.exp(2j * np.pi * np.outer(d, np.arange(K)) / K) @ a)
+
+
+def generators(s: SKP):
+    """Two-level generator form of an NKPA SKP: (r1, gen_axis2 per outer term (weight s_i),
+    gen_axis1 per term (weight s_ij), gen_axis0 per term), as consumed by kpme_set_skp."""
+    if not s.r1:
+        raise ValueError("generators() needs the two-level (NKPA) structure")
+    gen3, gen2, gen1 = [], [], []
+    t = 0
+    for i, r1 in enumerate(s.r1):
+        gen3.append(s.outer[i] * generator(s.a2[t]))
+        for j in range(r1):
+            gen2.append(s.inner[i][j] * generator(s.a1[t]))
+            gen1.append(generator(s.a0[t]))
+            t += 1
+    return np.asarray(s.r1, dtype=np.int32), np.asarray(gen3), np.asarray(gen2), np.asarray(gen1)

@@ -1,0 +1,283 @@
+"""ctypes binding of libkpme (include/kpme.h): argument marshalling only.
+
+Every computation happens in the CUDA library; this module converts torch
+tensors to device pointers, passes the current CUDA stream, and turns status
+codes into exceptions.  If ``libkpme.so`` has not been built the import of
+``lib()`` raises: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libkpme.so")
+
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4, "bf16x3": 5, "bf16x6": 6}
+SKP_METHODS = {"svd": 0, "sinc": 1}
+STEP_NAMES = ["spread", "split", "skp_stage1", "skp_stage2", "skp_stage3", "gather", "virial"]
+
+EXPORTS = [
+    "kpme_default_params", "kpme_plan", "kpme_destroy", "kpme_set_stream", "kpme_set_precision",
+    "kpme_build_skp", "kpme_set_skp", "kpme_get_skp", "kpme_potential", "kpme_energy_forces",
+    "kpme_spread", "kpme_apply", "kpme_gather", "kpme_set_profiling", "kpme_get_profile",
+    "kpme_get_info", "kpme_status_string", "kpme_last_error",
+]
+
+
+class Params(C.Structure):
+    _fields_ = [
+        ("center", C.c_double * 3), ("radius", C.c_double), ("beta", C.c_double),
+        ("order", C.c_int), ("K", C.c_int), ("skp_tol", C.c_double), ("skp_method", C.c_int),
+        ("precision", C.c_int), ("max_n", C.c_int64), ("coulomb_k", C.c_double),
+    ]
+
+
+class Info(C.Structure):
+    _fields_ = [
+        ("K", C.c_int), ("order", C.c_int), ("precision", C.c_int), ("r0", C.c_int), ("R", C.c_int),
+        ("skp_rel_err", C.c_double), ("max_n", C.c_int64), ("scratch_bytes", C.c_int64),
+        ("flops_useful", C.c_double), ("flops_executed", C.c_double), ("kernels_per_eval", C.c_int),
+    ]
+
+
+class KpmeError(RuntimeError):
+    def __init__(self, func, status, detail=""):
+        self.status = status
+        msg = f"{func} failed: {_LIB.kpme_status_string(status).decode() if _LIB else status}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_LIB = None
+_vp, _i64, _dp, _ip = C.c_void_p, C.c_int64, C.c_void_p, C.POINTER(C.c_int)
+
+
+def lib():
+    """Load libkpme.so (built by ``__graft_entry__.build()`` / ``python -m paper_2601_18838_gb300.build``)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build the CUDA library first "
+                           "(python -m paper_2601_18838_gb300.build)")
+    L = C.CDLL(LIB_PATH)
+    st = C.c_int
+    sig = {
+        "kpme_default_params": (st, [C.POINTER(Params)]),
+        "kpme_plan": (st, [C.POINTER(Params), _vp, C.POINTER(_vp)]),
+        "kpme_destroy": (None, [_vp]),
+        "kpme_set_stream": (st, [_vp, _vp]),
+        "kpme_set_precision": (st, [_vp, C.c_int]),
+        "kpme_build_skp": (st, [_vp, _ip, C.POINTER(C.c_double)]),
+        "kpme_set_skp": (st, [_vp, C.c_int, _ip, _dp, _dp, _dp, C.c_double]),
+        "kpme_get_skp": (st, [_vp, _ip, _ip, _ip, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_double)]),
+        "kpme_potential": (st, [_vp, _i64, _vp, _vp, _i64, _vp, _vp]),
+        "kpme_energy_forces": (st, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
+        "kpme_spread": (st, [_vp, _i64, _vp, _vp, _vp]),
+        "kpme_apply": (st, [_vp, _vp, _vp]),
+        "kpme_gather": (st, [_vp, _i64, _vp, _vp, _vp, _vp, _vp]),
+        "kpme_set_profiling": (st, [_vp, C.c_int]),
+        "kpme_get_profile": (st, [_vp, C.POINTER(C.c_double), C.POINTER(C.c_int64), C.c_int, _ip, C.c_int]),
+        "kpme_get_info": (st, [_vp, C.POINTER(Info)]),
+        "kpme_status_string": (C.c_char_p, [C.c_int]),
+        "kpme_last_error": (C.c_char_p, [_vp]),
+    }
+    for name, (res, args) in sig.items():
+        f = getattr(L, name)
+        f.restype = res
+        f.argtypes = args
+    _LIB = L
+    return L
+
+
+def _ptr(t):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _np_ptr(a):
+    return a.ctypes.data_as(C.c_void_p)
+
+
+def _check_dev(t, name, dtype, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
+
+
+class Plan:
+    """One reciprocal-space problem: box, mesh, B-spline order, Ewald beta, SKP, arithmetic.
+
+    Mirrors ``kpme_plan``.  ``box`` is the side L = 2 r_B; positions live in
+    [center - L/2, center + L/2)^3 (wrapped periodically)."""
+
+    def __init__(self, box: float, K: int, order: int, beta: float = 0.35, center=None,
+                 precision: str = "bf16x6", skp_tol: float = 1e-8, skp_method: str = "svd",
+                 max_n: int = 1 << 20, coulomb_k: float = 1.0, stream=None):
+        import torch
+        L = lib()
+        p = Params()
+        L.kpme_default_params(C.byref(p))
+        c = (0.5 * box,) * 3 if center is None else tuple(center)
+        p.center = (C.c_double * 3)(*c)
+        p.radius = 0.5 * box
+        p.beta = beta
+        p.order = order
+        p.K = K
+        p.skp_tol = skp_tol
+        p.skp_method = SKP_METHODS[skp_method]
+        p.precision = PRECISIONS[precision]
+        p.max_n = max_n
+        p.coulomb_k = coulomb_k
+        self.params = p
+        self.box, self.K, self.order, self.beta = box, K, order, beta
+        self.precision = precision
+        self._stream = stream
+        h = C.c_void_p()
+        st = L.kpme_plan(C.byref(p), self._stream_handle(), C.byref(h))
+        if st != 0:
+            raise KpmeError("kpme_plan", st)
+        self._h = h
+        self.R = 0
+
+    def _stream_handle(self):
+        import torch
+        s = self._stream if self._stream is not None else torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def _call(self, name, *args):
+        L = lib()
+        L.kpme_set_stream(self._h, self._stream_handle())
+        st = getattr(L, name)(self._h, *args)
+        if st != 0:
+            raise KpmeError(name, st, L.kpme_last_error(self._h).decode())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kpme_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- SKP ----
+    def build_skp(self):
+        r = C.c_int()
+        e = C.c_double()
+        self._call("kpme_build_skp", C.byref(r), C.byref(e))
+        self.R = r.value
+        return r.value, e.value
+
+    def set_skp(self, r1, gen3, gen2, gen1, c: float = 0.0):
+        import numpy as np
+        r1 = np.ascontiguousarray(r1, dtype=np.int32)
+        g3 = np.ascontiguousarray(gen3, dtype=np.float64)
+        g2 = np.ascontiguousarray(gen2, dtype=np.float64)
+        g1 = np.ascontiguousarray(gen1, dtype=np.float64)
+        R = int(r1.sum())
+        if g3.shape != (r1.size, self.K) or g2.shape != (R, self.K) or g1.shape != (R, self.K):
+            raise ValueError("generator shapes must be (r0, K), (R, K), (R, K)")
+        self._call("kpme_set_skp", C.c_int(r1.size), r1.ctypes.data_as(_ip), _np_ptr(g3), _np_ptr(g2),
+                   _np_ptr(g1), C.c_double(c))
+        self.R = R
+
+    def get_skp(self) -> dict:
+        import numpy as np
+        r0, R = C.c_int(), C.c_int()
+        self._call("kpme_get_skp", C.byref(r0), C.byref(R), None, None, None, None, None, None, None)
+        r1 = np.zeros(r0.value, np.int32)
+        g3 = np.zeros((r0.value, self.K))
+        g2 = np.zeros((R.value, self.K))
+        g1 = np.zeros((R.value, self.K))
+        so = np.zeros(r0.value)
+        si = np.zeros(R.value)
+        c = C.c_double()
+        self._call("kpme_get_skp", C.byref(r0), C.byref(R), r1.ctypes.data_as(_ip), _np_ptr(g3), _np_ptr(g2),
+                   _np_ptr(g1), _np_ptr(so), _np_ptr(si), C.byref(c))
+        return dict(r0=r0.value, R=R.value, r1=r1, gen3=g3, gen2=g2, gen1=g1, sigma_outer=so,
+                    sigma_inner=si, c=c.value)
+
+    def set_precision(self, precision: str):
+        self._call("kpme_set_precision", C.c_int(PRECISIONS[precision]))
+        self.precision = precision
+
+    # ---- evaluation ----
+    def energy_forces(self, x, q, forces: bool = True, dEdq: bool = True, virial: bool = False, out=None):
+        """Energy (and -dE/dx, dE/dq, virial trace) for positions x (n,3) and charges q (n,), float64 CUDA."""
+        import torch
+        n = x.shape[0]
+        _check_dev(x, "x", torch.float64, (n, 3))
+        _check_dev(q, "q", torch.float64, (n,))
+        dev = x.device
+        o = out or {}
+        E = o.get("energy") if o.get("energy") is not None else torch.empty(1, dtype=torch.float64, device=dev)
+        F = (o.get("forces") if o.get("forces") is not None else torch.empty((n, 3), dtype=torch.float64, device=dev)) if forces else None
+        P = (o.get("dEdq") if o.get("dEdq") is not None else torch.empty(n, dtype=torch.float64, device=dev)) if dEdq else None
+        W = (o.get("virial") if o.get("virial") is not None else torch.empty(1, dtype=torch.float64, device=dev)) if virial else None
+        self._call("kpme_energy_forces", C.c_int64(n), _ptr(x), _ptr(q), _ptr(E), _ptr(F), _ptr(P), _ptr(W))
+        return dict(energy=E, forces=F, dEdq=P, virial=W)
+
+    def potential(self, y, q, x):
+        import torch
+        _check_dev(y, "y", torch.float64, (y.shape[0], 3))
+        _check_dev(q, "q", torch.float64, (y.shape[0],))
+        _check_dev(x, "x", torch.float64, (x.shape[0], 3))
+        p = torch.empty(x.shape[0], dtype=torch.float64, device=x.device)
+        self._call("kpme_potential", C.c_int64(y.shape[0]), _ptr(y), _ptr(q), C.c_int64(x.shape[0]), _ptr(x), _ptr(p))
+        return p
+
+    def spread(self, x, q):
+        import torch
+        n = x.shape[0]
+        _check_dev(x, "x", torch.float64, (n, 3))
+        _check_dev(q, "q", torch.float64, (n,))
+        Q = torch.empty((self.K,) * 3, dtype=torch.float64, device=x.device)
+        self._call("kpme_spread", C.c_int64(n), _ptr(x), _ptr(q), _ptr(Q))
+        return Q
+
+    def apply(self, Q):
+        import torch
+        _check_dev(Q, "Q", torch.float64, (self.K,) * 3)
+        Phi = torch.empty_like(Q)
+        self._call("kpme_apply", _ptr(Q), _ptr(Phi))
+        return Phi
+
+    def gather(self, x, q, Phi, forces: bool = True):
+        import torch
+        n = x.shape[0]
+        _check_dev(x, "x", torch.float64, (n, 3))
+        _check_dev(q, "q", torch.float64, (n,))
+        _check_dev(Phi, "Phi", torch.float64, (self.K,) * 3)
+        phi = torch.empty(n, dtype=torch.float64, device=x.device)
+        F = torch.empty((n, 3), dtype=torch.float64, device=x.device) if forces else None
+        self._call("kpme_gather", C.c_int64(n), _ptr(x), _ptr(q), _ptr(Phi), _ptr(phi), _ptr(F))
+        return phi, F
+
+    # ---- introspection ----
+    def set_profiling(self, on: bool = True):
+        self._call("kpme_set_profiling", C.c_int(1 if on else 0))
+
+    def get_profile(self, reset: bool = True) -> dict:
+        ms = (C.c_double * 16)()
+        nl = (C.c_int64 * 16)()
+        n = C.c_int()
+        self._call("kpme_get_profile", ms, nl, C.c_int(16), C.byref(n), C.c_int(1 if reset else 0))
+        return {STEP_NAMES[i]: (ms[i], nl[i]) for i in range(min(n.value, len(STEP_NAMES)))}
+
+    def info(self) -> dict:
+        i = Info()
+        self._call("kpme_get_info", C.byref(i))
+        return {f: getattr(i, f) for f, _ in Info._fields_}

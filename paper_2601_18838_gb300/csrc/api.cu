@@ -1,0 +1,690 @@
+// Host side of the C ABI declared in include/kpme.h: plans, SKP installation and the
+// evaluation pipeline of Algorithm 4 on one GPU (spread -> SKP mode products -> gather ->
+// float64 reductions), with the mode products ordered as the three reshaped steps of
+// Algorithm 2.
+#include "kpme_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+
+using namespace kpme;
+
+namespace kpme {
+
+PrecInfo prec_info(int precision) {
+  PrecInfo pi;
+  switch (precision) {
+    case KPME_FP64: pi.fp64 = true; pi.elem_bytes = 8; break;
+    case KPME_FP32: pi.elem_bytes = 4; break;
+    case KPME_TF32: pi.tensor = pi.tf32 = true; pi.slices = 1; pi.n_products = 1; pi.elem_bytes = 4; break;
+    case KPME_TF32X3: pi.tensor = pi.tf32 = true; pi.slices = 2; pi.n_products = 3; pi.elem_bytes = 4; break;
+    case KPME_BF16: pi.tensor = true; pi.slices = 1; pi.n_products = 1; pi.elem_bytes = 2; break;
+    case KPME_BF16X3: pi.tensor = true; pi.slices = 2; pi.n_products = 3; pi.elem_bytes = 2; break;
+    case KPME_BF16X6: pi.tensor = true; pi.slices = 3; pi.n_products = 6; pi.elem_bytes = 2; break;
+    default: break;
+  }
+  return pi;
+}
+
+}  // namespace kpme
+
+namespace {
+
+bool valid_precision(int p) { return p >= KPME_FP64 && p <= KPME_BF16X6; }
+
+// mesh element size (meshes Q, Phi and the CUDA-core intermediates)
+size_t mesh_elem(const kpme_plan_t P) { return P->prec.fp64 ? sizeof(double) : sizeof(float); }
+
+int64_t K3(const kpme_plan_t P) { return (int64_t)P->p.K * P->p.K * P->p.K; }
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+kpme_status_t dalloc(kpme_plan_t P, void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    P->last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
+    cudaGetLastError();
+    return e == cudaErrorMemoryAllocation ? KPME_ERR_OOM : KPME_ERR_CUDA;
+  }
+  P->scratch_bytes += (int64_t)bytes;
+  return KPME_OK;
+}
+
+void free_joblist(JobList& j) {
+  dfree(j.d_start);
+  dfree(j.d_pairs);
+  j = JobList();
+}
+
+kpme_status_t upload_joblist(kpme_plan_t P, JobList& j) {
+  j.n_jobs = (int)j.h_start.size() - 1;
+  j.max_pairs = 0;
+  for (int i = 0; i < j.n_jobs; ++i) j.max_pairs = std::max(j.max_pairs, j.h_start[i + 1] - j.h_start[i]);
+  kpme_status_t st;
+  if ((st = dalloc(P, (void**)&j.d_start, j.h_start.size() * sizeof(int))) != KPME_OK) return st;
+  if ((st = dalloc(P, (void**)&j.d_pairs, std::max<size_t>(1, j.h_pairs.size()) * sizeof(int2))) != KPME_OK)
+    return st;
+  KPME_CUDA_TRY(P, cudaMemcpyAsync(j.d_start, j.h_start.data(), j.h_start.size() * sizeof(int),
+                                   cudaMemcpyHostToDevice, P->stream));
+  if (!j.h_pairs.empty())
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(j.d_pairs, j.h_pairs.data(), j.h_pairs.size() * sizeof(int2),
+                                     cudaMemcpyHostToDevice, P->stream));
+  return KPME_OK;
+}
+
+void release_skp_buffers(kpme_plan_t P) {
+  auto drop = [&](void*& p) {
+    dfree(p);
+  };
+  drop(P->d_fac3);
+  drop(P->d_fac2);
+  drop(P->d_fac1);
+  drop(P->d_Qs);
+  drop(P->d_Y);
+  drop(P->d_Z);
+  free_joblist(P->stage1);
+  for (auto& g : P->groups) {
+    free_joblist(g.stage2);
+    free_joblist(g.stage3);
+  }
+  P->groups.clear();
+}
+
+void release_mesh_buffers(kpme_plan_t P) {
+  dfree(P->d_Q);
+  dfree(P->d_Phi);
+  dfree(P->d_Psi);
+  dfree(P->d_tmp1);
+  dfree(P->d_tmp2);
+  dfree(P->d_facv);
+}
+
+// Tensor-core tile: BN output columns (<= 256, multiple of 16) and pipeline depth.
+void choose_tc_tiles(kpme_plan_t P) {
+  const int K = P->p.K;
+  int bn = K;
+  while (bn > 256 || (tc_smem_bytes(P->prec, bn, 2) > 220 * 1024 && bn % 32 == 0)) bn /= 2;
+  P->tc_bn = bn;
+  int stages = 4;
+  while (stages > 1 && tc_smem_bytes(P->prec, bn, stages) > 220 * 1024) --stages;
+  P->tc_stages = stages;
+}
+
+int64_t group_budget_bytes() {
+  const char* e = getenv("KPME_GROUP_MB");
+  int64_t mb = e ? atoll(e) : 64;
+  if (mb < 1) mb = 1;
+  return mb << 20;
+}
+
+kpme_status_t alloc_meshes(kpme_plan_t P) {
+  release_mesh_buffers(P);
+  const size_t b = (size_t)K3(P) * mesh_elem(P);
+  kpme_status_t st;
+  if ((st = dalloc(P, &P->d_Q, b)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_Phi, b)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_Psi, b)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_tmp1, b)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_tmp2, b)) != KPME_OK) return st;
+  // rank-one virial operator (CUDA-core format of the plan's mesh)
+  double* dg = nullptr;
+  if ((st = dalloc(P, (void**)&dg, P->p.K * sizeof(double))) != KPME_OK) return st;
+  cudaError_t e = launch_virial_generator(P, dg);
+  if (e == cudaSuccess) {
+    if ((st = dalloc(P, &P->d_facv, (size_t)P->p.K * P->p.K * mesh_elem(P))) != KPME_OK) {
+      cudaFree(dg);
+      return st;
+    }
+    e = launch_materialize(P, dg, 1, P->d_facv, 1, P->prec.fp64 ? 0 : 1);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  }
+  cudaFree(dg);
+  P->scratch_bytes -= P->p.K * sizeof(double);
+  if (e != cudaSuccess) {
+    P->last_error = std::string("virial operator: ") + cudaGetErrorString(e);
+    return KPME_ERR_CUDA;
+  }
+  return KPME_OK;
+}
+
+// Materialise the installed SKP in the plan's arithmetic: factors, intermediates, job lists
+// and (tensor path) TMA descriptors.
+kpme_status_t install_skp(kpme_plan_t P) {
+  release_skp_buffers(P);
+  const SkpHost& S = P->skp;
+  if (!S.valid) return KPME_OK;
+  const int K = P->p.K, r0 = S.r0, R = S.R;
+  const int64_t k3 = K3(P);
+  const PrecInfo& pi = P->prec;
+  const int slices = pi.tensor ? pi.slices : 1;
+  const size_t eb = pi.tensor ? (size_t)pi.elem_bytes : mesh_elem(P);
+  const int kind = pi.tensor ? (pi.tf32 ? 3 : 2) : (pi.fp64 ? 0 : 1);
+  kpme_status_t st;
+
+  // factors
+  auto mat = [&](const std::vector<double>& gen, int count, void** dst) -> kpme_status_t {
+    kpme_status_t s2;
+    if ((s2 = dalloc(P, dst, (size_t)slices * count * K * K * eb)) != KPME_OK) return s2;
+    double* dg = nullptr;
+    KPME_CUDA_TRY(P, cudaMalloc((void**)&dg, gen.size() * sizeof(double)));
+    cudaError_t e = cudaMemcpyAsync(dg, gen.data(), gen.size() * sizeof(double), cudaMemcpyHostToDevice, P->stream);
+    if (e == cudaSuccess) e = launch_materialize(P, dg, count, *dst, slices, kind);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    cudaFree(dg);
+    KPME_CUDA_TRY(P, e);
+    return KPME_OK;
+  };
+  if ((st = mat(S.gen3, r0, &P->d_fac3)) != KPME_OK) return st;
+  if ((st = mat(S.gen2, R, &P->d_fac2)) != KPME_OK) return st;
+  if ((st = mat(S.gen1, R, &P->d_fac1)) != KPME_OK) return st;
+
+  // intermediates
+  int G = (int)std::max<int64_t>(1, group_budget_bytes() / std::max<int64_t>(1, (int64_t)slices * k3 * (int64_t)eb));
+  G = std::min(G, R);
+  P->group_terms = G;
+  if (pi.tensor && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_Y, (size_t)slices * r0 * k3 * eb)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_Z, (size_t)slices * G * k3 * eb)) != KPME_OK) return st;
+
+  // job lists
+  P->stage1.h_start.clear();
+  P->stage1.h_pairs.clear();
+  for (int i = 0; i <= r0; ++i) P->stage1.h_start.push_back(i);
+  for (int i = 0; i < r0; ++i) P->stage1.h_pairs.push_back(make_int2(0, i));
+  if ((st = upload_joblist(P, P->stage1)) != KPME_OK) return st;
+
+  if (pi.tensor) choose_tc_tiles(P);
+  const int m_tiles = pi.tensor ? (K * K + 127) / 128 : (K * K + 63) / 64;
+  const int n_tiles = pi.tensor ? K / P->tc_bn : (K + 63) / 64;
+  for (int t0 = 0; t0 < R; t0 += G) {
+    TermGroup g;
+    g.t0 = t0;
+    g.t1 = std::min(R, t0 + G);
+    const int nt = g.t1 - g.t0;
+    for (int t = g.t0; t <= g.t1; ++t) g.stage2.h_start.push_back(t - g.t0);
+    for (int t = g.t0; t < g.t1; ++t) g.stage2.h_pairs.push_back(make_int2(S.outer_of[t], t));
+    int splits = (2 * P->sm_count + m_tiles * n_tiles - 1) / (m_tiles * n_tiles);
+    splits = std::max(1, std::min(splits, nt));
+    g.splits = splits;
+    int pos = 0;
+    g.stage3.h_start.push_back(0);
+    for (int s = 0; s < splits; ++s) {
+      const int a = g.t0 + (int)((int64_t)nt * s / splits), b = g.t0 + (int)((int64_t)nt * (s + 1) / splits);
+      for (int t = a; t < b; ++t) g.stage3.h_pairs.push_back(make_int2(t - g.t0, t));
+      pos += b - a;
+      g.stage3.h_start.push_back(pos);
+    }
+    if ((st = upload_joblist(P, g.stage2)) != KPME_OK) return st;
+    if ((st = upload_joblist(P, g.stage3)) != KPME_OK) return st;
+    P->groups.push_back(std::move(g));
+  }
+
+  if (pi.tensor) {
+    const bool f32 = pi.tf32;
+    const uint32_t box0 = 128 / pi.elem_bytes;
+    const uint64_t KK = (uint64_t)K * K;
+    bool ok = encode_tmap(P, &P->tm_Q, P->d_Qs, pi.elem_bytes, f32, K, KK, (uint64_t)slices, box0, 128) &&
+              encode_tmap(P, &P->tm_Y, P->d_Y, pi.elem_bytes, f32, K, KK, (uint64_t)slices * r0, box0, 128) &&
+              encode_tmap(P, &P->tm_Z, P->d_Z, pi.elem_bytes, f32, K, KK, (uint64_t)slices * G, box0, 128) &&
+              encode_tmap(P, &P->tm_f3, P->d_fac3, pi.elem_bytes, f32, K, (uint64_t)r0 * K, slices, box0, P->tc_bn) &&
+              encode_tmap(P, &P->tm_f2, P->d_fac2, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn) &&
+              encode_tmap(P, &P->tm_f1, P->d_fac1, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn);
+    if (!ok) return KPME_ERR_CUDA;
+  }
+  KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
+  return KPME_OK;
+}
+
+// ---- profiling helpers ----
+cudaEvent_t take_event(kpme_plan_t P) {
+  if (!P->event_pool.empty()) {
+    cudaEvent_t e = P->event_pool.back();
+    P->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct StepScope {
+  kpme_plan_t P;
+  int step;
+  cudaEvent_t a = nullptr;
+  int launches;
+  StepScope(kpme_plan_t p, int s, int nl) : P(p), step(s), launches(nl) {
+    if (P->profiling) {
+      a = take_event(P);
+      cudaEventRecord(a, P->stream);
+    }
+  }
+  ~StepScope() {
+    P->launches += launches;
+    if (P->profiling) {
+      cudaEvent_t b = take_event(P);
+      cudaEventRecord(b, P->stream);
+      P->pending.push_back({step, {a, b}});
+      P->prof_launch[step] += launches;
+    }
+  }
+};
+
+kpme_status_t check_device_status(kpme_plan_t P) {
+  // the status word lives in mapped pinned host memory: readable without a synchronisation
+  volatile int* h = reinterpret_cast<volatile int*>(P->d_status);
+  if (h && *h != DEV_OK) {
+    *h = DEV_OK;
+    P->last_error = "a bounded device wait gave up";
+    return KPME_ERR_TIMEOUT;
+  }
+  return KPME_OK;
+}
+
+kpme_status_t contract(kpme_plan_t P, const void* Q, void* Phi) {
+  const int K = P->p.K;
+  const int M = K * K;
+  const int64_t k3 = K3(P);
+  const PrecInfo& pi = P->prec;
+  const SkpHost& S = P->skp;
+  if (!pi.tensor) {
+    const bool dbl = pi.fp64;
+    {
+      StepScope sc(P, STEP_SKP1, 1);
+      KPME_CUDA_TRY(P, launch_mp_simt(dbl, Q, 0, P->d_fac3, P->d_Y, k3, M, K, K, P->stage1, 0, P->stream));
+    }
+    KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * mesh_elem(P), P->stream));
+    for (const auto& g : P->groups) {
+      {
+        StepScope sc(P, STEP_SKP2, 1);
+        KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_Y, k3, P->d_fac2, P->d_Z, k3, M, K, K, g.stage2, 0, P->stream));
+      }
+      StepScope sc(P, STEP_SKP3, 1);
+      KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_Z, k3, P->d_fac1, Phi, 0, M, K, K, g.stage3, 1, P->stream));
+    }
+    (void)S;
+    return KPME_OK;
+  }
+  {
+    StepScope sc(P, STEP_SPLIT, 1);
+    KPME_CUDA_TRY(P, launch_split(P, (const float*)Q, P->d_Qs, k3));
+  }
+  {
+    StepScope sc(P, STEP_SKP1, 1);
+    TcArgs a{&P->tm_Q, &P->tm_f3, 1, P->d_Y, (int64_t)S.r0 * k3, M, K, K, 0, &P->stage1};
+    KPME_CUDA_TRY(P, launch_mp_tc(P, a));
+  }
+  KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
+  for (const auto& g : P->groups) {
+    {
+      StepScope sc(P, STEP_SKP2, 1);
+      TcArgs a{&P->tm_Y, &P->tm_f2, S.r0, P->d_Z, (int64_t)P->group_terms * k3, M, K, K, 0, &g.stage2};
+      KPME_CUDA_TRY(P, launch_mp_tc(P, a));
+    }
+    StepScope sc(P, STEP_SKP3, 1);
+    TcArgs a{&P->tm_Z, &P->tm_f1, P->group_terms, Phi, 0, M, K, K, 1, &g.stage3};
+    KPME_CUDA_TRY(P, launch_mp_tc(P, a));
+  }
+  return KPME_OK;
+}
+
+kpme_status_t virial(kpme_plan_t P, const double* energy, double* out) {
+  const int K = P->p.K, M = K * K;
+  const int64_t k3 = K3(P);
+  const bool dbl = P->prec.fp64;
+  StepScope sc(P, STEP_VIRIAL, 5);
+  KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_Q, 0, P->d_facv, P->d_tmp1, 0, M, K, K, P->single, 0, P->stream));
+  KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp1, 0, P->d_facv, P->d_tmp2, 0, M, K, K, P->single, 0, P->stream));
+  KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp2, 0, P->d_facv, P->d_Psi, 0, M, K, K, P->single, 0, P->stream));
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_qpsi, 0, sizeof(double), P->stream));
+  KPME_CUDA_TRY(P, launch_dot(P, P->d_Q, P->d_Psi, k3, P->d_qpsi));
+  const double L = 2.0 * P->p.radius;
+  const double t0 = 1.0 / (M_PI * L * L * L);
+  const double coef = 2.0 * M_PI * M_PI / (P->p.beta * P->p.beta);
+  KPME_CUDA_TRY(P, launch_virial_finalize(P, energy, P->d_qpsi, t0, coef, out));
+  return KPME_OK;
+}
+
+kpme_status_t common_checks(kpme_plan_t P, int64_t n) {
+  if (!P) return KPME_ERR_INVALID_ARG;
+  if (n < 0) return KPME_ERR_INVALID_ARG;
+  if (n > P->max_n) return KPME_ERR_CAPACITY;
+  kpme_status_t st = check_device_status(P);
+  if (st != KPME_OK) return st;
+  KPME_CUDA_TRY(P, cudaSetDevice(P->device));
+  return KPME_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+kpme_status_t kpme_default_params(kpme_params_t* p) {
+  if (!p) return KPME_ERR_INVALID_ARG;
+  memset(p, 0, sizeof(*p));
+  p->radius = 1.0;
+  p->beta = 0.35;
+  p->order = 4;
+  p->K = 32;
+  p->skp_tol = 1e-8;
+  p->skp_method = KPME_SKP_SVD;
+  p->precision = KPME_FP32;
+  p->max_n = 1 << 20;
+  p->coulomb_k = 1.0;
+  return KPME_OK;
+}
+
+const char* kpme_status_string(kpme_status_t s) {
+  switch (s) {
+    case KPME_OK: return "ok";
+    case KPME_ERR_INVALID_ARG: return "invalid argument";
+    case KPME_ERR_NOT_BUILT: return "SKP factors not built";
+    case KPME_ERR_CUDA: return "CUDA error";
+    case KPME_ERR_OOM: return "out of device memory";
+    case KPME_ERR_CAPACITY: return "particle count exceeds plan capacity";
+    case KPME_ERR_TIMEOUT: return "bounded device wait timed out";
+    case KPME_ERR_TOLERANCE: return "tolerance not reached";
+    case KPME_ERR_UNSUPPORTED: return "unsupported on this device or size";
+  }
+  return "unknown status";
+}
+
+const char* kpme_last_error(kpme_plan_t P) { return P ? P->last_error.c_str() : ""; }
+
+kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* out) {
+  if (!params || !out) return KPME_ERR_INVALID_ARG;
+  *out = nullptr;
+  const kpme_params_t& p = *params;
+  const bool ok = std::isfinite(p.radius) && p.radius > 0 && std::isfinite(p.beta) && p.beta > 0 &&
+                  (p.order == 4 || p.order == 6 || p.order == 8) && p.K % 2 == 0 && p.K >= 2 * p.order &&
+                  p.K <= 512 && std::isfinite(p.skp_tol) && p.skp_tol >= 0 &&
+                  (p.skp_method == KPME_SKP_SVD || p.skp_method == KPME_SKP_SINC) && valid_precision(p.precision) &&
+                  p.max_n >= 0 && std::isfinite(p.coulomb_k) && std::isfinite(p.center[0]) &&
+                  std::isfinite(p.center[1]) && std::isfinite(p.center[2]);
+  if (!ok) return KPME_ERR_INVALID_ARG;
+  kpme_plan_t P = new (std::nothrow) kpme_plan_s();
+  if (!P) return KPME_ERR_OOM;
+  P->p = p;
+  P->stream = (cudaStream_t)stream;
+  P->max_n = p.max_n;
+  P->prec = prec_info(p.precision);
+  auto fail = [&](kpme_status_t s) {
+    kpme_destroy(P);
+    return s;
+  };
+  if (cudaGetDevice(&P->device) != cudaSuccess) return fail(KPME_ERR_CUDA);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, P->device) != cudaSuccess) return fail(KPME_ERR_CUDA);
+  P->sm_count = prop.multiProcessorCount;
+  P->cc_major = prop.major;
+  P->cc_minor = prop.minor;
+  if (P->prec.tensor && (P->cc_major != 10 || p.K % 16 != 0)) {
+    P->last_error = "tensor-core precisions need an sm_103 device and K divisible by 16";
+    kpme_destroy(P);
+    return KPME_ERR_UNSUPPORTED;
+  }
+  int* hs = nullptr;
+  if (cudaHostAlloc((void**)&hs, sizeof(int), cudaHostAllocMapped) != cudaSuccess) return fail(KPME_ERR_CUDA);
+  *hs = DEV_OK;
+  P->d_status = hs;   // host pointer; its device alias is taken below
+  int* ds = nullptr;
+  if (cudaHostGetDevicePointer((void**)&ds, hs, 0) != cudaSuccess) return fail(KPME_ERR_CUDA);
+  // keep the host pointer for polling; kernels receive the device alias
+  P->d_status = ds == hs ? hs : ds;
+  if (ds != hs) {
+    // unified addressing makes both pointers equal on every supported system
+    P->last_error = "mapped status word needs unified addressing";
+    return fail(KPME_ERR_UNSUPPORTED);
+  }
+  double* acc = nullptr;
+  kpme_status_t st = dalloc(P, (void**)&acc, 4 * sizeof(double));
+  if (st != KPME_OK) return fail(st);
+  P->d_sumq = acc;
+  P->d_energy = acc + 1;
+  P->d_qpsi = acc + 2;
+  if ((st = alloc_meshes(P)) != KPME_OK) return fail(st);
+  P->single.h_start = {0, 1};
+  P->single.h_pairs = {make_int2(0, 0)};
+  if ((st = upload_joblist(P, P->single)) != KPME_OK) return fail(st);
+  if (cudaStreamSynchronize(P->stream) != cudaSuccess) return fail(KPME_ERR_CUDA);
+  *out = P;
+  return KPME_OK;
+}
+
+void kpme_destroy(kpme_plan_t P) {
+  if (!P) return;
+  cudaStreamSynchronize(P->stream);
+  release_skp_buffers(P);
+  release_mesh_buffers(P);
+  free_joblist(P->single);
+  if (P->d_sumq) cudaFree(P->d_sumq);
+  if (P->d_status) cudaFreeHost(P->d_status);
+  for (auto& pe : P->pending) {
+    cudaEventDestroy(pe.second.first);
+    cudaEventDestroy(pe.second.second);
+  }
+  for (auto e : P->event_pool) cudaEventDestroy(e);
+  delete P;
+}
+
+kpme_status_t kpme_set_stream(kpme_plan_t P, void* stream) {
+  if (!P) return KPME_ERR_INVALID_ARG;
+  P->stream = (cudaStream_t)stream;
+  return KPME_OK;
+}
+
+kpme_status_t kpme_set_precision(kpme_plan_t P, int precision) {
+  if (!P || !valid_precision(precision)) return KPME_ERR_INVALID_ARG;
+  const PrecInfo pi = prec_info(precision);
+  if (pi.tensor && (P->cc_major != 10 || P->p.K % 16 != 0)) {
+    P->last_error = "tensor-core precisions need an sm_103 device and K divisible by 16";
+    return KPME_ERR_UNSUPPORTED;
+  }
+  KPME_CUDA_TRY(P, cudaSetDevice(P->device));
+  KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
+  const bool mesh_change = pi.fp64 != P->prec.fp64;
+  P->p.precision = precision;
+  P->prec = pi;
+  kpme_status_t st;
+  if (mesh_change && (st = alloc_meshes(P)) != KPME_OK) return st;
+  return install_skp(P);
+}
+
+kpme_status_t kpme_build_skp(kpme_plan_t P, int* rank_out, double* err_out) {
+  if (!P) return KPME_ERR_INVALID_ARG;
+  KPME_CUDA_TRY(P, cudaSetDevice(P->device));
+  SkpHost S;
+  kpme_status_t st = P->p.skp_method == KPME_SKP_SVD ? build_skp_svd(P, S) : build_skp_sinc(P, S);
+  if (st != KPME_OK) return st;
+  P->skp = S;
+  if ((st = install_skp(P)) != KPME_OK) return st;
+  if (rank_out) *rank_out = S.R;
+  if (err_out) *err_out = S.rel_err;
+  return check_device_status(P);
+}
+
+kpme_status_t kpme_set_skp(kpme_plan_t P, int r0, const int* r1, const double* gen3, const double* gen2,
+                           const double* gen1, double c) {
+  if (!P || r0 <= 0 || !r1 || !gen3 || !gen2 || !gen1 || !std::isfinite(c)) return KPME_ERR_INVALID_ARG;
+  KPME_CUDA_TRY(P, cudaSetDevice(P->device));
+  const int K = P->p.K;
+  SkpHost S;
+  S.r0 = r0;
+  for (int i = 0; i < r0; ++i) {
+    if (r1[i] <= 0) return KPME_ERR_INVALID_ARG;
+    S.r1.push_back(r1[i]);
+    for (int j = 0; j < r1[i]; ++j) S.outer_of.push_back(i);
+  }
+  S.R = (int)S.outer_of.size();
+  S.gen3.assign(gen3, gen3 + (size_t)r0 * K);
+  S.gen2.assign(gen2, gen2 + (size_t)S.R * K);
+  S.gen1.assign(gen1, gen1 + (size_t)S.R * K);
+  S.sig_outer.assign(r0, 0.0);
+  S.sig_inner.assign(S.R, 0.0);
+  S.c = c;
+  S.valid = true;
+  P->skp = S;
+  return install_skp(P);
+}
+
+kpme_status_t kpme_get_skp(kpme_plan_t P, int* r0_out, int* R_out, int* r1, double* gen3, double* gen2,
+                           double* gen1, double* so, double* si, double* c_out) {
+  if (!P) return KPME_ERR_INVALID_ARG;
+  const SkpHost& S = P->skp;
+  if (!S.valid) return KPME_ERR_NOT_BUILT;
+  if (r0_out) *r0_out = S.r0;
+  if (R_out) *R_out = S.R;
+  if (r1) std::copy(S.r1.begin(), S.r1.end(), r1);
+  if (gen3) std::copy(S.gen3.begin(), S.gen3.end(), gen3);
+  if (gen2) std::copy(S.gen2.begin(), S.gen2.end(), gen2);
+  if (gen1) std::copy(S.gen1.begin(), S.gen1.end(), gen1);
+  if (so) std::copy(S.sig_outer.begin(), S.sig_outer.end(), so);
+  if (si) std::copy(S.sig_inner.begin(), S.sig_inner.end(), si);
+  if (c_out) *c_out = S.c;
+  return KPME_OK;
+}
+
+kpme_status_t kpme_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, double* Q) {
+  kpme_status_t st = common_checks(P, n);
+  if (st != KPME_OK) return st;
+  if (!Q || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
+  const int64_t k3 = K3(P);
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * mesh_elem(P), P->stream));
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+  KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
+  KPME_CUDA_TRY(P, launch_convert(P->d_Q, P->prec.fp64, Q, true, k3, P->stream));
+  return KPME_OK;
+}
+
+kpme_status_t kpme_apply(kpme_plan_t P, const double* Q, double* Phi) {
+  kpme_status_t st = common_checks(P, 0);
+  if (st != KPME_OK) return st;
+  if (!Q || !Phi) return KPME_ERR_INVALID_ARG;
+  if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
+  const int64_t k3 = K3(P);
+  KPME_CUDA_TRY(P, launch_convert(Q, true, P->d_Q, P->prec.fp64, k3, P->stream));
+  if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;
+  KPME_CUDA_TRY(P, launch_convert(P->d_Phi, P->prec.fp64, Phi, true, k3, P->stream));
+  if (P->skp.c != 0.0) {
+    P->last_error = "kpme_apply with a non-zero correction constant is not supported";
+    return KPME_ERR_UNSUPPORTED;
+  }
+  return KPME_OK;
+}
+
+kpme_status_t kpme_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const double* Phi,
+                          double* phi, double* F) {
+  kpme_status_t st = common_checks(P, n);
+  if (st != KPME_OK) return st;
+  if (!Phi || (n > 0 && (!x || !phi || (F && !q)))) return KPME_ERR_INVALID_ARG;
+  KPME_CUDA_TRY(P, launch_convert(Phi, true, P->d_Phi, P->prec.fp64, K3(P), P->stream));
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+  KPME_CUDA_TRY(P, launch_gather(P, n, x, F ? q : nullptr, P->d_Phi, phi, F, nullptr, 1.0));
+  return KPME_OK;
+}
+
+kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
+                                 double* forces, double* dEdq, double* vir) {
+  kpme_status_t st = common_checks(P, n);
+  if (st != KPME_OK) return st;
+  if (!energy || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
+  if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
+  P->launches = 0;
+  const int64_t k3 = K3(P);
+  KPME_CUDA_TRY(P, cudaMemsetAsync(energy, 0, sizeof(double), P->stream));
+  {
+    StepScope sc(P, STEP_SPREAD, n > 0 ? 1 : 0);
+    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * mesh_elem(P), P->stream));
+    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+    KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
+  }
+  if (n > 0) {
+    if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;
+    StepScope sc(P, STEP_GATHER, 1);
+    KPME_CUDA_TRY(P, launch_gather(P, n, x, q, P->d_Phi, dEdq, forces, energy, 1.0));
+  }
+  if (vir) {
+    if (n > 0) {
+      if ((st = virial(P, energy, vir)) != KPME_OK) return st;
+    } else {
+      KPME_CUDA_TRY(P, cudaMemsetAsync(vir, 0, sizeof(double), P->stream));
+    }
+  }
+  return KPME_OK;
+}
+
+kpme_status_t kpme_potential(kpme_plan_t P, int64_t n_y, const double* y, const double* q, int64_t n_x,
+                             const double* x, double* p) {
+  kpme_status_t st = common_checks(P, std::max(n_y, n_x));
+  if (st != KPME_OK) return st;
+  if ((n_y > 0 && (!y || !q)) || (n_x > 0 && (!x || !p)) || n_y < 0 || n_x < 0) return KPME_ERR_INVALID_ARG;
+  if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
+  const int64_t k3 = K3(P);
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * mesh_elem(P), P->stream));
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+  KPME_CUDA_TRY(P, launch_spread(P, n_y, y, q, P->d_Q));
+  if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;
+  KPME_CUDA_TRY(P, launch_gather(P, n_x, x, nullptr, P->d_Phi, p, nullptr, nullptr, 1.0));
+  return KPME_OK;
+}
+
+kpme_status_t kpme_set_profiling(kpme_plan_t P, int enable) {
+  if (!P) return KPME_ERR_INVALID_ARG;
+  P->profiling = enable != 0;
+  return KPME_OK;
+}
+
+kpme_status_t kpme_get_profile(kpme_plan_t P, double* ms, int64_t* launches, int n_steps, int* n_out, int reset) {
+  if (!P) return KPME_ERR_INVALID_ARG;
+  KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
+  for (auto& pe : P->pending) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, pe.second.first, pe.second.second) == cudaSuccess) P->prof_ms[pe.first] += t;
+    P->event_pool.push_back(pe.second.first);
+    P->event_pool.push_back(pe.second.second);
+  }
+  P->pending.clear();
+  for (int i = 0; i < NUM_STEPS && i < n_steps; ++i) {
+    if (ms) ms[i] = P->prof_ms[i];
+    if (launches) launches[i] = P->prof_launch[i];
+  }
+  if (n_out) *n_out = NUM_STEPS;
+  if (reset) {
+    for (int i = 0; i < NUM_STEPS; ++i) {
+      P->prof_ms[i] = 0.0;
+      P->prof_launch[i] = 0;
+    }
+  }
+  return check_device_status(P);
+}
+
+kpme_status_t kpme_get_info(kpme_plan_t P, kpme_info_t* info) {
+  if (!P || !info) return KPME_ERR_INVALID_ARG;
+  memset(info, 0, sizeof(*info));
+  const double K = P->p.K;
+  info->K = P->p.K;
+  info->order = P->p.order;
+  info->precision = P->p.precision;
+  info->r0 = P->skp.valid ? P->skp.r0 : 0;
+  info->R = P->skp.valid ? P->skp.R : 0;
+  info->skp_rel_err = P->skp.rel_err;
+  info->max_n = P->max_n;
+  info->scratch_bytes = P->scratch_bytes;
+  info->flops_useful = 6.0 * info->R * K * K * K * K;
+  const double mp = 2.0 * K * K * K * K;   // one mode product of one term
+  const double per_eval = (info->r0 + 2.0 * info->R) * mp;
+  info->flops_executed = per_eval * (P->prec.tensor ? P->prec.n_products : 1);
+  int kernels = 1 /*spread*/ + 1 /*gather*/ + 1 /*stage 1*/ + 2 * (int)P->groups.size();
+  if (P->prec.tensor) kernels += 1;
+  info->kernels_per_eval = kernels;
+  return KPME_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,176 @@
+// Internal declarations shared by the translation units of libkpme.
+#pragma once
+
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cudaTypedefs.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "kpme.h"
+
+namespace kpme {
+
+// Device status word values (written by bounded waits that give up).
+enum DeviceStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
+
+// Bounded spin budget for every device-side wait (~1 s at 2 GHz).
+constexpr long long kWaitCycles = 2000000000LL;
+
+// Steps reported by kpme_get_profile.
+enum Step : int {
+  STEP_SPREAD = 0, STEP_SPLIT, STEP_SKP1, STEP_SKP2, STEP_SKP3, STEP_GATHER, STEP_VIRIAL, NUM_STEPS
+};
+
+// Mode-product job list: job j accumulates pairs [start[j], start[j+1]) of (a_batch, factor).
+struct JobList {
+  int n_jobs = 0;
+  int* d_start = nullptr;   // n_jobs + 1
+  int2* d_pairs = nullptr;  // (a_batch, factor)
+  std::vector<int> h_start;
+  std::vector<int2> h_pairs;
+  int max_pairs = 0;
+};
+
+// One group of consecutive Kronecker terms processed by stages 2 and 3 together.
+struct TermGroup {
+  int t0 = 0, t1 = 0;       // terms [t0, t1)
+  JobList stage2;           // one job per term: (outer index of the term, term)
+  JobList stage3;           // split-K jobs: (term - t0, term)
+  int splits = 1;
+};
+
+struct SkpHost {
+  int r0 = 0, R = 0;
+  std::vector<int> r1;
+  std::vector<int> outer_of;               // term -> outer index
+  std::vector<double> gen3, gen2, gen1;    // r0 x K, R x K, R x K
+  std::vector<double> sig_outer, sig_inner;
+  double c = 0.0;
+  double rel_err = 0.0;
+  bool valid = false;
+};
+
+// Precision traits of a plan.
+struct PrecInfo {
+  bool tensor = false;    // tcgen05 path
+  bool fp64 = false;      // SIMT DFMA
+  bool tf32 = false;      // kind::tf32 (else kind::f16 with bf16)
+  int slices = 1;         // operand slices per value
+  int n_products = 1;     // MMAs per k-step
+  int elem_bytes = 4;     // bytes per stored slice element
+};
+PrecInfo prec_info(int precision);
+
+}  // namespace kpme
+
+struct kpme_plan_s {
+  kpme_params_t p{};
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int sm_count = 0;
+  int cc_major = 0, cc_minor = 0;
+  std::string last_error;
+  kpme::PrecInfo prec;
+
+  // particle-side scratch
+  int64_t max_n = 0;
+  double* d_sumq = nullptr;        // sum of charges of the last spread
+  double* d_energy = nullptr;      // accumulators (float64)
+  double* d_qpsi = nullptr;        // <Q, Psi> for the virial
+  int* d_status = nullptr;         // device status word
+
+  // meshes (float or double by precision), K^3 each
+  void* d_Q = nullptr;
+  void* d_Phi = nullptr;
+  void* d_Psi = nullptr;           // virial contraction output
+  void* d_tmp1 = nullptr;          // K^3 scratch for the rank-one virial contraction
+  void* d_tmp2 = nullptr;
+
+  // SKP
+  kpme::SkpHost skp;
+  void* d_fac3 = nullptr;          // factors in the plan's format
+  void* d_fac2 = nullptr;
+  void* d_fac1 = nullptr;
+  void* d_facv = nullptr;          // virial circulant (float/double), K x K
+  void* d_Qs = nullptr;            // tensor path: sliced Q
+  void* d_Y = nullptr;             // stage-1 output (r0 tensors)
+  void* d_Z = nullptr;             // stage-2 output (one term group)
+  int group_terms = 0;             // capacity of d_Z in terms
+  kpme::JobList stage1;
+  std::vector<kpme::TermGroup> groups;
+  kpme::JobList single;            // one job, one pair (0,0): rank-one contractions
+
+  // tensor maps (tcgen05 path)
+  CUtensorMap tm_Q{}, tm_Y{}, tm_Z{}, tm_f3{}, tm_f2{}, tm_f1{};
+  int tc_bn = 0, tc_stages = 0;
+
+  // profiling
+  bool profiling = false;
+  cudaEvent_t ev[2 * kpme::NUM_STEPS] = {};
+  double prof_ms[kpme::NUM_STEPS] = {};
+  int64_t prof_launch[kpme::NUM_STEPS] = {};
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+  std::vector<cudaEvent_t> event_pool;
+  int64_t launches = 0;            // kernels launched by the last evaluation
+
+  int64_t scratch_bytes = 0;
+};
+
+namespace kpme {
+
+// ---- launchers implemented in the .cu files -------------------------------------------------
+
+// particles.cu
+cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, void* Q);
+cudaError_t launch_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
+                          double* phi, double* F, double* energy, double scale_phi_extra);
+cudaError_t launch_dot(kpme_plan_t P, const void* a, const void* b, int64_t count, double* out);
+cudaError_t launch_virial_finalize(kpme_plan_t P, const double* energy, const double* qpsi,
+                                   double t0, double coef, double* virial);
+cudaError_t launch_convert(const void* src, bool src_double, void* dst, bool dst_double, int64_t count,
+                           cudaStream_t s);
+
+// skp_build.cu
+kpme_status_t build_skp_svd(kpme_plan_t P, SkpHost& out);
+kpme_status_t build_skp_sinc(kpme_plan_t P, SkpHost& out);
+cudaError_t launch_materialize(kpme_plan_t P, const double* d_gen, int count, void* dst, int fmt_slices,
+                               int fmt_kind);
+cudaError_t launch_virial_generator(kpme_plan_t P, double* d_gen);
+
+// gemm_simt.cu: out[job][n][m] (+)= sum_pairs sum_k fac[f][n][k] in[a][m][k]
+cudaError_t launch_mp_simt(bool dbl, const void* in, int64_t in_bs, const void* fac, void* out,
+                           int64_t out_bs, int M, int N, int Kr, const JobList& jobs, int mode,
+                           cudaStream_t s);
+
+// gemm_tc.cu
+struct TcArgs {
+  const CUtensorMap* tmA;
+  const CUtensorMap* tmB;
+  int nbatchA;              // batches per slice plane of A
+  void* out;                // slices [S][nbatch_out][N][M] or float Phi [N][M]
+  int64_t out_plane;        // elements per output slice plane (nbatch_out * N * M)
+  int M, N, Kr;
+  int mode;                 // 0 store slices, 1 atomic-add float
+  const JobList* jobs;
+};
+cudaError_t launch_mp_tc(kpme_plan_t P, const TcArgs& a);
+cudaError_t launch_split(kpme_plan_t P, const float* src, void* dst, int64_t count);
+bool encode_tmap(kpme_plan_t P, CUtensorMap* map, const void* base, int elem_bytes, bool is_f32,
+                 uint64_t dim0, uint64_t dim1, uint64_t dim2, uint32_t box0, uint32_t box1);
+int tc_smem_bytes(const PrecInfo& pi, int bn, int stages);
+
+}  // namespace kpme
+
+#define KPME_CUDA_TRY(P, expr)                                                   \
+  do {                                                                           \
+    cudaError_t _e = (expr);                                                     \
+    if (_e != cudaSuccess) {                                                     \
+      (P)->last_error = std::string(#expr) + ": " + cudaGetErrorString(_e);      \
+      return _e == cudaErrorMemoryAllocation ? KPME_ERR_OOM : KPME_ERR_CUDA;     \
+    }                                                                            \
+  } while (0)
