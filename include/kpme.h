@@ -192,6 +192,25 @@ kpme_status_t kpme_set_profiling(kpme_plan_t plan, int enable);
 kpme_status_t kpme_get_profile(kpme_plan_t plan, double* ms, int64_t* launches, int n_steps,
                                int* n_out, int reset);
 
+/* Charge spreading without any device allocation (the paper has no counterpart: this
+ * serves callers that may not call cudaMalloc — code running during CUDA-graph stream
+ * capture, engines whose device memory belongs to their own pool allocator, loops that
+ * cannot afford an allocation's device synchronisation).  Same result as kpme_spread
+ * with a float32 mesh, but without a plan: params describes the box, order and K
+ * (the other fields are ignored), stream is a cudaStream_t, x (n x 3), q (n) and Q
+ * (K^3, float64) are device pointers owned by the caller.
+ * Scratch: a static device array of 256 B + KPME_NOALLOC_MAX_K^3 float32 (1 MiB for
+ * K <= 64) that every GPU loading the library keeps until process exit.  K above
+ * KPME_NOALLOC_MAX_K returns KPME_ERR_CAPACITY; bad arguments KPME_ERR_INVALID_ARG.
+ * The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture begins.  All calls share the
+ * array and each clears it first: calls whose GPU work overlaps race and must be
+ * serialised by the caller.  Allocates nothing (no cudaMalloc, cudaFree or allocating
+ * library call). */
+#define KPME_NOALLOC_MAX_K 64
+kpme_status_t kpme_spread_noalloc(const kpme_params_t* params, void* stream, int64_t n, const double* x,
+                                  const double* q, double* Q);
+
 typedef struct {
   int K, order, precision, r0, R;
   double skp_rel_err;

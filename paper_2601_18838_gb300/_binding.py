@@ -21,7 +21,7 @@ EXPORTS = [
     "kpme_default_params", "kpme_plan", "kpme_destroy", "kpme_set_stream", "kpme_set_precision",
     "kpme_build_skp", "kpme_set_skp", "kpme_get_skp", "kpme_potential", "kpme_energy_forces",
     "kpme_spread", "kpme_apply", "kpme_gather", "kpme_set_profiling", "kpme_get_profile",
-    "kpme_get_info", "kpme_status_string", "kpme_last_error",
+    "kpme_get_info", "kpme_status_string", "kpme_last_error", "kpme_spread_noalloc",
 ]
 
 
@@ -83,6 +83,7 @@ def lib():
         "kpme_get_info": (st, [_vp, C.POINTER(Info)]),
         "kpme_status_string": (C.c_char_p, [C.c_int]),
         "kpme_last_error": (C.c_char_p, [_vp]),
+        "kpme_spread_noalloc": (st, [C.POINTER(Params), _vp, _i64, _vp, _vp, _vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -134,6 +134,8 @@ cudaError_t launch_virial_finalize(kpme_plan_t P, const double* energy, const do
                                    double t0, double coef, double* virial);
 cudaError_t launch_convert(const void* src, bool src_double, void* dst, bool dst_double, int64_t count,
                            cudaStream_t s);
+cudaError_t launch_spread_raw(const kpme_params_t& p, int sm_count, cudaStream_t s, int64_t n, const double* x,
+                              const double* q, float* Q, double* sumq);
 
 // skp_build.cu
 kpme_status_t build_skp_svd(kpme_plan_t P, SkpHost& out);

@@ -285,3 +285,29 @@ cudaError_t launch_convert(const void* src, bool src_double, void* dst, bool dst
 }
 
 }  // namespace kpme
+
+namespace kpme {
+
+// Spread into caller-provided float32 mesh / float64 charge-sum buffers, without a plan.
+cudaError_t launch_spread_raw(const kpme_params_t& p, int sm_count, cudaStream_t s, int64_t n, const double* x,
+                              const double* q, float* Q, double* sumq) {
+  if (n <= 0) return cudaSuccess;
+  MeshGeom G;
+  G.c0 = p.center[0];
+  G.c1 = p.center[1];
+  G.c2 = p.center[2];
+  G.L = 2.0 * p.radius;
+  G.K = p.K;
+  int64_t want = (n + kThreads - 1) / kThreads;
+  const int64_t cap = (int64_t)sm_count * 8;
+  const int grid = (int)(want > cap ? cap : (want < 1 ? 1 : want));
+  switch (p.order) {
+    case 4: spread_kernel<float, 4><<<grid, kThreads, 0, s>>>(G, n, x, q, Q, sumq); break;
+    case 6: spread_kernel<float, 6><<<grid, kThreads, 0, s>>>(G, n, x, q, Q, sumq); break;
+    case 8: spread_kernel<float, 8><<<grid, kThreads, 0, s>>>(G, n, x, q, Q, sumq); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kpme
