@@ -33,7 +33,7 @@ WORKLOAD_TEXT = {
     "large": "1e6 charges +-1, L=220 A, order 6, K=256, beta=0.35/A, SKP tol 1e-7",
 }
 DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16": "bf16", "bf16x3": "bf16",
-         "bf16x6": "bf16"}
+         "bf16x6": "bf16", "bf16x10": "bf16"}
 
 
 def _peaks():
@@ -154,7 +154,7 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water", choices=list(WORKLOAD_TEXT))
-    ap.add_argument("--precision", default="bf16x6")
+    ap.add_argument("--precision", default="bf16x10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
     args = ap.parse_args(argv)
@@ -236,7 +236,7 @@ def main(argv=None):
     skp_launches = sum(prof[k][1] for k in ("skp_stage1", "skp_stage2", "skp_stage3")) / args.steps
     launches_per_step = sum(v[1] for v in prof.values()) / args.steps
     peaks, peak_src = _peaks()
-    tensor = args.precision in ("bf16", "tf32", "bf16x3", "tf32x3", "bf16x6")
+    tensor = args.precision in ("bf16", "tf32", "bf16x3", "tf32x3", "bf16x6", "bf16x10")
     # algorithmic MMA flops of the split method per step: executed products of slices
     mp_flops = info["flops_executed"]
     per_launch_ms = skp_ms / max(skp_launches, 1)

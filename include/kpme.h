@@ -73,10 +73,10 @@ typedef enum {
   KPME_ERR_UNSUPPORTED = 8    /* precision or size not supported on this device       */
 } kpme_status_t;
 
-/* Arithmetic of the SKP mode products (the dominant step).  Meshes are float32
- * except for KPME_FP64; spreading and gathering run in float32 (float64 for
- * KPME_FP64) after float64 mesh coordinates; energy and virial are reduced in
- * float64 in every mode. */
+/* Arithmetic of the SKP mode products (the dominant step).  In every mode the
+ * mesh coordinates are float64, the charge mesh is accumulated in float64, and
+ * energy and virial are reduced in float64; the potential mesh and the gather
+ * are float32 except for KPME_FP64. */
 typedef enum {
   KPME_FP64 = 0,    /* CUDA-core DFMA mode products                                 */
   KPME_FP32 = 1,    /* CUDA-core FFMA mode products                                 */
@@ -84,7 +84,10 @@ typedef enum {
   KPME_TF32X3 = 3,  /* tcgen05 kind::tf32, hi+lo split, three products              */
   KPME_BF16 = 4,    /* tcgen05 kind::f16 (bf16), one product                        */
   KPME_BF16X3 = 5,  /* bf16 hi+lo split, three products                             */
-  KPME_BF16X6 = 6   /* bf16 hi+mid+lo split, six products (all with slice sum <= 2) */
+  KPME_BF16X6 = 6,  /* bf16 hi+mid+lo split, six products (all with slice sum <= 2) */
+  KPME_BF16X10 = 7  /* error-free split: four fixed-point bf16 slices per row with a common
+                       exponent, ten products; the leading products sum exactly in FP32
+                       (Ozaki et al. splitting); float32 intermediates                  */
 } kpme_precision_t;
 
 typedef enum {

@@ -13,7 +13,7 @@ import os
 PKG = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(PKG, "libkpme.so")
 
-PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4, "bf16x3": 5, "bf16x6": 6}
+PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4, "bf16x3": 5, "bf16x6": 6, "bf16x10": 7}
 SKP_METHODS = {"svd": 0, "sinc": 1}
 STEP_NAMES = ["spread", "split", "skp_stage1", "skp_stage2", "skp_stage3", "gather", "virial"]
 
@@ -123,7 +123,7 @@ class Plan:
     [center - L/2, center + L/2)^3 (wrapped periodically)."""
 
     def __init__(self, box: float, K: int, order: int, beta: float = 0.35, center=None,
-                 precision: str = "bf16x6", skp_tol: float = 1e-8, skp_method: str = "svd",
+                 precision: str = "bf16x10", skp_tol: float = 1e-8, skp_method: str = "svd",
                  max_n: int = 1 << 20, coulomb_k: float = 1.0, stream=None):
         import torch
         L = lib()

@@ -24,6 +24,7 @@ PrecInfo prec_info(int precision) {
     case KPME_BF16: pi.tensor = true; pi.slices = 1; pi.n_products = 1; pi.elem_bytes = 2; break;
     case KPME_BF16X3: pi.tensor = true; pi.slices = 2; pi.n_products = 3; pi.elem_bytes = 2; break;
     case KPME_BF16X6: pi.tensor = true; pi.slices = 3; pi.n_products = 6; pi.elem_bytes = 2; break;
+    case KPME_BF16X10: pi.tensor = pi.oz = true; pi.slices = 4; pi.n_products = 10; pi.elem_bytes = 2; break;
     default: break;
   }
   return pi;
@@ -33,7 +34,7 @@ PrecInfo prec_info(int precision) {
 
 namespace {
 
-bool valid_precision(int p) { return p >= KPME_FP64 && p <= KPME_BF16X6; }
+bool valid_precision(int p) { return p >= KPME_FP64 && p <= KPME_BF16X10; }
 
 // mesh element size (meshes Q, Phi and the CUDA-core intermediates)
 size_t mesh_elem(const kpme_plan_t P) { return P->prec.fp64 ? sizeof(double) : sizeof(float); }
@@ -90,6 +91,9 @@ void release_skp_buffers(kpme_plan_t P) {
   drop(P->d_Qs);
   drop(P->d_Y);
   drop(P->d_Z);
+  dfree(P->d_rmQ);
+  dfree(P->d_rmY);
+  dfree(P->d_rmZ);
   free_joblist(P->stage1);
   for (auto& g : P->groups) {
     free_joblist(g.stage2);
@@ -100,6 +104,7 @@ void release_skp_buffers(kpme_plan_t P) {
 
 void release_mesh_buffers(kpme_plan_t P) {
   dfree(P->d_Q);
+  dfree(P->d_Qf);
   dfree(P->d_Phi);
   dfree(P->d_Psi);
   dfree(P->d_tmp1);
@@ -110,6 +115,13 @@ void release_mesh_buffers(kpme_plan_t P) {
 // Tensor-core tile: BN output columns (<= 256, multiple of 16) and pipeline depth.
 void choose_tc_tiles(kpme_plan_t P) {
   const int K = P->p.K;
+  if (P->prec.oz) {
+    // error-free split: four A slices (64 KB) + four B slices per stage, two stages
+    P->tc_bn = K <= 96 ? K : 64;
+    P->tc_stages = 2;
+    while (P->tc_stages > 1 && oz_smem_bytes(P->tc_bn, P->tc_stages) > 227 * 1024) --P->tc_stages;
+    return;
+  }
   int bn = K;
   while (bn > 256 || (tc_smem_bytes(P->prec, bn, 2) > 220 * 1024 && bn % 32 == 0)) bn /= 2;
   P->tc_bn = bn;
@@ -129,7 +141,8 @@ kpme_status_t alloc_meshes(kpme_plan_t P) {
   release_mesh_buffers(P);
   const size_t b = (size_t)K3(P) * mesh_elem(P);
   kpme_status_t st;
-  if ((st = dalloc(P, &P->d_Q, b)) != KPME_OK) return st;
+  if ((st = dalloc(P, (void**)&P->d_Q, (size_t)K3(P) * sizeof(double))) != KPME_OK) return st;
+  if (!P->prec.fp64 && (st = dalloc(P, (void**)&P->d_Qf, (size_t)K3(P) * sizeof(float))) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_Phi, b)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_Psi, b)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_tmp1, b)) != KPME_OK) return st;
@@ -166,7 +179,7 @@ kpme_status_t install_skp(kpme_plan_t P) {
   const PrecInfo& pi = P->prec;
   const int slices = pi.tensor ? pi.slices : 1;
   const size_t eb = pi.tensor ? (size_t)pi.elem_bytes : mesh_elem(P);
-  const int kind = pi.tensor ? (pi.tf32 ? 3 : 2) : (pi.fp64 ? 0 : 1);
+  const int kind = pi.oz ? 4 : pi.tensor ? (pi.tf32 ? 3 : 2) : (pi.fp64 ? 0 : 1);
   kpme_status_t st;
 
   // factors
@@ -186,13 +199,21 @@ kpme_status_t install_skp(kpme_plan_t P) {
   if ((st = mat(S.gen2, R, &P->d_fac2)) != KPME_OK) return st;
   if ((st = mat(S.gen1, R, &P->d_fac1)) != KPME_OK) return st;
 
-  // intermediates
-  int G = (int)std::max<int64_t>(1, group_budget_bytes() / std::max<int64_t>(1, (int64_t)slices * k3 * (int64_t)eb));
+  // intermediates (the error-free split keeps float32 values and per-row maxima)
+  const int islices = pi.oz ? 1 : slices;
+  const size_t ieb = pi.oz ? sizeof(float) : eb;
+  int G = (int)std::max<int64_t>(1, group_budget_bytes() / std::max<int64_t>(1, (int64_t)islices * k3 * (int64_t)ieb));
   G = std::min(G, R);
   P->group_terms = G;
-  if (pi.tensor && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
-  if ((st = dalloc(P, &P->d_Y, (size_t)slices * r0 * k3 * eb)) != KPME_OK) return st;
-  if ((st = dalloc(P, &P->d_Z, (size_t)slices * G * k3 * eb)) != KPME_OK) return st;
+  if (pi.tensor && !pi.oz && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_Y, (size_t)islices * r0 * k3 * ieb)) != KPME_OK) return st;
+  if ((st = dalloc(P, &P->d_Z, (size_t)islices * G * k3 * ieb)) != KPME_OK) return st;
+  if (pi.oz) {
+    const size_t k2 = (size_t)K * K;
+    if ((st = dalloc(P, (void**)&P->d_rmQ, k2 * sizeof(float))) != KPME_OK) return st;
+    if ((st = dalloc(P, (void**)&P->d_rmY, (size_t)r0 * k2 * sizeof(float))) != KPME_OK) return st;
+    if ((st = dalloc(P, (void**)&P->d_rmZ, (size_t)G * k2 * sizeof(float))) != KPME_OK) return st;
+  }
 
   // job lists
   P->stage1.h_start.clear();
@@ -231,9 +252,10 @@ kpme_status_t install_skp(kpme_plan_t P) {
     const bool f32 = pi.tf32;
     const uint32_t box0 = 128 / pi.elem_bytes;
     const uint64_t KK = (uint64_t)K * K;
-    bool ok = encode_tmap(P, &P->tm_Q, P->d_Qs, pi.elem_bytes, f32, K, KK, (uint64_t)slices, box0, 128) &&
-              encode_tmap(P, &P->tm_Y, P->d_Y, pi.elem_bytes, f32, K, KK, (uint64_t)slices * r0, box0, 128) &&
-              encode_tmap(P, &P->tm_Z, P->d_Z, pi.elem_bytes, f32, K, KK, (uint64_t)slices * G, box0, 128) &&
+    bool ok = (pi.oz ||
+               (encode_tmap(P, &P->tm_Q, P->d_Qs, pi.elem_bytes, f32, K, KK, (uint64_t)slices, box0, 128) &&
+                encode_tmap(P, &P->tm_Y, P->d_Y, pi.elem_bytes, f32, K, KK, (uint64_t)slices * r0, box0, 128) &&
+                encode_tmap(P, &P->tm_Z, P->d_Z, pi.elem_bytes, f32, K, KK, (uint64_t)slices * G, box0, 128))) &&
               encode_tmap(P, &P->tm_f3, P->d_fac3, pi.elem_bytes, f32, K, (uint64_t)r0 * K, slices, box0, P->tc_bn) &&
               encode_tmap(P, &P->tm_f2, P->d_fac2, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn) &&
               encode_tmap(P, &P->tm_f1, P->d_fac1, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn);
@@ -288,7 +310,8 @@ kpme_status_t check_device_status(kpme_plan_t P) {
   return KPME_OK;
 }
 
-kpme_status_t contract(kpme_plan_t P, const void* Q, void* Phi) {
+// Q: the float64 charge mesh; Phi: float32 (float64 for the FP64 form).
+kpme_status_t contract(kpme_plan_t P, const double* Q, void* Phi) {
   const int K = P->p.K;
   const int M = K * K;
   const int64_t k3 = K3(P);
@@ -296,9 +319,15 @@ kpme_status_t contract(kpme_plan_t P, const void* Q, void* Phi) {
   const SkpHost& S = P->skp;
   if (!pi.tensor) {
     const bool dbl = pi.fp64;
+    const void* Qin = Q;
+    if (!dbl) {
+      StepScope sc(P, STEP_SPLIT, 1);
+      KPME_CUDA_TRY(P, launch_convert(Q, true, P->d_Qf, false, k3, P->stream));
+      Qin = P->d_Qf;
+    }
     {
       StepScope sc(P, STEP_SKP1, 1);
-      KPME_CUDA_TRY(P, launch_mp_simt(dbl, Q, 0, P->d_fac3, P->d_Y, k3, M, K, K, P->stage1, 0, P->stream));
+      KPME_CUDA_TRY(P, launch_mp_simt(dbl, Qin, 0, P->d_fac3, P->d_Y, k3, M, K, K, P->stage1, 0, P->stream));
     }
     KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * mesh_elem(P), P->stream));
     for (const auto& g : P->groups) {
@@ -312,9 +341,36 @@ kpme_status_t contract(kpme_plan_t P, const void* Q, void* Phi) {
     (void)S;
     return KPME_OK;
   }
+  if (pi.oz) {
+    const int64_t k2 = (int64_t)K * K;
+    {
+      StepScope sc(P, STEP_SPLIT, 1);
+      KPME_CUDA_TRY(P, launch_rowmax(P, Q, k2, K, P->d_rmQ));
+    }
+    {
+      StepScope sc(P, STEP_SKP1, 1);
+      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmY, 0, (size_t)S.r0 * k2 * sizeof(float), P->stream));
+      OzArgs a{&P->tm_f3, Q, true, 0, P->d_rmQ, 0, (float*)P->d_Y, k3, P->d_rmY, k2, M, K, K, 0, &P->stage1};
+      KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+    }
+    KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
+    for (const auto& g : P->groups) {
+      {
+        StepScope sc(P, STEP_SKP2, 1);
+        KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
+        OzArgs a{&P->tm_f2, P->d_Y, false, k3, P->d_rmY, k2, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K, K, 0,
+                 &g.stage2};
+        KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+      }
+      StepScope sc(P, STEP_SKP3, 1);
+      OzArgs a{&P->tm_f1, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1, &g.stage3};
+      KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+    }
+    return KPME_OK;
+  }
   {
     StepScope sc(P, STEP_SPLIT, 1);
-    KPME_CUDA_TRY(P, launch_split(P, (const float*)Q, P->d_Qs, k3));
+    KPME_CUDA_TRY(P, launch_split(P, Q, P->d_Qs, k3));
   }
   {
     StepScope sc(P, STEP_SKP1, 1);
@@ -339,12 +395,17 @@ kpme_status_t virial(kpme_plan_t P, const double* energy, double* out) {
   const int K = P->p.K, M = K * K;
   const int64_t k3 = K3(P);
   const bool dbl = P->prec.fp64;
-  StepScope sc(P, STEP_VIRIAL, 5);
-  KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_Q, 0, P->d_facv, P->d_tmp1, 0, M, K, K, P->single, 0, P->stream));
+  StepScope sc(P, STEP_VIRIAL, dbl ? 5 : 6);
+  const void* Qv = P->d_Q;
+  if (!dbl) {
+    KPME_CUDA_TRY(P, launch_convert(P->d_Q, true, P->d_Qf, false, k3, P->stream));
+    Qv = P->d_Qf;
+  }
+  KPME_CUDA_TRY(P, launch_mp_simt(dbl, Qv, 0, P->d_facv, P->d_tmp1, 0, M, K, K, P->single, 0, P->stream));
   KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp1, 0, P->d_facv, P->d_tmp2, 0, M, K, K, P->single, 0, P->stream));
   KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp2, 0, P->d_facv, P->d_Psi, 0, M, K, K, P->single, 0, P->stream));
   KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_qpsi, 0, sizeof(double), P->stream));
-  KPME_CUDA_TRY(P, launch_dot(P, P->d_Q, P->d_Psi, k3, P->d_qpsi));
+  KPME_CUDA_TRY(P, launch_dot(P, Qv, P->d_Psi, k3, P->d_qpsi));
   const double L = 2.0 * P->p.radius;
   const double t0 = 1.0 / (M_PI * L * L * L);
   const double coef = 2.0 * M_PI * M_PI / (P->p.beta * P->p.beta);
@@ -556,10 +617,10 @@ kpme_status_t kpme_spread(kpme_plan_t P, int64_t n, const double* x, const doubl
   if (st != KPME_OK) return st;
   if (!Q || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
   const int64_t k3 = K3(P);
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * mesh_elem(P), P->stream));
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
   KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
   KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
-  KPME_CUDA_TRY(P, launch_convert(P->d_Q, P->prec.fp64, Q, true, k3, P->stream));
+  KPME_CUDA_TRY(P, cudaMemcpyAsync(Q, P->d_Q, (size_t)k3 * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
   return KPME_OK;
 }
 
@@ -569,7 +630,7 @@ kpme_status_t kpme_apply(kpme_plan_t P, const double* Q, double* Phi) {
   if (!Q || !Phi) return KPME_ERR_INVALID_ARG;
   if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
   const int64_t k3 = K3(P);
-  KPME_CUDA_TRY(P, launch_convert(Q, true, P->d_Q, P->prec.fp64, k3, P->stream));
+  KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_Q, Q, (size_t)k3 * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
   if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;
   KPME_CUDA_TRY(P, launch_convert(P->d_Phi, P->prec.fp64, Phi, true, k3, P->stream));
   if (P->skp.c != 0.0) {
@@ -601,7 +662,7 @@ kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, cons
   KPME_CUDA_TRY(P, cudaMemsetAsync(energy, 0, sizeof(double), P->stream));
   {
     StepScope sc(P, STEP_SPREAD, n > 0 ? 1 : 0);
-    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * mesh_elem(P), P->stream));
+    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
     KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
     KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
   }
@@ -627,7 +688,7 @@ kpme_status_t kpme_potential(kpme_plan_t P, int64_t n_y, const double* y, const 
   if ((n_y > 0 && (!y || !q)) || (n_x > 0 && (!x || !p)) || n_y < 0 || n_x < 0) return KPME_ERR_INVALID_ARG;
   if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
   const int64_t k3 = K3(P);
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * mesh_elem(P), P->stream));
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
   KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
   KPME_CUDA_TRY(P, launch_spread(P, n_y, y, q, P->d_Q));
   if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;

@@ -308,20 +308,20 @@ __global__ void __launch_bounds__(kThreads, 1)
 
 // fp32 -> S slices (bf16 round-to-nearest cascade, or tf32 hi / lo in float32)
 template <bool TF32, int S>
-__global__ void split_kernel(const float* __restrict__ src, void* __restrict__ dst, int64_t count) {
+__global__ void split_kernel(const double* __restrict__ src, void* __restrict__ dst, int64_t count) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const float v = src[i];
+    const double v = src[i];
     if constexpr (TF32) {
-      const float hi = tf32_rn(v);
+      const float hi = tf32_rn((float)v);
       reinterpret_cast<float*>(dst)[i] = hi;
-      if (S > 1) reinterpret_cast<float*>(dst)[count + i] = v - hi;
+      if (S > 1) reinterpret_cast<float*>(dst)[count + i] = (float)(v - (double)hi);
     } else {
-      float rem = v;
+      double rem = v;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const __nv_bfloat16 h = __float2bfloat16_rn(rem);
+        const __nv_bfloat16 h = __double2bfloat16(rem);
         reinterpret_cast<__nv_bfloat16*>(dst)[s * count + i] = h;
-        rem -= __bfloat162float(h);
+        rem -= (double)__bfloat162float(h);
       }
     }
   }
@@ -415,7 +415,7 @@ cudaError_t launch_mp_tc(kpme_plan_t P, const TcArgs& a) {
   return launch_t<false, 3>(P, a, prm, grid, smem);
 }
 
-cudaError_t launch_split(kpme_plan_t P, const float* src, void* dst, int64_t count) {
+cudaError_t launch_split(kpme_plan_t P, const double* src, void* dst, int64_t count) {
   const PrecInfo& pi = P->prec;
   int grid = (int)((count + 255) / 256);
   if (grid > P->sm_count * 8) grid = P->sm_count * 8;

@@ -63,6 +63,7 @@ struct PrecInfo {
   int slices = 1;         // operand slices per value
   int n_products = 1;     // MMAs per k-step
   int elem_bytes = 4;     // bytes per stored slice element
+  bool oz = false;        // error-free fixed-point split (float32 intermediates + row maxima)
 };
 PrecInfo prec_info(int precision);
 
@@ -84,8 +85,9 @@ struct kpme_plan_s {
   double* d_qpsi = nullptr;        // <Q, Psi> for the virial
   int* d_status = nullptr;         // device status word
 
-  // meshes (float or double by precision), K^3 each
-  void* d_Q = nullptr;
+  // meshes, K^3 each: Q is float64 for every arithmetic, Phi float32 (float64 for FP64)
+  double* d_Q = nullptr;
+  float* d_Qf = nullptr;           // float32 copy of Q for the CUDA-core float32 consumers
   void* d_Phi = nullptr;
   void* d_Psi = nullptr;           // virial contraction output
   void* d_tmp1 = nullptr;          // K^3 scratch for the rank-one virial contraction
@@ -100,6 +102,9 @@ struct kpme_plan_s {
   void* d_Qs = nullptr;            // tensor path: sliced Q
   void* d_Y = nullptr;             // stage-1 output (r0 tensors)
   void* d_Z = nullptr;             // stage-2 output (one term group)
+  float* d_rmQ = nullptr;          // error-free split: row maxima of Q, Y, Z (next-stage rows)
+  float* d_rmY = nullptr;
+  float* d_rmZ = nullptr;
   int group_terms = 0;             // capacity of d_Z in terms
   kpme::JobList stage1;
   std::vector<kpme::TermGroup> groups;
@@ -126,7 +131,7 @@ namespace kpme {
 // ---- launchers implemented in the .cu files -------------------------------------------------
 
 // particles.cu
-cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, void* Q);
+cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, double* Q);
 cudaError_t launch_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
                           double* phi, double* F, double* energy, double scale_phi_extra);
 cudaError_t launch_dot(kpme_plan_t P, const void* a, const void* b, int64_t count, double* out);
@@ -161,7 +166,26 @@ struct TcArgs {
   const JobList* jobs;
 };
 cudaError_t launch_mp_tc(kpme_plan_t P, const TcArgs& a);
-cudaError_t launch_split(kpme_plan_t P, const float* src, void* dst, int64_t count);
+cudaError_t launch_split(kpme_plan_t P, const double* src, void* dst, int64_t count);
+
+// gemm_oz.cu: error-free fixed-point split (KPME_BF16X10)
+struct OzArgs {
+  const CUtensorMap* tmB;
+  const void* in;                  // float32, or float64 when in_double
+  bool in_double;
+  int64_t in_bs;
+  const float* rowmax_in;
+  int64_t rm_in_bs;
+  float* out;
+  int64_t out_bs;
+  float* rowmax_out;
+  int64_t rm_out_bs;
+  int M, N, Kr, mode;
+  const JobList* jobs;
+};
+cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a);
+cudaError_t launch_rowmax(kpme_plan_t P, const double* Q, int64_t rows, int K, float* out);
+int oz_smem_bytes(int bn, int stages);
 bool encode_tmap(kpme_plan_t P, CUtensorMap* map, const void* base, int elem_bytes, bool is_f32,
                  uint64_t dim0, uint64_t dim1, uint64_t dim2, uint32_t box0, uint32_t box1);
 int tc_smem_bytes(const PrecInfo& pi, int bn, int stages);

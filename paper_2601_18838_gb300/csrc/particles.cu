@@ -239,10 +239,12 @@ cudaError_t gather_t(kpme_plan_t P, int64_t n, const double* x, const double* q,
 
 }  // namespace
 
-cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, void* Q) {
+cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, double* Q) {
+  // The charge mesh is accumulated in float64 for every arithmetic: each mesh value is a sum
+  // of many contributions of both signs (neutral molecules), and float32 accumulation of it
+  // dominates the potential error of the float32-class paths.
   if (n <= 0) return cudaSuccess;
-  if (P->prec.fp64) return spread_t<double>(P, n, x, q, (double*)Q);
-  return spread_t<float>(P, n, x, q, (float*)Q);
+  return spread_t<double>(P, n, x, q, Q);
 }
 
 cudaError_t launch_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,

@@ -241,7 +241,9 @@ __device__ __forceinline__ float tf32_rn(float x) {
 }
 
 // Circulant matrices F[s][t][n][k] = slice s of g_t((n - k) mod K) in the requested format.
-// kind: 0 float64, 1 float32, 2 bf16 slices (round-to-nearest cascade), 3 tf32 hi/lo in float32.
+// kind: 0 float64, 1 float32, 2 bf16 slices (round-to-nearest cascade), 3 tf32 hi/lo in float32,
+// 4 fixed-point bf16 slices with one exponent per factor (every circulant row holds the same
+// values): v = 2^(e-7) sum_s d_s 2^(-8s), d_s integers in [-128, 128], 2^e >= max |g|.
 __global__ void materialize_kernel(const double* __restrict__ gen, int count, int K, int slices, int kind,
                                    void* __restrict__ dst) {
   const int64_t per = (int64_t)K * K;
@@ -263,6 +265,17 @@ __global__ void materialize_kernel(const double* __restrict__ gen, int count, in
         const __nv_bfloat16 h = __double2bfloat16(r);
         ((__nv_bfloat16*)dst)[s * total + idx] = h;
         r -= (double)__bfloat162float(h);
+      }
+    } else if (kind == 4) {
+      double gmax = 0.0;
+      for (int j = 0; j < K; ++j) gmax = fmax(gmax, fabs(gen[(int64_t)t * K + j]));
+      int e = 0;
+      frexp(gmax, &e);
+      double u = ldexp(v, 7 - e);
+      for (int s = 0; s < slices; ++s) {
+        const double dg = rint(u);
+        u = (u - dg) * 256.0;
+        ((__nv_bfloat16*)dst)[s * total + idx] = __double2bfloat16(ldexp(dg, e - 7 - 8 * s));
       }
     } else {
       const float hi = tf32_rn((float)v);

@@ -11,7 +11,7 @@ pytestmark = pytest.mark.gpu
 
 # tolerances on relative RMS error against the float64 oracle (potentials, forces)
 TOL = {"fp64": (1e-12, 1e-11), "fp32": (5e-6, 2e-5), "tf32x3": (5e-6, 3e-5), "bf16x6": (1e-6, 1e-5),
-       "bf16x3": (1e-4, 5e-4), "tf32": (2e-2, 5e-2), "bf16": (5e-2, 2e-1)}
+       "bf16x3": (1e-4, 5e-4), "tf32": (2e-2, 5e-2), "bf16": (5e-2, 2e-1), "bf16x10": (1e-6, 1e-5)}
 
 
 @pytest.fixture(scope="module")
@@ -73,7 +73,7 @@ def test_skp_build_matches_oracle(torch):
     assert rel(Phi_gpu, Phi_ref) < 4 * s.skp_tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x6", "bf16x3", "tf32", "bf16"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x6", "bf16x3", "tf32", "bf16", "bf16x10"])
 def test_apply_with_oracle_factors(torch, prec):
     s = wl.small()
     o = _oracle_skp(s)
@@ -100,7 +100,7 @@ def test_gather(torch, prec):
     assert rel(host(phi), phi_r) < tol and rel(host(F), F_r) < tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x6", "bf16x3"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x6", "bf16x3", "bf16x10"])
 def test_energy_forces_small(torch, prec):
     s = wl.small()
     o = _oracle_skp(s)
@@ -118,6 +118,7 @@ def test_energy_forces_small(torch, prec):
 
 @pytest.mark.parametrize("prec", [
     "fp64",
+    "bf16x10",
     pytest.param("bf16x6", marks=pytest.mark.xfail(
         reason="floating bf16 slices accumulate in the tensor core's float32 accumulator; measured "
                "phi 4.8e-6 / F 1.2e-5 on this box, above the 1e-6 / 1e-5 bar", strict=False)),
@@ -135,6 +136,21 @@ def test_energy_forces_water_box(torch, prec):
     print(f"water {prec}: phi {e_phi:.2e} F {e_f:.2e}")
     tp, tf = TOL[prec]
     assert e_phi < tp and e_f < tf
+
+
+@pytest.mark.parametrize("K,order,n,L", [(32, 4, 1001, 18.0), (48, 4, 2050, 30.0), (96, 6, 4003, 70.0)])
+def test_error_free_split_sizes(torch, K, order, n, L):
+    # ragged particle counts, K not a multiple of 32 (row maxima across warp boundaries),
+    # several 64-wide reduction chunks (K = 96)
+    s = wl.random_system(n, L, K, order, seed=K + n)
+    o = _oracle_skp(s)
+    ref = skp.reciprocal(s.x, s.q, s.box, K, order, s.beta, s.skp_tol, skp=o)
+    plan = _plan(s, "bf16x10")
+    plan.set_skp(*skp.generators(o))
+    out = plan.energy_forces(dev(torch, s.x), dev(torch, s.q))
+    e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
+    print(f"bf16x10 K={K}: phi {e_phi:.2e} F {e_f:.2e}")
+    assert e_phi < 1e-6 and e_f < 1e-5
 
 
 def test_potential_targets_differ_from_sources(torch):
