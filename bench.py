@@ -172,9 +172,9 @@ def main(argv=None):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=dev)
         pg = dist
-    import __graft_entry__
+    from paper_2601_18838_gb300 import build as _build
     if rank == 0:
-        __graft_entry__.build()
+        _build.build()
     if pg:
         pg.barrier()
     from paper_2601_18838_gb300 import Plan

@@ -91,8 +91,8 @@ void release_skp_buffers(kpme_plan_t P) {
   drop(P->d_Qs);
   drop(P->d_Y);
   drop(P->d_Z);
-  dfree(P->d_rmQ);
-  dfree(P->d_rmY);
+  dfree(P->d_Qsl);
+  dfree(P->d_Ysl);
   dfree(P->d_rmZ);
   free_joblist(P->stage1);
   for (auto& g : P->groups) {
@@ -132,7 +132,7 @@ void choose_tc_tiles(kpme_plan_t P) {
 
 int64_t group_budget_bytes() {
   const char* e = getenv("KPME_GROUP_MB");
-  int64_t mb = e ? atoll(e) : 64;
+  int64_t mb = e ? atoll(e) : 256;
   if (mb < 1) mb = 1;
   return mb << 20;
 }
@@ -202,16 +202,20 @@ kpme_status_t install_skp(kpme_plan_t P) {
   // intermediates (the error-free split keeps float32 values and per-row maxima)
   const int islices = pi.oz ? 1 : slices;
   const size_t ieb = pi.oz ? sizeof(float) : eb;
-  int G = (int)std::max<int64_t>(1, group_budget_bytes() / std::max<int64_t>(1, (int64_t)islices * k3 * (int64_t)ieb));
+  // terms per group: as many as fit the budget (L2-sized by default), but at least 16 so that
+  // large meshes do not degenerate into one launch pair per term
+  int G = (int)std::max<int64_t>(16, group_budget_bytes() / std::max<int64_t>(1, (int64_t)islices * k3 * (int64_t)ieb));
   G = std::min(G, R);
   P->group_terms = G;
   if (pi.tensor && !pi.oz && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_Y, (size_t)islices * r0 * k3 * ieb)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_Z, (size_t)islices * G * k3 * ieb)) != KPME_OK) return st;
   if (pi.oz) {
+    // Q and Y are read by several jobs each: they are cut into fixed-point slices once and
+    // fed by TMA; Z is read once and is sliced on the fly from float32 with its row maxima
     const size_t k2 = (size_t)K * K;
-    if ((st = dalloc(P, (void**)&P->d_rmQ, k2 * sizeof(float))) != KPME_OK) return st;
-    if ((st = dalloc(P, (void**)&P->d_rmY, (size_t)r0 * k2 * sizeof(float))) != KPME_OK) return st;
+    if ((st = dalloc(P, &P->d_Qsl, (size_t)4 * k3 * sizeof(__nv_bfloat16))) != KPME_OK) return st;
+    if ((st = dalloc(P, &P->d_Ysl, (size_t)4 * r0 * k3 * sizeof(__nv_bfloat16))) != KPME_OK) return st;
     if ((st = dalloc(P, (void**)&P->d_rmZ, (size_t)G * k2 * sizeof(float))) != KPME_OK) return st;
   }
 
@@ -252,8 +256,9 @@ kpme_status_t install_skp(kpme_plan_t P) {
     const bool f32 = pi.tf32;
     const uint32_t box0 = 128 / pi.elem_bytes;
     const uint64_t KK = (uint64_t)K * K;
-    bool ok = (pi.oz ||
-               (encode_tmap(P, &P->tm_Q, P->d_Qs, pi.elem_bytes, f32, K, KK, (uint64_t)slices, box0, 128) &&
+    bool ok = (pi.oz ? (encode_tmap(P, &P->tm_Q, P->d_Qsl, 2, false, K, KK, 4, 64, 128) &&
+                        encode_tmap(P, &P->tm_Y, P->d_Ysl, 2, false, K, KK, (uint64_t)4 * r0, 64, 128))
+                     : (encode_tmap(P, &P->tm_Q, P->d_Qs, pi.elem_bytes, f32, K, KK, (uint64_t)slices, box0, 128) &&
                 encode_tmap(P, &P->tm_Y, P->d_Y, pi.elem_bytes, f32, K, KK, (uint64_t)slices * r0, box0, 128) &&
                 encode_tmap(P, &P->tm_Z, P->d_Z, pi.elem_bytes, f32, K, KK, (uint64_t)slices * G, box0, 128))) &&
               encode_tmap(P, &P->tm_f3, P->d_fac3, pi.elem_bytes, f32, K, (uint64_t)r0 * K, slices, box0, P->tc_bn) &&
@@ -345,25 +350,27 @@ kpme_status_t contract(kpme_plan_t P, const double* Q, void* Phi) {
     const int64_t k2 = (int64_t)K * K;
     {
       StepScope sc(P, STEP_SPLIT, 1);
-      KPME_CUDA_TRY(P, launch_rowmax(P, Q, k2, K, P->d_rmQ));
+      KPME_CUDA_TRY(P, launch_slice_rows(P, Q, true, k2, 1, K, P->d_Qsl));
     }
     {
-      StepScope sc(P, STEP_SKP1, 1);
-      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmY, 0, (size_t)S.r0 * k2 * sizeof(float), P->stream));
-      OzArgs a{&P->tm_f3, Q, true, 0, P->d_rmQ, 0, (float*)P->d_Y, k3, P->d_rmY, k2, M, K, K, 0, &P->stage1};
+      StepScope sc(P, STEP_SKP1, 2);
+      OzArgs a{&P->tm_f3, &P->tm_Q, 1, nullptr, false, 0, nullptr, 0, (float*)P->d_Y, k3, nullptr, 0, M, K, K, 0,
+               &P->stage1};
       KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+      KPME_CUDA_TRY(P, launch_slice_rows(P, P->d_Y, false, k2, S.r0, K, P->d_Ysl));
     }
     KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
     for (const auto& g : P->groups) {
       {
         StepScope sc(P, STEP_SKP2, 1);
         KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
-        OzArgs a{&P->tm_f2, P->d_Y, false, k3, P->d_rmY, k2, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K, K, 0,
-                 &g.stage2};
+        OzArgs a{&P->tm_f2, &P->tm_Y, S.r0, nullptr, false, 0, nullptr, 0, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K, K,
+                 0, &g.stage2};
         KPME_CUDA_TRY(P, launch_mp_oz(P, a));
       }
       StepScope sc(P, STEP_SKP3, 1);
-      OzArgs a{&P->tm_f1, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1, &g.stage3};
+      OzArgs a{&P->tm_f1, nullptr, 0, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1,
+               &g.stage3};
       KPME_CUDA_TRY(P, launch_mp_oz(P, a));
     }
     return KPME_OK;

@@ -11,22 +11,18 @@
 // accumulation of them is exact whatever its rounding.  The leading products go to an
 // accumulator D0, the nine products with slice sum 1..3 (at most 2^-8 of D0) to D1.
 //
-// The input rows come from float32 intermediates; converter warps slice them on the fly
-// with the per-row maximum that the producing stage recorded (atomicMax over the rows of
-// the consuming stage).  Factors are sliced once at plan time and streamed by TMA.
-//
-// CTA = 192 threads, one 128 x BN output tile, the pairs of one job in sequence:
-//   warp 0 lane 0  : TMA producer of the four factor slices (BN rows x 128 B per chunk)
-//   warp 1         : TMEM allocation; lane 0 issues the MMAs
-//   warps 2..5     : converters (row r = 32 (warp % 4) + lane) and epilogue; per pair they
-//                    drain D0 + D1 from TMEM (double buffered) into float32 registers.
+// The input rows come from float32 intermediates (or the float32 hi/lo split of the float64
+// charge mesh); converter warps slice them on the fly with the per-row maximum that the
+// producing stage recorded (atomicMax over the rows of the consuming stage).  Factors are
+// sliced once at plan time and streamed by TMA.  TMEM holds two (D0, D1) pairs so that the
+// epilogue drains one Kronecker term while the MMAs of the next run.
 // All waits are bounded; a wait that runs out raises the device status word.
 #include "kpme_internal.cuh"
 
 namespace kpme {
 namespace {
 
-constexpr int kThreads = 192;
+constexpr int kThreads = 320;
 constexpr int kBM = 128;
 constexpr int kSlices = 4;
 constexpr int kProducts = 10;
@@ -47,6 +43,8 @@ struct OzParams {
   int64_t rm_out_bs;
   const int* start;
   const int2* pairs;
+  int n_jobs;
+  int nbatch_a;      // batches per slice plane of the pre-sliced A (TMA mode)
   int* status;
 };
 
@@ -136,33 +134,63 @@ __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&h);
 }
 
+// 2^k as a float32 (exact): a bit pattern for normal exponents, ldexpf outside.
+__device__ __forceinline__ float pow2f(int k) {
+  return (k >= -126 && k <= 127) ? __int_as_float((127 + k) << 23) : ldexpf(1.0f, k);
+}
+
 // Four fixed-point digits of 8 values scaled by 2^(7 - e): writes slices s = 0..3 of one
 // 16-byte group (8 consecutive k) as packed bf16, each slice carrying its own power of two.
-// Every step (scaling by a power of two, rint, subtraction of the digit, scaling by 2^8) is
-// exact in the input's floating type.
-template <typename T>
-__device__ __forceinline__ void slice8(const T (&v)[8], int e, uint4 (&o)[kSlices]) {
-  T t[8];
+// Input: one float32 per value, or a float32 hi/lo pair (hi + lo = the float64 value to
+// about 2^-48).  Scaling by a power of two, rint and the subtraction of the digit are exact
+// in float32; the lo part joins the first remainder (rounded at 2^-25 of the digit scale,
+// below the last digit's resolution).
+template <typename TIN>
+__device__ __forceinline__ void slice8(const TIN* v, int e, uint4 (&o)[kSlices]) {
+  const float up = pow2f(7 - e);
+  float t[8];
+  float d[kSlices][8];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) t[i] = ldexp(v[i], 7 - e);
+  for (int i = 0; i < 8; ++i) {
+    float th, tl = 0.0f;
+    if constexpr (sizeof(TIN) == 8) {
+      th = v[i].x * up;
+      tl = v[i].y * up;
+    } else {
+      th = v[i] * up;
+    }
+    const float d0 = rintf(th);
+    d[0][i] = d0;
+    t[i] = ((th - d0) + tl) * 256.0f;
+  }
 #pragma unroll
-  for (int s = 0; s < kSlices; ++s) {
-    float d[8];
+  for (int s = 1; s < kSlices; ++s) {
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const T di = rint(t[i]);
-      t[i] = (t[i] - di) * T(256);
-      d[i] = ldexpf((float)di, e - 7 - 8 * s);
+      const float di = rintf(t[i]);
+      t[i] = (t[i] - di) * 256.0f;
+      d[s][i] = di;
     }
-    o[s].x = pack_bf16(d[0], d[1]);
-    o[s].y = pack_bf16(d[2], d[3]);
-    o[s].z = pack_bf16(d[4], d[5]);
-    o[s].w = pack_bf16(d[6], d[7]);
+  }
+#pragma unroll
+  for (int s = 0; s < kSlices; ++s) {
+    const float dn = pow2f(e - 7 - 8 * s);
+    o[s].x = pack_bf16(d[s][0] * dn, d[s][1] * dn);
+    o[s].y = pack_bf16(d[s][2] * dn, d[s][3] * dn);
+    o[s].z = pack_bf16(d[s][4] * dn, d[s][5] * dn);
+    o[s].w = pack_bf16(d[s][6] * dn, d[s][7] * dn);
   }
 }
 
-template <int BN, typename TIN>
-__global__ void __launch_bounds__(kThreads, 1) mp_oz_kernel(const __grid_constant__ CUtensorMap tmB, OzParams prm) {
+// Persistent CTA: 10 warps, work items (m-tile, n-tile, job) strided by gridDim.x, every role
+// walking the same sequence of (item, pair, 64-wide chunk) so the shared ring counters agree.
+//   warp 0      : TMA of the four factor slices per chunk
+//   warp 1      : TMEM allocation; lane 0 issues 10 products per 16-wide k step
+//   warps 2..5  : converters, one operand row per thread
+//   warps 6..9  : epilogue, TMEM lanes 32 (warp % 4) .. + 31, one output row per thread
+template <int BN, typename TIN, bool A_TMA>
+__global__ void __launch_bounds__(kThreads, 1)
+    mp_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams prm) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   constexpr int kBSlice = BN * 128;
@@ -176,11 +204,14 @@ __global__ void __launch_bounds__(kThreads, 1) mp_oz_kernel(const __grid_constan
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * BN, job = blockIdx.z;
+  const int m_tiles = (prm.M + kBM - 1) / kBM;
+  const int n_tiles = prm.N / BN;
+  const int n_items = m_tiles * n_tiles * prm.n_jobs;
+  const int kchunks = (prm.Kr + kChunk - 1) / kChunk;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(&full_a[s], 128);
+      mbar_init(&full_a[s], A_TMA ? 1 : 128);
       mbar_init(&full_b[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -203,165 +234,212 @@ __global__ void __launch_bounds__(kThreads, 1) mp_oz_kernel(const __grid_constan
   fence_after();
   const uint32_t tmem = *taddr_slot;
 
-  const int p0 = prm.start[job], np = prm.start[job + 1] - p0;
-  const int kchunks = (prm.Kr + kChunk - 1) / kChunk;
-  const int total = np * kchunks;
+  auto decode = [&](int w, int& m0, int& n0, int& job) {
+    const int per_job = m_tiles * n_tiles;
+    job = w / per_job;
+    const int rem = w - job * per_job;
+    n0 = (rem / m_tiles) * BN;
+    m0 = (rem % m_tiles) * kBM;
+  };
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- factor slices by TMA ----------------
-      for (int it = 0; it < total; ++it) {
-        const int s = it % S;
-        const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) break;
-        const int2 pr = prm.pairs[p0 + it / kchunks];
-        const int kc = (it % kchunks) * kChunk;
-        uint8_t* sb = smem + s * prm.stage_bytes + kSlices * kASlice;
-        mbar_expect_tx(&full_b[s], (uint32_t)(kSlices * kBSlice));
+      int it = 0;
+      for (int w = blockIdx.x; w < n_items && !*abort_flag; w += gridDim.x) {
+        int m0, n0, job;
+        decode(w, m0, n0, job);
+        const int p0 = prm.start[job], p1 = prm.start[job + 1];
+        for (int p = p0; p < p1; ++p) {
+          const int2 pr = prm.pairs[p];
+          for (int c = 0; c < kchunks; ++c, ++it) {
+            const int s = it % S;
+            const uint32_t ph = (uint32_t)(it / S) & 1u;
+            if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) break;
+            uint8_t* sa = smem + s * prm.stage_bytes;
+            uint8_t* sb = sa + kSlices * kASlice;
+            if constexpr (A_TMA) {
+              mbar_expect_tx(&full_a[s], (uint32_t)(kSlices * kASlice));
 #pragma unroll
-        for (int b = 0; b < kSlices; ++b) tma_load_3d(sb + b * kBSlice, &tmB, &full_b[s], kc, pr.y * prm.N + n0, b);
+              for (int a = 0; a < kSlices; ++a)
+                tma_load_3d(sa + a * kASlice, &tmA, &full_a[s], c * kChunk, m0, a * prm.nbatch_a + pr.x);
+            }
+            mbar_expect_tx(&full_b[s], (uint32_t)(kSlices * kBSlice));
+#pragma unroll
+            for (int b = 0; b < kSlices; ++b)
+              tma_load_3d(sb + b * kBSlice, &tmB, &full_b[s], c * kChunk, pr.y * prm.N + n0, b);
+          }
+        }
       }
     }
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issuer ----------------
       const uint32_t id = idesc_bf16(kBM, BN);
-      for (int pl = 0; pl < np && !*abort_flag; ++pl) {
-        const int buf = pl & 1;
-        if (pl >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((pl >> 1) - 1) & 1u, abort_flag, prm.status)) break;
-        fence_after();
-        const uint32_t d0 = tmem + (uint32_t)(buf * 2 * BN), d1 = d0 + BN;
-        bool ok = true;
-        for (int c = 0; c < kchunks; ++c) {
-          const int it = pl * kchunks + c;
+      int it = 0, pc = 0;
+      for (int w = blockIdx.x; w < n_items && !*abort_flag; w += gridDim.x) {
+        int m0, n0, job;
+        decode(w, m0, n0, job);
+        const int np = prm.start[job + 1] - prm.start[job];
+        for (int pl = 0; pl < np && !*abort_flag; ++pl, ++pc) {
+          const int buf = pc & 1;
+          if (pc >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((pc >> 1) - 1) & 1u, abort_flag, prm.status)) break;
+          fence_after();
+          const uint32_t d0 = tmem + (uint32_t)(buf * 2 * BN), d1 = d0 + BN;
+          for (int c = 0; c < kchunks; ++c, ++it) {
+            const int s = it % S;
+            const uint32_t ph = (uint32_t)(it / S) & 1u;
+            if (!mbar_wait(&full_a[s], ph, abort_flag, prm.status) || !mbar_wait(&full_b[s], ph, abort_flag, prm.status))
+              break;
+            fence_after();
+            int ksteps = (prm.Kr - c * kChunk + 15) / 16;
+            ksteps = ksteps > 4 ? 4 : ksteps;
+            const uint32_t sa = smem_u32(smem + s * prm.stage_bytes);
+            const uint32_t sb = sa + kSlices * kASlice;
+            for (int kk = 0; kk < ksteps; ++kk) {
+              const bool first = (c == 0 && kk == 0);
+#pragma unroll
+              for (int p = 0; p < kProducts; ++p) {
+                const uint64_t da = sdesc(sa + pa(p) * kASlice + kk * 32);
+                const uint64_t db = sdesc(sb + pb(p) * kBSlice + kk * 32);
+                if (p == 0)
+                  mma_bf16(d0, da, db, id, first ? 0u : 1u);
+                else
+                  mma_bf16(d1, da, db, id, (first && p == 1) ? 0u : 1u);
+              }
+            }
+            mma_commit(&empty[s]);
+          }
+          mma_commit(&acc_full[buf]);
+        }
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- converters (operand rows sliced on the fly) ----------------
+    if constexpr (A_TMA) {
+      // the A slices come pre-cut by TMA: nothing to convert
+    } else {
+    const int r = 32 * (warp - 2) + lane;
+    int it = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+      int m0, n0, job;
+      decode(w, m0, n0, job);
+      const int row = m0 + r;
+      const bool valid = row < prm.M;
+      const int p0 = prm.start[job], p1 = prm.start[job + 1];
+      for (int p = p0; p < p1 && ok; ++p) {
+        const int2 pr = prm.pairs[p];
+        const TIN* rowp = reinterpret_cast<const TIN*>(prm.in) + (int64_t)pr.x * prm.in_bs + (int64_t)row * prm.Kr;
+        int e = 0;
+        if (valid) frexpf(prm.rowmax_in[(int64_t)pr.x * prm.rm_in_bs + row], &e);
+        for (int c = 0; c < kchunks; ++c, ++it) {
           const int s = it % S;
           const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (!mbar_wait(&full_a[s], ph, abort_flag, prm.status) || !mbar_wait(&full_b[s], ph, abort_flag, prm.status)) {
+          if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) {
             ok = false;
             break;
           }
-          fence_after();
-          int ksteps = (prm.Kr - c * kChunk + 15) / 16;
-          ksteps = ksteps > 4 ? 4 : ksteps;
-          const uint32_t sa = smem_u32(smem + s * prm.stage_bytes);
-          const uint32_t sb = sa + kSlices * kASlice;
-          for (int kk = 0; kk < ksteps; ++kk) {
-            const bool first = (c == 0 && kk == 0);
+          uint8_t* sa = smem + s * prm.stage_bytes;
+          const int kc = c * kChunk;
+          // all loads of a pass are issued before any use, so one memory latency per pass
+          constexpr int kPasses = sizeof(TIN) == 8 ? 2 : 1;
+          constexpr int kGroups = 8 / kPasses;
 #pragma unroll
-            for (int p = 0; p < kProducts; ++p) {
-              const uint64_t da = sdesc(sa + pa(p) * kASlice + kk * 32);
-              const uint64_t db = sdesc(sb + pb(p) * kBSlice + kk * 32);
-              if (p == 0)
-                mma_bf16(d0, da, db, id, first ? 0u : 1u);
-              else
-                mma_bf16(d1, da, db, id, (first && p == 1) ? 0u : 1u);
+          for (int h = 0; h < kPasses; ++h) {
+            TIN v[kGroups * 8];
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) {
+              const int k = kc + 8 * (h * kGroups + g);
+              if (valid && k < prm.Kr) {
+#pragma unroll
+                for (int i = 0; i < 8; i += 16 / (int)sizeof(TIN)) {
+                  const float4 x = *reinterpret_cast<const float4*>(rowp + k + i);
+                  if constexpr (sizeof(TIN) == 4) {
+                    v[8 * g + i] = x.x; v[8 * g + i + 1] = x.y; v[8 * g + i + 2] = x.z; v[8 * g + i + 3] = x.w;
+                  } else {
+                    v[8 * g + i] = make_float2(x.x, x.y);
+                    v[8 * g + i + 1] = make_float2(x.z, x.w);
+                  }
+                }
+              } else {
+#pragma unroll
+                for (int i = 0; i < 8; ++i) v[8 * g + i] = TIN{};
+              }
+            }
+#pragma unroll
+            for (int g = 0; g < kGroups; ++g) {
+              const int j = h * kGroups + g;
+              uint4 o[kSlices];
+              slice8(v + 8 * g, e, o);
+              const int off = r * 128 + ((j ^ (r & 7)) << 4);
+#pragma unroll
+              for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint4*>(sa + sl * kASlice + off) = o[sl];
             }
           }
-          mma_commit(&empty[s]);
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_arrive(&full_a[s]);
         }
-        if (!ok) break;
-        mma_commit(&acc_full[buf]);
       }
     }
+    }
   } else {
-    // ---------------- converters + epilogue ----------------
+    // ---------------- epilogue ----------------
     const int r = 32 * (warp & 3) + lane;
-    const int row = m0 + r;
-    const bool valid = row < prm.M;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
-    float acc[BN];
-#pragma unroll
-    for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
-
-    auto drain = [&](int pl) -> bool {
-      const int buf = pl & 1;
-      if (!mbar_wait(&acc_full[buf], (uint32_t)(pl >> 1) & 1u, abort_flag, prm.status)) return false;
-      fence_after();
-#pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 16) {
-        uint32_t a0[16], a1[16];
-        tmem_ld16(lane_base + (uint32_t)(buf * 2 * BN + c0), a0);
-        tmem_ld16(lane_base + (uint32_t)(buf * 2 * BN + BN + c0), a1);
-        tmem_wait_ld();
-#pragma unroll
-        for (int i = 0; i < 16; ++i) acc[c0 + i] += __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
-      }
-      fence_before();
-      mbar_arrive(&acc_empty[buf]);
-      return true;
-    };
-
+    int pc = 0;
     bool ok = true;
-    for (int pl = 0; pl < np && ok; ++pl) {
-      const int2 pr = prm.pairs[p0 + pl];
-      const TIN* rowp = reinterpret_cast<const TIN*>(prm.in) + (int64_t)pr.x * prm.in_bs + (int64_t)row * prm.Kr;
-      int e = 0;
-      if (valid) frexpf(prm.rowmax_in[(int64_t)pr.x * prm.rm_in_bs + row], &e);
-      for (int c = 0; c < kchunks; ++c) {
-        const int it = pl * kchunks + c;
-        const int s = it % S;
-        const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) {
+    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+      int m0, n0, job;
+      decode(w, m0, n0, job);
+      const int row = m0 + r;
+      const int np = prm.start[job + 1] - prm.start[job];
+      float acc[BN];
+#pragma unroll
+      for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
+      for (int pl = 0; pl < np; ++pl, ++pc) {
+        const int buf = pc & 1;
+        if (!mbar_wait(&acc_full[buf], (uint32_t)(pc >> 1) & 1u, abort_flag, prm.status)) {
           ok = false;
           break;
         }
-        uint8_t* sa = smem + s * prm.stage_bytes;
-        const int kc = c * kChunk;
+        fence_after();
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          TIN v[8];
-          const int k = kc + 8 * j;
-          if (valid && k < prm.Kr) {
-            if constexpr (sizeof(TIN) == 4) {
-              const float4 x0 = *reinterpret_cast<const float4*>(rowp + k);
-              const float4 x1 = *reinterpret_cast<const float4*>(rowp + k + 4);
-              v[0] = x0.x; v[1] = x0.y; v[2] = x0.z; v[3] = x0.w;
-              v[4] = x1.x; v[5] = x1.y; v[6] = x1.z; v[7] = x1.w;
-            } else {
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+          uint32_t a0[16], a1[16];
+          tmem_ld16(lane_base + (uint32_t)(buf * 2 * BN + c0), a0);
+          tmem_ld16(lane_base + (uint32_t)(buf * 2 * BN + BN + c0), a1);
+          tmem_wait_ld();
 #pragma unroll
-              for (int i = 0; i < 8; i += 2) {
-                const double2 x = *reinterpret_cast<const double2*>(rowp + k + i);
-                v[i] = x.x;
-                v[i + 1] = x.y;
-              }
+          for (int i = 0; i < 16; ++i) acc[c0 + i] += __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
+        }
+        fence_before();
+        mbar_arrive(&acc_empty[buf]);
+      }
+      if (!ok || *abort_flag || row >= prm.M) continue;
+      if (prm.mode == 1) {
+        float* o = prm.out + (int64_t)n0 * prm.M + row;
+#pragma unroll
+        for (int c = 0; c < BN; ++c) atomicAdd(o + (int64_t)c * prm.M, acc[c]);
+      } else {
+        float* o = prm.out + (int64_t)job * prm.out_bs + (int64_t)n0 * prm.M + row;
+#pragma unroll
+        for (int c = 0; c < BN; ++c) o[(int64_t)c * prm.M] = acc[c];
+        if (prm.rowmax_out != nullptr) {
+          // row maxima of the consuming stage: its rows are (n, row / K) with n the output column
+          const int K = prm.Kr;
+          const int64_t rows_next = prm.M / K;
+          unsigned int* dst = reinterpret_cast<unsigned int*>(prm.rowmax_out + (int64_t)job * prm.rm_out_bs) +
+                              (int64_t)n0 * rows_next + row / K;
+          if ((K % 32) == 0) {
+#pragma unroll
+            for (int c = 0; c < BN; ++c) {
+              const unsigned int mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(acc[c])));
+              if (lane == 0) atomicMax(dst + (int64_t)c * rows_next, mx);
             }
           } else {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) v[i] = TIN(0);
-          }
-          uint4 o[kSlices];
-          slice8(v, e, o);
-          const int off = r * 128 + ((j ^ (r & 7)) << 4);
-#pragma unroll
-          for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint4*>(sa + sl * kASlice + off) = o[sl];
-        }
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        mbar_arrive(&full_a[s]);
-      }
-      if (ok && pl > 0) ok = drain(pl - 1);
-    }
-    if (ok && np > 0) ok = drain(np - 1);
-    if (ok && !*abort_flag && valid) {
-      if (prm.mode == 1) {
-#pragma unroll
-        for (int c = 0; c < BN; ++c) atomicAdd(prm.out + (int64_t)(n0 + c) * prm.M + row, acc[c]);
-      } else {
-        float* o = prm.out + (int64_t)job * prm.out_bs;
-        const int K = prm.Kr;
-        const bool warp_row = (K % 32) == 0;
-        const int64_t rows_next = prm.M / K;
-#pragma unroll
-        for (int c = 0; c < BN; ++c) {
-          const int n = n0 + c;
-          o[(int64_t)n * prm.M + row] = acc[c];
-          unsigned int mx = __float_as_uint(fabsf(acc[c]));
-          unsigned int* dst = reinterpret_cast<unsigned int*>(prm.rowmax_out + (int64_t)job * prm.rm_out_bs) +
-                              (int64_t)n * rows_next + row / K;
-          if (warp_row) {
-            mx = __reduce_max_sync(0xffffffffu, mx);
-            if (lane == 0) atomicMax(dst, mx);
-          } else {
-            atomicMax(dst, mx);
+            for (int c = 0; c < BN; ++c) atomicMax(dst + (int64_t)c * rows_next, __float_as_uint(fabsf(acc[c])));
           }
         }
       }
@@ -375,27 +453,70 @@ __global__ void __launch_bounds__(kThreads, 1) mp_oz_kernel(const __grid_constan
   }
 }
 
-// max_k |Q[m][k]| for the K^2 rows of the float64 charge mesh (one warp per row).  The
-// float32 result rounds to nearest, so its frexp exponent still bounds the row (a power of
-// two is representable, so rounding never crosses it).
-__global__ void rowmax_kernel(const double* __restrict__ Q, int64_t rows, int K, float* __restrict__ out) {
+// Row slicer: every row of K contiguous values (float32, or float64 read as a float32 hi/lo
+// pair) is cut into four fixed-point bf16 slices relative to the power of two above its own
+// maximum; slice s of row r of batch b goes to out[(s * nbatch + b) * rows + r][k].  One warp
+// per row.
+template <typename TIN>
+__global__ void slice_rows_kernel(const TIN* __restrict__ in, int64_t rows_total, int64_t rows_per_batch, int nbatch,
+                                  int K, __nv_bfloat16* __restrict__ out) {
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
-  if (w >= rows) return;
-  double m = 0.0;
-  for (int k = lane; k < K; k += 32) m = fmax(m, fabs(Q[w * K + k]));
+  if (w >= rows_total) return;
+  const TIN* row = in + w * K;
+  float m = 0.0f;
+  for (int k = lane; k < K; k += 32) {
+    if constexpr (sizeof(TIN) == 8) {
+      m = fmaxf(m, fabsf((float)row[k]));
+    } else {
+      m = fmaxf(m, fabsf(row[k]));
+    }
+  }
+  // float32 of a float64 value rounds to nearest: the exponent bound still holds
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  if (lane == 0) out[w] = (float)m;
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  int e = 0;
+  frexpf(m, &e);
+  const float up = pow2f(7 - e);
+  const int64_t b = w / rows_per_batch, r = w - b * rows_per_batch;
+  const int64_t plane = (int64_t)nbatch * rows_per_batch * K;
+  __nv_bfloat16* o = out + (b * rows_per_batch + r) * K;
+  for (int k = lane; k < K; k += 32) {
+    float th, tl = 0.0f;
+    if constexpr (sizeof(TIN) == 8) {
+      const double x = row[k];
+      const float h = (float)x;
+      th = h * up;
+      tl = (float)(x - (double)h) * up;
+    } else {
+      th = row[k] * up;
+    }
+    float d = rintf(th);
+    float t = ((th - d) + tl) * 256.0f;
+    o[k] = __float2bfloat16_rn(d * pow2f(e - 7));
+#pragma unroll
+    for (int s = 1; s < kSlices; ++s) {
+      d = rintf(t);
+      t = (t - d) * 256.0f;
+      o[s * plane + k] = __float2bfloat16_rn(d * pow2f(e - 7 - 8 * s));
+    }
+  }
 }
 
-template <int BN, typename TIN>
-cudaError_t launch_bn(cudaStream_t st, const CUtensorMap* tmB, const OzParams& prm, dim3 grid, int smem) {
-  auto kern = mp_oz_kernel<BN, TIN>;
+template <int BN, typename TIN, bool A_TMA>
+cudaError_t launch_bn(cudaStream_t st, const CUtensorMap* tmA, const CUtensorMap* tmB, const OzParams& prm, dim3 grid,
+                      int smem) {
+  auto kern = mp_oz_kernel<BN, TIN, A_TMA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, smem, st>>>(*tmB, prm);
+  kern<<<grid, kThreads, smem, st>>>(*tmA, *tmB, prm);
   return cudaGetLastError();
+}
+
+template <int BN>
+cudaError_t launch_mode(const OzArgs& a, cudaStream_t st, const OzParams& prm, dim3 grid, int smem) {
+  if (a.tmA) return launch_bn<BN, float, true>(st, a.tmA, a.tmB, prm, grid, smem);
+  return launch_bn<BN, float, false>(st, a.tmB, a.tmB, prm, grid, smem);
 }
 
 }  // namespace
@@ -424,31 +545,32 @@ cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a) {
   prm.rm_out_bs = a.rm_out_bs;
   prm.start = a.jobs->d_start;
   prm.pairs = a.jobs->d_pairs;
+  prm.n_jobs = a.jobs->n_jobs;
+  prm.nbatch_a = a.nbatch_a;
   prm.status = P->d_status;
   const int smem = oz_smem_bytes(P->tc_bn, P->tc_stages);
-  dim3 grid((a.M + kBM - 1) / kBM, a.N / P->tc_bn, a.jobs->n_jobs);
-  if (a.in_double) {
-    switch (P->tc_bn) {
-      case 32: return launch_bn<32, double>(P->stream, a.tmB, prm, grid, smem);
-      case 48: return launch_bn<48, double>(P->stream, a.tmB, prm, grid, smem);
-      case 64: return launch_bn<64, double>(P->stream, a.tmB, prm, grid, smem);
-      case 96: return launch_bn<96, double>(P->stream, a.tmB, prm, grid, smem);
-      default: return cudaErrorInvalidValue;
-    }
-  }
+  const int items = ((a.M + kBM - 1) / kBM) * (a.N / P->tc_bn) * a.jobs->n_jobs;
+  dim3 grid(items < P->sm_count ? items : P->sm_count);
   switch (P->tc_bn) {
-    case 32: return launch_bn<32, float>(P->stream, a.tmB, prm, grid, smem);
-    case 48: return launch_bn<48, float>(P->stream, a.tmB, prm, grid, smem);
-    case 64: return launch_bn<64, float>(P->stream, a.tmB, prm, grid, smem);
-    case 96: return launch_bn<96, float>(P->stream, a.tmB, prm, grid, smem);
+    case 32: return launch_mode<32>(a, P->stream, prm, grid, smem);
+    case 48: return launch_mode<48>(a, P->stream, prm, grid, smem);
+    case 64: return launch_mode<64>(a, P->stream, prm, grid, smem);
+    case 96: return launch_mode<96>(a, P->stream, prm, grid, smem);
     default: return cudaErrorInvalidValue;
   }
 }
 
-cudaError_t launch_rowmax(kpme_plan_t P, const double* Q, int64_t rows, int K, float* out) {
+cudaError_t launch_slice_rows(kpme_plan_t P, const void* in, bool in_double, int64_t rows_per_batch, int nbatch,
+                              int K, void* out) {
   const int threads = 256;
+  const int64_t rows = rows_per_batch * nbatch;
   const int64_t blocks = (rows * 32 + threads - 1) / threads;
-  rowmax_kernel<<<(unsigned)blocks, threads, 0, P->stream>>>(Q, rows, K, out);
+  if (in_double)
+    slice_rows_kernel<double><<<(unsigned)blocks, threads, 0, P->stream>>>((const double*)in, rows, rows_per_batch,
+                                                                          nbatch, K, (__nv_bfloat16*)out);
+  else
+    slice_rows_kernel<float><<<(unsigned)blocks, threads, 0, P->stream>>>((const float*)in, rows, rows_per_batch,
+                                                                         nbatch, K, (__nv_bfloat16*)out);
   return cudaGetLastError();
 }
 

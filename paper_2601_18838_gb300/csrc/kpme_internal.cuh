@@ -102,9 +102,9 @@ struct kpme_plan_s {
   void* d_Qs = nullptr;            // tensor path: sliced Q
   void* d_Y = nullptr;             // stage-1 output (r0 tensors)
   void* d_Z = nullptr;             // stage-2 output (one term group)
-  float* d_rmQ = nullptr;          // error-free split: row maxima of Q, Y, Z (next-stage rows)
-  float* d_rmY = nullptr;
-  float* d_rmZ = nullptr;
+  void* d_Qsl = nullptr;           // error-free split: fixed-point slices of Q [4][K^2][K]
+  void* d_Ysl = nullptr;           // error-free split: fixed-point slices of Y [4][r0][K^2][K]
+  float* d_rmZ = nullptr;          // error-free split: row maxima of Z (rows of stage 3)
   int group_terms = 0;             // capacity of d_Z in terms
   kpme::JobList stage1;
   std::vector<kpme::TermGroup> groups;
@@ -171,7 +171,9 @@ cudaError_t launch_split(kpme_plan_t P, const double* src, void* dst, int64_t co
 // gemm_oz.cu: error-free fixed-point split (KPME_BF16X10)
 struct OzArgs {
   const CUtensorMap* tmB;
-  const void* in;                  // float32, or float64 when in_double
+  const CUtensorMap* tmA;          // pre-sliced A by TMA (nullptr: slice float32 rows on the fly)
+  int nbatch_a;
+  const void* in;                  // float32, or float2 hi/lo pairs when in_double
   bool in_double;
   int64_t in_bs;
   const float* rowmax_in;
@@ -184,7 +186,8 @@ struct OzArgs {
   const JobList* jobs;
 };
 cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a);
-cudaError_t launch_rowmax(kpme_plan_t P, const double* Q, int64_t rows, int K, float* out);
+cudaError_t launch_slice_rows(kpme_plan_t P, const void* in, bool in_double, int64_t rows_per_batch, int nbatch,
+                              int K, void* out);
 int oz_smem_bytes(int bn, int stages);
 bool encode_tmap(kpme_plan_t P, CUtensorMap* map, const void* base, int elem_bytes, bool is_f32,
                  uint64_t dim0, uint64_t dim1, uint64_t dim2, uint32_t box0, uint32_t box1);
