@@ -112,6 +112,11 @@ void release_mesh_buffers(kpme_plan_t P) {
   dfree(P->d_facv);
 }
 
+void drop_graph(kpme_plan_t P) {
+  if (P->graph_exec) cudaGraphExecDestroy(P->graph_exec);
+  P->graph_exec = nullptr;
+}
+
 // Tensor-core tile: BN output columns (<= 256, multiple of 16) and pipeline depth.
 void choose_tc_tiles(kpme_plan_t P) {
   const int K = P->p.K;
@@ -171,6 +176,7 @@ kpme_status_t alloc_meshes(kpme_plan_t P) {
 // Materialise the installed SKP in the plan's arithmetic: factors, intermediates, job lists
 // and (tensor path) TMA descriptors.
 kpme_status_t install_skp(kpme_plan_t P) {
+  drop_graph(P);
   release_skp_buffers(P);
   const SkpHost& S = P->skp;
   if (!S.valid) return KPME_OK;
@@ -483,6 +489,10 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->stream = (cudaStream_t)stream;
   P->max_n = p.max_n;
   P->prec = prec_info(p.precision);
+  {
+    const char* g = getenv("KPME_GRAPHS");
+    P->use_graphs = !(g && g[0] == '0');
+  }
   auto fail = [&](kpme_status_t s) {
     kpme_destroy(P);
     return s;
@@ -529,6 +539,8 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
 void kpme_destroy(kpme_plan_t P) {
   if (!P) return;
   cudaStreamSynchronize(P->stream);
+  drop_graph(P);
+  if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
   release_skp_buffers(P);
   release_mesh_buffers(P);
   free_joblist(P->single);
@@ -658,12 +670,9 @@ kpme_status_t kpme_gather(kpme_plan_t P, int64_t n, const double* x, const doubl
   return KPME_OK;
 }
 
-kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
-                                 double* forces, double* dEdq, double* vir) {
-  kpme_status_t st = common_checks(P, n);
-  if (st != KPME_OK) return st;
-  if (!energy || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
-  if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
+static kpme_status_t energy_forces_body(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
+                                       double* forces, double* dEdq, double* vir) {
+  kpme_status_t st;
   P->launches = 0;
   const int64_t k3 = K3(P);
   KPME_CUDA_TRY(P, cudaMemsetAsync(energy, 0, sizeof(double), P->stream));
@@ -685,6 +694,40 @@ kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, cons
       KPME_CUDA_TRY(P, cudaMemsetAsync(vir, 0, sizeof(double), P->stream));
     }
   }
+  return KPME_OK;
+}
+
+kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
+                                 double* forces, double* dEdq, double* vir) {
+  kpme_status_t st = common_checks(P, n);
+  if (st != KPME_OK) return st;
+  if (!energy || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
+  if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
+  if (P->profiling || !P->use_graphs) return energy_forces_body(P, n, x, q, energy, forces, dEdq, vir);
+  // Replay a captured graph when the call signature repeats (the usual MD / benchmark loop).
+  const int64_t key[8] = {n, (int64_t)x, (int64_t)q, (int64_t)energy, (int64_t)forces, (int64_t)dEdq,
+                          (int64_t)vir, (int64_t)P->p.precision};
+  if (!P->graph_exec || memcmp(key, P->graph_key, sizeof(key)) != 0) {
+    drop_graph(P);
+    if (!P->capture_stream) KPME_CUDA_TRY(P, cudaStreamCreateWithFlags(&P->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t user = P->stream;
+    P->stream = P->capture_stream;
+    KPME_CUDA_TRY(P, cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeRelaxed));
+    st = energy_forces_body(P, n, x, q, energy, forces, dEdq, vir);
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamEndCapture(P->capture_stream, &g);
+    P->stream = user;
+    if (st != KPME_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    KPME_CUDA_TRY(P, e);
+    e = cudaGraphInstantiate(&P->graph_exec, g, 0);
+    cudaGraphDestroy(g);
+    KPME_CUDA_TRY(P, e);
+    memcpy(P->graph_key, key, sizeof(key));
+  }
+  KPME_CUDA_TRY(P, cudaGraphLaunch(P->graph_exec, P->stream));
   return KPME_OK;
 }
 

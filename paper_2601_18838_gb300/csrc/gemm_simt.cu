@@ -12,19 +12,22 @@
 namespace kpme {
 namespace {
 
-constexpr int BM = 64, BN = 64, BK = 16, TM = 4, TN = 4, THREADS = 256;
+constexpr int BK = 16;
 
-template <typename T>
+// BM x BN tile per CTA of THREADS threads, each computing TM x TN outputs:
+// (64, 64, 256 threads, 4 x 4) for large grids, (32, 32, 64 threads, 4 x 4) for small ones.
+template <typename T, int BM, int BN, int THREADS>
 __global__ void __launch_bounds__(THREADS) mp_simt_kernel(const T* __restrict__ in, int64_t in_bs,
                                                           const T* __restrict__ fac, T* __restrict__ out,
                                                           int64_t out_bs, int M, int N, int Kr,
                                                           const int* __restrict__ start,
                                                           const int2* __restrict__ pairs, int mode) {
+  constexpr int TM = 4, TN = 4, TX = BM / TM;
   __shared__ T As[BK][BM + 1];
   __shared__ T Bs[BK][BN + 1];
   const int job = blockIdx.z;
   const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  const int tx = threadIdx.x % TX, ty = threadIdx.x / TX;
   T acc[TM][TN];
 #pragma unroll
   for (int i = 0; i < TM; ++i)
@@ -52,9 +55,9 @@ __global__ void __launch_bounds__(THREADS) mp_simt_kernel(const T* __restrict__ 
       for (int kk = 0; kk < BK; ++kk) {
         T a[TM], b[TN];
 #pragma unroll
-        for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + 16 * i];
+        for (int i = 0; i < TM; ++i) a[i] = As[kk][tx + TX * i];
 #pragma unroll
-        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + 16 * j];
+        for (int j = 0; j < TN; ++j) b[j] = Bs[kk][ty + (BN / TN) * j];
 #pragma unroll
         for (int i = 0; i < TM; ++i)
 #pragma unroll
@@ -66,11 +69,11 @@ __global__ void __launch_bounds__(THREADS) mp_simt_kernel(const T* __restrict__ 
   T* O = out + (mode == 0 ? (int64_t)job * out_bs : 0);
 #pragma unroll
   for (int j = 0; j < TN; ++j) {
-    const int n = n0 + ty + 16 * j;
+    const int n = n0 + ty + (BN / TN) * j;
     if (n >= N) continue;
 #pragma unroll
     for (int i = 0; i < TM; ++i) {
-      const int m = m0 + tx + 16 * i;
+      const int m = m0 + tx + TX * i;
       if (m >= M) continue;
       T* dst = O + (int64_t)n * M + m;
       if (mode == 0)
@@ -83,16 +86,24 @@ __global__ void __launch_bounds__(THREADS) mp_simt_kernel(const T* __restrict__ 
 
 }  // namespace
 
-cudaError_t launch_mp_simt(bool dbl, const void* in, int64_t in_bs, const void* fac, void* out, int64_t out_bs,
-                           int M, int N, int Kr, const JobList& jobs, int mode, cudaStream_t s) {
+template <int BM, int BN, int THREADS>
+cudaError_t launch_tiles(bool dbl, const void* in, int64_t in_bs, const void* fac, void* out, int64_t out_bs, int M,
+                         int N, int Kr, const JobList& jobs, int mode, cudaStream_t s) {
   dim3 grid((M + BM - 1) / BM, (N + BN - 1) / BN, jobs.n_jobs);
   if (dbl)
-    mp_simt_kernel<double><<<grid, THREADS, 0, s>>>((const double*)in, in_bs, (const double*)fac, (double*)out,
-                                                    out_bs, M, N, Kr, jobs.d_start, jobs.d_pairs, mode);
+    mp_simt_kernel<double, BM, BN, THREADS><<<grid, THREADS, 0, s>>>(
+        (const double*)in, in_bs, (const double*)fac, (double*)out, out_bs, M, N, Kr, jobs.d_start, jobs.d_pairs, mode);
   else
-    mp_simt_kernel<float><<<grid, THREADS, 0, s>>>((const float*)in, in_bs, (const float*)fac, (float*)out,
-                                                   out_bs, M, N, Kr, jobs.d_start, jobs.d_pairs, mode);
+    mp_simt_kernel<float, BM, BN, THREADS><<<grid, THREADS, 0, s>>>(
+        (const float*)in, in_bs, (const float*)fac, (float*)out, out_bs, M, N, Kr, jobs.d_start, jobs.d_pairs, mode);
   return cudaGetLastError();
+}
+
+cudaError_t launch_mp_simt(bool dbl, const void* in, int64_t in_bs, const void* fac, void* out, int64_t out_bs,
+                           int M, int N, int Kr, const JobList& jobs, int mode, cudaStream_t s) {
+  const int64_t big = (int64_t)((M + 63) / 64) * ((N + 63) / 64) * jobs.n_jobs;
+  if (big >= 4 * 152) return launch_tiles<64, 64, 256>(dbl, in, in_bs, fac, out, out_bs, M, N, Kr, jobs, mode, s);
+  return launch_tiles<32, 32, 64>(dbl, in, in_bs, fac, out, out_bs, M, N, Kr, jobs, mode, s);
 }
 
 }  // namespace kpme

@@ -124,6 +124,12 @@ struct kpme_plan_s {
   int64_t launches = 0;            // kernels launched by the last evaluation
 
   int64_t scratch_bytes = 0;
+
+  // CUDA graph of kpme_energy_forces, keyed by its arguments; replayed on the caller's stream
+  cudaStream_t capture_stream = nullptr;
+  cudaGraphExec_t graph_exec = nullptr;
+  int64_t graph_key[8] = {};
+  bool use_graphs = true;
 };
 
 namespace kpme {
