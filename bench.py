@@ -31,6 +31,8 @@ WORKLOAD_TEXT = {
     "small": "1000 charges +-1, L=20 A, order 4, K=32, beta=0.35/A, SKP tol 1e-8",
     "mixed": "1e5 charges (+-1, +-0.5), L=100 A, order 6, K=96, beta=0.35/A, SKP tol 1e-8",
     "large": "1e6 charges +-1, L=220 A, order 6, K=256, beta=0.35/A, SKP tol 1e-7",
+    "batched": "64 independent neutral +-1 systems, N log-uniform in [2000, 50000], box 30-80 A, "
+               "K in {32, 48, 64} (box/K <= 1.25 A), order 4, one graph launch per evaluation",
 }
 DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16": "bf16", "bf16x3": "bf16",
          "bf16x6": "bf16", "bf16x10": "bf16"}
@@ -147,6 +149,58 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """All systems of the batched workload per step (one graph launch); value in
+    system-evaluations per second."""
+    import numpy as np
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_2601_18838_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    from paper_2601_18838_gb300 import Batch
+    from paper_2601_18838_gb300 import workloads
+    systems = workloads.batched()
+    batch = Batch([dict(box=s.box, K=s.K, order=s.order, beta=s.beta, skp_tol=s.skp_tol, max_n=s.n) for s in systems],
+                  precision=args.precision)
+    ranks = batch.build_skp()
+    offsets = np.cumsum([0] + [s.n for s in systems])
+    x = torch.tensor(np.concatenate([s.x for s in systems]), device=dev)
+    q = torch.tensor(np.concatenate([s.q for s in systems]), device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        batch.energy_forces(x, q, offsets, virial=True)
+    torch.cuda.synchronize()
+    clk = ClockSampler(local)
+    clk.start()
+    ms = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        batch.energy_forces(x, q, offsets, virial=True)
+        b.record(stream)
+        b.synchronize()
+        ms += a.elapsed_time(b)
+    clocks = clk.stop()
+    n_sys = len(systems)
+    line = {"metric": METRIC, "value": n_sys * args.steps / (ms * 1e-3), "unit": "system-evals/s", "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": DTYPE.get(args.precision, args.precision),
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD_TEXT["batched"], "precision": args.precision, "systems": n_sys,
+                       "particles": int(offsets[-1]), "skp_ranks": [int(r) for r in ranks],
+                       "l2": "flushed between steps (256 MB write outside the timed events)"},
+            "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -161,6 +215,8 @@ def main(argv=None):
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
 
     import numpy as np
     import torch

@@ -214,6 +214,31 @@ kpme_status_t kpme_get_profile(kpme_plan_t plan, double* ms, int64_t* launches, 
 kpme_status_t kpme_spread_noalloc(const kpme_params_t* params, void* stream, int64_t n, const double* x,
                                   const double* q, double* Q);
 
+/* ---- Batches of independent systems --------------------------------------------
+ * Many independent periodic systems (uneven particle counts, boxes and meshes) evaluated
+ * by ONE CUDA graph launch per call: every system's pipeline (Algorithm 4 on its own box)
+ * is a parallel branch of the captured graph, replayed while the call signature repeats.
+ * Each system is described by its own kpme_params_t; systems with identical box, order,
+ * K, beta, tolerance and method share one SKP build. */
+typedef struct kpme_batch_s* kpme_batch_t;
+
+/* Create plans for n_sys systems (params[n_sys]) on one stream. */
+kpme_status_t kpme_batch_create(int n_sys, const kpme_params_t* params, void* stream, kpme_batch_t* out);
+void kpme_batch_destroy(kpme_batch_t batch);
+kpme_status_t kpme_batch_set_stream(kpme_batch_t batch, void* stream);
+
+/* Build (or share) the SKP of every system; ranks_out[n_sys] (may be NULL) gets each R. */
+kpme_status_t kpme_batch_build_skp(kpme_batch_t batch, int* ranks_out);
+
+/* Evaluate all systems.  offsets (HOST, n_sys + 1 entries, non-decreasing) delimit each
+ * system's particles in the concatenated DEVICE arrays x (total x 3), q (total), forces
+ * (total x 3, may be NULL) and dEdq (total, may be NULL); energies and virials (may be NULL)
+ * are DEVICE arrays of n_sys values.  A system with zero particles gets zero energy. */
+kpme_status_t kpme_batch_energy_forces(kpme_batch_t batch, const int64_t* offsets, const double* x, const double* q,
+                                       double* energies, double* forces, double* dEdq, double* virials);
+
+const char* kpme_batch_last_error(kpme_batch_t batch);
+
 typedef struct {
   int K, order, precision, r0, R;
   double skp_rel_err;

@@ -8,5 +8,5 @@ this package is its thin Python binding:
 * ``reciprocal_energy``    differentiable energy (torch.autograd.Function).
 * ``workloads``            seeded synthetic point clouds.
 """
-from ._binding import Plan, KpmeError, PRECISIONS, EXPORTS, lib  # noqa: F401
+from ._binding import Plan, Batch, KpmeError, PRECISIONS, EXPORTS, lib  # noqa: F401
 from .autograd import reciprocal_energy  # noqa: F401

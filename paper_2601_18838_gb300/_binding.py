@@ -22,6 +22,8 @@ EXPORTS = [
     "kpme_build_skp", "kpme_set_skp", "kpme_get_skp", "kpme_potential", "kpme_energy_forces",
     "kpme_spread", "kpme_apply", "kpme_gather", "kpme_set_profiling", "kpme_get_profile",
     "kpme_get_info", "kpme_status_string", "kpme_last_error", "kpme_spread_noalloc",
+    "kpme_batch_create", "kpme_batch_destroy", "kpme_batch_set_stream", "kpme_batch_build_skp",
+    "kpme_batch_energy_forces", "kpme_batch_last_error",
 ]
 
 
@@ -84,6 +86,12 @@ def lib():
         "kpme_status_string": (C.c_char_p, [C.c_int]),
         "kpme_last_error": (C.c_char_p, [_vp]),
         "kpme_spread_noalloc": (st, [C.POINTER(Params), _vp, _i64, _vp, _vp, _vp]),
+        "kpme_batch_create": (st, [C.c_int, C.POINTER(Params), _vp, C.POINTER(_vp)]),
+        "kpme_batch_destroy": (None, [_vp]),
+        "kpme_batch_set_stream": (st, [_vp, _vp]),
+        "kpme_batch_build_skp": (st, [_vp, _ip]),
+        "kpme_batch_energy_forces": (st, [_vp, C.POINTER(C.c_int64), _vp, _vp, _vp, _vp, _vp, _vp]),
+        "kpme_batch_last_error": (C.c_char_p, [_vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -282,3 +290,85 @@ class Plan:
         i = Info()
         self._call("kpme_get_info", C.byref(i))
         return {f: getattr(i, f) for f, _ in Info._fields_}
+
+
+class Batch:
+    """Independent systems evaluated by one graph launch (``kpme_batch_*``).
+
+    ``systems``: list of dicts with keys box, K, order and optionally beta, center,
+    skp_tol, max_n.  ``energy_forces`` takes the concatenated positions / charges and the
+    host offsets delimiting each system."""
+
+    def __init__(self, systems, precision: str = "bf16x10", skp_method: str = "svd", coulomb_k: float = 1.0,
+                 stream=None):
+        L = lib()
+        arr = (Params * len(systems))()
+        for i, sd in enumerate(systems):
+            p = arr[i]
+            L.kpme_default_params(C.byref(p))
+            box = float(sd["box"])
+            c = sd.get("center") or (0.5 * box,) * 3
+            p.center = (C.c_double * 3)(*c)
+            p.radius = 0.5 * box
+            p.beta = sd.get("beta", 0.35)
+            p.order = sd["order"]
+            p.K = sd["K"]
+            p.skp_tol = sd.get("skp_tol", 1e-8)
+            p.skp_method = SKP_METHODS[skp_method]
+            p.precision = PRECISIONS[precision]
+            p.max_n = sd.get("max_n", 1 << 20)
+            p.coulomb_k = coulomb_k
+        self.n_sys = len(systems)
+        self._stream = stream
+        h = C.c_void_p()
+        st = L.kpme_batch_create(C.c_int(self.n_sys), arr, self._stream_handle(), C.byref(h))
+        if st != 0:
+            raise KpmeError("kpme_batch_create", st)
+        self._h = h
+
+    def _stream_handle(self):
+        import torch
+        s = self._stream if self._stream is not None else torch.cuda.current_stream()
+        return C.c_void_p(s.cuda_stream)
+
+    def _call(self, name, *args):
+        L = lib()
+        L.kpme_batch_set_stream(self._h, self._stream_handle())
+        st = getattr(L, name)(self._h, *args)
+        if st != 0:
+            raise KpmeError(name, st, L.kpme_batch_last_error(self._h).decode())
+
+    def build_skp(self):
+        import numpy as np
+        r = np.zeros(self.n_sys, np.int32)
+        self._call("kpme_batch_build_skp", r.ctypes.data_as(_ip))
+        return r
+
+    def energy_forces(self, x, q, offsets, forces: bool = True, dEdq: bool = True, virial: bool = False):
+        import numpy as np
+        import torch
+        n = x.shape[0]
+        _check_dev(x, "x", torch.float64, (n, 3))
+        _check_dev(q, "q", torch.float64, (n,))
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if off.size != self.n_sys + 1 or off[-1] != n:
+            raise ValueError("offsets must have n_sys + 1 entries ending at the particle count")
+        dev = x.device
+        E = torch.empty(self.n_sys, dtype=torch.float64, device=dev)
+        F = torch.empty((n, 3), dtype=torch.float64, device=dev) if forces else None
+        P = torch.empty(n, dtype=torch.float64, device=dev) if dEdq else None
+        W = torch.empty(self.n_sys, dtype=torch.float64, device=dev) if virial else None
+        self._call("kpme_batch_energy_forces", off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(x), _ptr(q), _ptr(E),
+                   _ptr(F), _ptr(P), _ptr(W))
+        return dict(energy=E, forces=F, dEdq=P, virial=W)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().kpme_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

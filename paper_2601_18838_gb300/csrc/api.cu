@@ -438,6 +438,13 @@ kpme_status_t common_checks(kpme_plan_t P, int64_t n) {
 
 }  // namespace
 
+namespace kpme {
+kpme_status_t plan_install_skp(kpme_plan_t P, const SkpHost& S) {
+  P->skp = S;
+  return install_skp(P);
+}
+}  // namespace kpme
+
 extern "C" {
 
 kpme_status_t kpme_default_params(kpme_params_t* p) {
@@ -670,7 +677,9 @@ kpme_status_t kpme_gather(kpme_plan_t P, int64_t n, const double* x, const doubl
   return KPME_OK;
 }
 
-static kpme_status_t energy_forces_body(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
+}  // extern "C"
+
+kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
                                        double* forces, double* dEdq, double* vir) {
   kpme_status_t st;
   P->launches = 0;
@@ -697,13 +706,15 @@ static kpme_status_t energy_forces_body(kpme_plan_t P, int64_t n, const double* 
   return KPME_OK;
 }
 
+extern "C" {
+
 kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
                                  double* forces, double* dEdq, double* vir) {
   kpme_status_t st = common_checks(P, n);
   if (st != KPME_OK) return st;
   if (!energy || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
   if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
-  if (P->profiling || !P->use_graphs) return energy_forces_body(P, n, x, q, energy, forces, dEdq, vir);
+  if (P->profiling || !P->use_graphs) return eval_energy_forces(P, n, x, q, energy, forces, dEdq, vir);
   // Replay a captured graph when the call signature repeats (the usual MD / benchmark loop).
   const int64_t key[8] = {n, (int64_t)x, (int64_t)q, (int64_t)energy, (int64_t)forces, (int64_t)dEdq,
                           (int64_t)vir, (int64_t)P->p.precision};
@@ -713,7 +724,7 @@ kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, cons
     cudaStream_t user = P->stream;
     P->stream = P->capture_stream;
     KPME_CUDA_TRY(P, cudaStreamBeginCapture(P->capture_stream, cudaStreamCaptureModeRelaxed));
-    st = energy_forces_body(P, n, x, q, energy, forces, dEdq, vir);
+    st = eval_energy_forces(P, n, x, q, energy, forces, dEdq, vir);
     cudaGraph_t g = nullptr;
     cudaError_t e = cudaStreamEndCapture(P->capture_stream, &g);
     P->stream = user;

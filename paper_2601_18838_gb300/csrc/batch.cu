@@ -1,0 +1,179 @@
+// Batched evaluation of many independent periodic systems (uneven N, box and K) with one
+// CUDA graph launch.  Each system owns a plan; one evaluation is captured as a graph whose
+// parallel branches run the systems' pipelines (spread, SKP mode products, gather,
+// reductions) on up to 16 branch streams, and the executable graph is replayed while the
+// call signature repeats.  Systems with identical parameters share one SKP build.
+#include "kpme_internal.cuh"
+
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <new>
+#include <tuple>
+
+struct kpme_batch_s {
+  std::vector<kpme_plan_t> plans;
+  cudaStream_t stream = nullptr;       // caller's stream
+  cudaStream_t root = nullptr;         // capture origin
+  std::vector<cudaStream_t> branches;
+  cudaEvent_t fork = nullptr;
+  std::vector<cudaEvent_t> joins;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int64_t> key;
+  std::string last_error;
+};
+
+namespace {
+
+void release(kpme_batch_t B) {
+  if (!B) return;
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  for (auto p : B->plans) kpme_destroy(p);
+  for (auto s : B->branches) cudaStreamDestroy(s);
+  if (B->root) cudaStreamDestroy(B->root);
+  if (B->fork) cudaEventDestroy(B->fork);
+  for (auto e : B->joins) cudaEventDestroy(e);
+  delete B;
+}
+
+kpme_status_t fail(kpme_batch_t B, const char* what, cudaError_t e) {
+  B->last_error = std::string(what) + ": " + cudaGetErrorString(e);
+  return e == cudaErrorMemoryAllocation ? KPME_ERR_OOM : KPME_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+kpme_status_t kpme_batch_create(int n_sys, const kpme_params_t* params, void* stream, kpme_batch_t* out) {
+  if (!out || n_sys <= 0 || !params) return KPME_ERR_INVALID_ARG;
+  *out = nullptr;
+  kpme_batch_t B = new (std::nothrow) kpme_batch_s();
+  if (!B) return KPME_ERR_OOM;
+  B->stream = (cudaStream_t)stream;
+  for (int s = 0; s < n_sys; ++s) {
+    kpme_plan_t P = nullptr;
+    kpme_status_t st = kpme_plan(&params[s], stream, &P);
+    if (st != KPME_OK) {
+      release(B);
+      return st;
+    }
+    P->use_graphs = false;
+    B->plans.push_back(P);
+  }
+  const int nb = std::min(n_sys, 16);
+  cudaError_t e = cudaStreamCreateWithFlags(&B->root, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming);
+  for (int i = 0; i < nb && e == cudaSuccess; ++i) {
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    if (s) B->branches.push_back(s);
+    if (ev) B->joins.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    kpme_status_t st = e == cudaErrorMemoryAllocation ? KPME_ERR_OOM : KPME_ERR_CUDA;
+    release(B);
+    return st;
+  }
+  *out = B;
+  return KPME_OK;
+}
+
+void kpme_batch_destroy(kpme_batch_t B) {
+  if (B && B->stream) cudaStreamSynchronize(B->stream);
+  release(B);
+}
+
+kpme_status_t kpme_batch_build_skp(kpme_batch_t B, int* ranks_out) {
+  if (!B) return KPME_ERR_INVALID_ARG;
+  using Key = std::tuple<int, int, double, double, double, int>;
+  std::map<Key, int> first;
+  for (size_t s = 0; s < B->plans.size(); ++s) {
+    kpme_plan_t P = B->plans[s];
+    const Key k{P->p.K, P->p.order, P->p.radius, P->p.beta, P->p.skp_tol, P->p.skp_method};
+    auto it = first.find(k);
+    kpme_status_t st;
+    if (it == first.end()) {
+      st = kpme_build_skp(P, nullptr, nullptr);
+      first[k] = (int)s;
+    } else {
+      st = kpme::plan_install_skp(P, B->plans[it->second]->skp);
+    }
+    if (st != KPME_OK) {
+      B->last_error = P->last_error;
+      return st;
+    }
+    if (ranks_out) ranks_out[s] = P->skp.R;
+  }
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  B->exec = nullptr;
+  return KPME_OK;
+}
+
+kpme_status_t kpme_batch_energy_forces(kpme_batch_t B, const int64_t* offsets, const double* x, const double* q,
+                                       double* energies, double* forces, double* dEdq, double* virials) {
+  if (!B || !offsets || !energies) return KPME_ERR_INVALID_ARG;
+  const int n_sys = (int)B->plans.size();
+  for (int s = 0; s < n_sys; ++s) {
+    const int64_t n = offsets[s + 1] - offsets[s];
+    if (offsets[s] < 0 || n < 0) return KPME_ERR_INVALID_ARG;
+    if (n > B->plans[s]->max_n) return KPME_ERR_CAPACITY;
+    if (!B->plans[s]->skp.valid) return KPME_ERR_NOT_BUILT;
+  }
+  if (offsets[n_sys] > 0 && (!x || !q)) return KPME_ERR_INVALID_ARG;
+  std::vector<int64_t> key(offsets, offsets + n_sys + 1);
+  for (const void* p : {(const void*)x, (const void*)q, (const void*)energies, (const void*)forces,
+                        (const void*)dEdq, (const void*)virials})
+    key.push_back((int64_t)p);
+  if (!B->exec || key != B->key) {
+    if (B->exec) cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(B->root, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) return fail(B, "cudaStreamBeginCapture", e);
+    cudaEventRecord(B->fork, B->root);
+    for (auto s : B->branches) cudaStreamWaitEvent(s, B->fork, 0);
+    kpme_status_t st = KPME_OK;
+    for (int s = 0; s < n_sys && st == KPME_OK; ++s) {
+      kpme_plan_t P = B->plans[s];
+      const int64_t o = offsets[s], n = offsets[s + 1] - offsets[s];
+      cudaStream_t keep = P->stream;
+      P->stream = B->branches[s % B->branches.size()];
+      st = kpme::eval_energy_forces(P, n, x ? x + 3 * o : nullptr, q ? q + o : nullptr, energies + s,
+                                    forces ? forces + 3 * o : nullptr, dEdq ? dEdq + o : nullptr,
+                                    virials ? virials + s : nullptr);
+      if (st != KPME_OK) B->last_error = P->last_error;
+      P->stream = keep;
+    }
+    for (size_t i = 0; i < B->branches.size(); ++i) {
+      cudaEventRecord(B->joins[i], B->branches[i]);
+      cudaStreamWaitEvent(B->root, B->joins[i], 0);
+    }
+    cudaGraph_t g = nullptr;
+    e = cudaStreamEndCapture(B->root, &g);
+    if (st != KPME_OK) {
+      if (g) cudaGraphDestroy(g);
+      return st;
+    }
+    if (e != cudaSuccess) return fail(B, "cudaStreamEndCapture", e);
+    e = cudaGraphInstantiate(&B->exec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return fail(B, "cudaGraphInstantiate", e);
+    B->key = key;
+  }
+  cudaError_t e = cudaGraphLaunch(B->exec, B->stream);
+  if (e != cudaSuccess) return fail(B, "cudaGraphLaunch", e);
+  return KPME_OK;
+}
+
+kpme_status_t kpme_batch_set_stream(kpme_batch_t B, void* stream) {
+  if (!B) return KPME_ERR_INVALID_ARG;
+  B->stream = (cudaStream_t)stream;
+  for (auto P : B->plans) P->stream = (cudaStream_t)stream;
+  return KPME_OK;
+}
+
+const char* kpme_batch_last_error(kpme_batch_t B) { return B ? B->last_error.c_str() : ""; }
+
+}  // extern "C"

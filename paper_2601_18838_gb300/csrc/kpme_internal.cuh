@@ -201,6 +201,13 @@ int tc_smem_bytes(const PrecInfo& pi, int bn, int stages);
 
 }  // namespace kpme
 
+namespace kpme {
+// api.cu: the uncaptured evaluation of kpme_energy_forces on P->stream, and SKP installation
+kpme_status_t eval_energy_forces(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
+                                 double* forces, double* dEdq, double* vir);
+kpme_status_t plan_install_skp(kpme_plan_t P, const SkpHost& S);
+}  // namespace kpme
+
 #define KPME_CUDA_TRY(P, expr)                                                   \
   do {                                                                           \
     cudaError_t _e = (expr);                                                     \
