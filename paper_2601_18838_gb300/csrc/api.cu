@@ -321,8 +321,15 @@ kpme_status_t check_device_status(kpme_plan_t P) {
   return KPME_OK;
 }
 
-// Q: the float64 charge mesh; Phi: float32 (float64 for the FP64 form).
-kpme_status_t contract(kpme_plan_t P, const double* Q, void* Phi) {
+// The charge mesh handed to the mode products: float64 (FP64 form, untiled fallback, stage
+// entry points) or float32 (cell-sorted spreading).
+struct MeshRef {
+  const void* p;
+  bool dbl;
+};
+
+// Phi: float32 (float64 for the FP64 form).
+kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
   const int K = P->p.K;
   const int M = K * K;
   const int64_t k3 = K3(P);
@@ -330,10 +337,10 @@ kpme_status_t contract(kpme_plan_t P, const double* Q, void* Phi) {
   const SkpHost& S = P->skp;
   if (!pi.tensor) {
     const bool dbl = pi.fp64;
-    const void* Qin = Q;
-    if (!dbl) {
+    const void* Qin = Q.p;
+    if (!dbl && Q.dbl) {
       StepScope sc(P, STEP_SPLIT, 1);
-      KPME_CUDA_TRY(P, launch_convert(Q, true, P->d_Qf, false, k3, P->stream));
+      KPME_CUDA_TRY(P, launch_convert(Q.p, true, P->d_Qf, false, k3, P->stream));
       Qin = P->d_Qf;
     }
     {
@@ -356,7 +363,7 @@ kpme_status_t contract(kpme_plan_t P, const double* Q, void* Phi) {
     const int64_t k2 = (int64_t)K * K;
     {
       StepScope sc(P, STEP_SPLIT, 1);
-      KPME_CUDA_TRY(P, launch_slice_rows(P, Q, true, k2, 1, K, P->d_Qsl));
+      KPME_CUDA_TRY(P, launch_slice_rows(P, Q.p, Q.dbl, k2, 1, K, P->d_Qsl));
     }
     {
       StepScope sc(P, STEP_SKP1, 2);
@@ -383,7 +390,7 @@ kpme_status_t contract(kpme_plan_t P, const double* Q, void* Phi) {
   }
   {
     StepScope sc(P, STEP_SPLIT, 1);
-    KPME_CUDA_TRY(P, launch_split(P, Q, P->d_Qs, k3));
+    KPME_CUDA_TRY(P, launch_split(P, Q.p, Q.dbl, P->d_Qs, k3));
   }
   {
     StepScope sc(P, STEP_SKP1, 1);
@@ -404,14 +411,15 @@ kpme_status_t contract(kpme_plan_t P, const double* Q, void* Phi) {
   return KPME_OK;
 }
 
-kpme_status_t virial(kpme_plan_t P, const double* energy, double* out) {
+kpme_status_t virial(kpme_plan_t P, MeshRef Q, const double* energy, double* out) {
   const int K = P->p.K, M = K * K;
   const int64_t k3 = K3(P);
   const bool dbl = P->prec.fp64;
-  StepScope sc(P, STEP_VIRIAL, dbl ? 5 : 6);
-  const void* Qv = P->d_Q;
-  if (!dbl) {
-    KPME_CUDA_TRY(P, launch_convert(P->d_Q, true, P->d_Qf, false, k3, P->stream));
+  const bool conv = !dbl && Q.dbl;
+  StepScope sc(P, STEP_VIRIAL, conv ? 6 : 5);
+  const void* Qv = Q.p;
+  if (conv) {
+    KPME_CUDA_TRY(P, launch_convert(Q.p, true, P->d_Qf, false, k3, P->stream));
     Qv = P->d_Qf;
   }
   KPME_CUDA_TRY(P, launch_mp_simt(dbl, Qv, 0, P->d_facv, P->d_tmp1, 0, M, K, K, P->single, 0, P->stream));
@@ -423,6 +431,40 @@ kpme_status_t virial(kpme_plan_t P, const double* energy, double* out) {
   const double t0 = 1.0 / (M_PI * L * L * L);
   const double coef = 2.0 * M_PI * M_PI / (P->p.beta * P->p.beta);
   KPME_CUDA_TRY(P, launch_virial_finalize(P, energy, P->d_qpsi, t0, coef, out));
+  return KPME_OK;
+}
+
+bool tiled(kpme_plan_t P) { return !P->prec.fp64 && P->tile > 0; }
+
+// Charge mesh of n particles: cell sort + tile-staged float32 spreading, or float64 atomics
+// for the FP64 form (and meshes the tiling does not divide).
+kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, MeshRef& out) {
+  const int64_t k3 = K3(P);
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+  if (!tiled(P)) {
+    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
+    KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
+    out = {P->d_Q, true};
+    return KPME_OK;
+  }
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Qf, 0, (size_t)k3 * sizeof(float), P->stream));
+  KPME_CUDA_TRY(P, launch_sort(P, n, x, q, P->d_sumq));
+  KPME_CUDA_TRY(P, launch_spread_tiled(P, n, q, P->d_Qf));
+  out = {P->d_Qf, false};
+  return KPME_OK;
+}
+
+// Potentials (and forces, energy) at n particles from the plan's potential mesh.  sorted:
+// the cell sort of these positions is already in place (same call).
+kpme_status_t gather_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, double* phi, double* F,
+                          double* energy, bool correct, bool sorted) {
+  if (!tiled(P)) {
+    if (!correct) KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+    KPME_CUDA_TRY(P, launch_gather(P, n, x, q, P->d_Phi, phi, F, energy, 1.0));
+    return KPME_OK;
+  }
+  if (!sorted) KPME_CUDA_TRY(P, launch_sort(P, n, x, nullptr, nullptr));
+  KPME_CUDA_TRY(P, launch_gather_tiled(P, n, q, (const float*)P->d_Phi, phi, F, energy, correct));
   return KPME_OK;
 }
 
@@ -534,6 +576,17 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->d_sumq = acc;
   P->d_energy = acc + 1;
   P->d_qpsi = acc + 2;
+  P->tile = choose_tile(p.K, p.order);
+  if (P->tile > 0) {
+    const int kt = p.K / P->tile;
+    const size_t nt = (size_t)kt * kt * kt;
+    const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
+    if ((st = dalloc(P, (void**)&P->d_tcount, nt * sizeof(int))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_tstart, (nt + 1) * sizeof(int))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_rec_in, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_rec, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
+  }
   if ((st = alloc_meshes(P)) != KPME_OK) return fail(st);
   P->single.h_start = {0, 1};
   P->single.h_pairs = {make_int2(0, 0)};
@@ -552,6 +605,11 @@ void kpme_destroy(kpme_plan_t P) {
   release_mesh_buffers(P);
   free_joblist(P->single);
   if (P->d_sumq) cudaFree(P->d_sumq);
+  dfree(P->d_tcount);
+  dfree(P->d_tstart);
+  dfree(P->d_tslot);
+  dfree(P->d_rec_in);
+  dfree(P->d_rec);
   if (P->d_status) cudaFreeHost(P->d_status);
   for (auto& pe : P->pending) {
     cudaEventDestroy(pe.second.first);
@@ -643,10 +701,9 @@ kpme_status_t kpme_spread(kpme_plan_t P, int64_t n, const double* x, const doubl
   if (st != KPME_OK) return st;
   if (!Q || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
   const int64_t k3 = K3(P);
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-  KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
-  KPME_CUDA_TRY(P, cudaMemcpyAsync(Q, P->d_Q, (size_t)k3 * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+  MeshRef m;
+  if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
+  KPME_CUDA_TRY(P, launch_convert(m.p, m.dbl, Q, true, k3, P->stream));
   return KPME_OK;
 }
 
@@ -656,8 +713,14 @@ kpme_status_t kpme_apply(kpme_plan_t P, const double* Q, double* Phi) {
   if (!Q || !Phi) return KPME_ERR_INVALID_ARG;
   if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
   const int64_t k3 = K3(P);
-  KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_Q, Q, (size_t)k3 * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
-  if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;
+  MeshRef m{P->d_Q, true};
+  if (tiled(P)) {
+    KPME_CUDA_TRY(P, launch_convert(Q, true, P->d_Qf, false, k3, P->stream));
+    m = {P->d_Qf, false};
+  } else {
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_Q, Q, (size_t)k3 * sizeof(double), cudaMemcpyDeviceToDevice, P->stream));
+  }
+  if ((st = contract(P, m, P->d_Phi)) != KPME_OK) return st;
   KPME_CUDA_TRY(P, launch_convert(P->d_Phi, P->prec.fp64, Phi, true, k3, P->stream));
   if (P->skp.c != 0.0) {
     P->last_error = "kpme_apply with a non-zero correction constant is not supported";
@@ -672,9 +735,7 @@ kpme_status_t kpme_gather(kpme_plan_t P, int64_t n, const double* x, const doubl
   if (st != KPME_OK) return st;
   if (!Phi || (n > 0 && (!x || !phi || (F && !q)))) return KPME_ERR_INVALID_ARG;
   KPME_CUDA_TRY(P, launch_convert(Phi, true, P->d_Phi, P->prec.fp64, K3(P), P->stream));
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-  KPME_CUDA_TRY(P, launch_gather(P, n, x, F ? q : nullptr, P->d_Phi, phi, F, nullptr, 1.0));
-  return KPME_OK;
+  return gather_mesh(P, n, x, F ? q : nullptr, phi, F, nullptr, false, false);
 }
 
 }  // extern "C"
@@ -684,21 +745,21 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
   kpme_status_t st;
   P->launches = 0;
   const int64_t k3 = K3(P);
+  (void)k3;
   KPME_CUDA_TRY(P, cudaMemsetAsync(energy, 0, sizeof(double), P->stream));
+  MeshRef m;
   {
-    StepScope sc(P, STEP_SPREAD, n > 0 ? 1 : 0);
-    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
-    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-    KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
+    StepScope sc(P, STEP_SPREAD, n > 0 ? (tiled(P) ? 4 : 1) : 0);
+    if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
   }
   if (n > 0) {
-    if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;
+    if ((st = contract(P, m, P->d_Phi)) != KPME_OK) return st;
     StepScope sc(P, STEP_GATHER, 1);
-    KPME_CUDA_TRY(P, launch_gather(P, n, x, q, P->d_Phi, dEdq, forces, energy, 1.0));
+    if ((st = gather_mesh(P, n, x, q, dEdq, forces, energy, true, true)) != KPME_OK) return st;
   }
   if (vir) {
     if (n > 0) {
-      if ((st = virial(P, energy, vir)) != KPME_OK) return st;
+      if ((st = virial(P, m, energy, vir)) != KPME_OK) return st;
     } else {
       KPME_CUDA_TRY(P, cudaMemsetAsync(vir, 0, sizeof(double), P->stream));
     }
@@ -748,13 +809,10 @@ kpme_status_t kpme_potential(kpme_plan_t P, int64_t n_y, const double* y, const 
   if (st != KPME_OK) return st;
   if ((n_y > 0 && (!y || !q)) || (n_x > 0 && (!x || !p)) || n_y < 0 || n_x < 0) return KPME_ERR_INVALID_ARG;
   if (!P->skp.valid) return KPME_ERR_NOT_BUILT;
-  const int64_t k3 = K3(P);
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-  KPME_CUDA_TRY(P, launch_spread(P, n_y, y, q, P->d_Q));
-  if ((st = contract(P, P->d_Q, P->d_Phi)) != KPME_OK) return st;
-  KPME_CUDA_TRY(P, launch_gather(P, n_x, x, nullptr, P->d_Phi, p, nullptr, nullptr, 1.0));
-  return KPME_OK;
+  MeshRef m;
+  if ((st = spread_mesh(P, n_y, y, q, m)) != KPME_OK) return st;
+  if ((st = contract(P, m, P->d_Phi)) != KPME_OK) return st;
+  return gather_mesh(P, n_x, x, nullptr, p, nullptr, nullptr, true, false);
 }
 
 kpme_status_t kpme_set_profiling(kpme_plan_t P, int enable) {

@@ -307,10 +307,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 }
 
 // fp32 -> S slices (bf16 round-to-nearest cascade, or tf32 hi / lo in float32)
-template <bool TF32, int S>
-__global__ void split_kernel(const double* __restrict__ src, void* __restrict__ dst, int64_t count) {
+template <bool TF32, int S, typename TS>
+__global__ void split_kernel(const TS* __restrict__ src, void* __restrict__ dst, int64_t count) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x) {
-    const double v = src[i];
+    const double v = (double)src[i];
     if constexpr (TF32) {
       const float hi = tf32_rn((float)v);
       reinterpret_cast<float*>(dst)[i] = hi;
@@ -415,21 +415,27 @@ cudaError_t launch_mp_tc(kpme_plan_t P, const TcArgs& a) {
   return launch_t<false, 3>(P, a, prm, grid, smem);
 }
 
-cudaError_t launch_split(kpme_plan_t P, const double* src, void* dst, int64_t count) {
+template <typename TS>
+cudaError_t split_t(kpme_plan_t P, const TS* src, void* dst, int64_t count) {
   const PrecInfo& pi = P->prec;
   int grid = (int)((count + 255) / 256);
   if (grid > P->sm_count * 8) grid = P->sm_count * 8;
   if (pi.tf32) {
-    if (pi.slices == 1) split_kernel<true, 1><<<grid, 256, 0, P->stream>>>(src, dst, count);
-    else split_kernel<true, 2><<<grid, 256, 0, P->stream>>>(src, dst, count);
+    if (pi.slices == 1) split_kernel<true, 1, TS><<<grid, 256, 0, P->stream>>>(src, dst, count);
+    else split_kernel<true, 2, TS><<<grid, 256, 0, P->stream>>>(src, dst, count);
   } else if (pi.slices == 1) {
-    split_kernel<false, 1><<<grid, 256, 0, P->stream>>>(src, dst, count);
+    split_kernel<false, 1, TS><<<grid, 256, 0, P->stream>>>(src, dst, count);
   } else if (pi.slices == 2) {
-    split_kernel<false, 2><<<grid, 256, 0, P->stream>>>(src, dst, count);
+    split_kernel<false, 2, TS><<<grid, 256, 0, P->stream>>>(src, dst, count);
   } else {
-    split_kernel<false, 3><<<grid, 256, 0, P->stream>>>(src, dst, count);
+    split_kernel<false, 3, TS><<<grid, 256, 0, P->stream>>>(src, dst, count);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_split(kpme_plan_t P, const void* src, bool src_double, void* dst, int64_t count) {
+  if (src_double) return split_t<double>(P, (const double*)src, dst, count);
+  return split_t<float>(P, (const float*)src, dst, count);
 }
 
 }  // namespace kpme

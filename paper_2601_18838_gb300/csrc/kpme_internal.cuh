@@ -85,7 +85,15 @@ struct kpme_plan_s {
   double* d_qpsi = nullptr;        // <Q, Psi> for the virial
   int* d_status = nullptr;         // device status word
 
-  // meshes, K^3 each: Q is float64 for every arithmetic, Phi float32 (float64 for FP64)
+  // cell sort (float32-mesh arithmetics): tiles of tile^3 cells
+  int tile = 0;
+  int* d_tcount = nullptr;         // particles per tile
+  int* d_tstart = nullptr;         // exclusive prefix (tiles + 1)
+  int2* d_tslot = nullptr;         // (tile, slot) per particle
+  float4* d_rec_in = nullptr;      // per-particle records (cell, index, offsets), input order
+  float4* d_rec = nullptr;         // the same records sorted by tile
+  // meshes, K^3 each: Q float64 (FP64 form, or untiled fallback) / Qf float32, Phi float32
+  // (float64 for FP64)
   double* d_Q = nullptr;
   float* d_Qf = nullptr;           // float32 copy of Q for the CUDA-core float32 consumers
   void* d_Phi = nullptr;
@@ -147,6 +155,11 @@ cudaError_t launch_convert(const void* src, bool src_double, void* dst, bool dst
                            cudaStream_t s);
 cudaError_t launch_spread_raw(const kpme_params_t& p, int sm_count, cudaStream_t s, int64_t n, const double* x,
                               const double* q, float* Q, double* sumq);
+int choose_tile(int K, int order);
+cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double* q, double* sumq);
+cudaError_t launch_spread_tiled(kpme_plan_t P, int64_t n, const double* q, float* Q);
+cudaError_t launch_gather_tiled(kpme_plan_t P, int64_t n, const double* q, const float* Phi, double* phi, double* F,
+                                double* energy, bool correct);
 
 // skp_build.cu
 kpme_status_t build_skp_svd(kpme_plan_t P, SkpHost& out);
@@ -172,7 +185,7 @@ struct TcArgs {
   const JobList* jobs;
 };
 cudaError_t launch_mp_tc(kpme_plan_t P, const TcArgs& a);
-cudaError_t launch_split(kpme_plan_t P, const double* src, void* dst, int64_t count);
+cudaError_t launch_split(kpme_plan_t P, const void* src, bool src_double, void* dst, int64_t count);
 
 // gemm_oz.cu: error-free fixed-point split (KPME_BF16X10)
 struct OzArgs {

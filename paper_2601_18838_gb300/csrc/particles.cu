@@ -19,9 +19,12 @@ struct MeshGeom {
 __device__ __forceinline__ void mesh_coord(double x, double c, double L, int K, int& g, double& f) {
   double s = __dadd_rn(__ddiv_rn(__dsub_rn(x, c), L), 0.5);
   double u = __dmul_rn((double)K, s);
-  double m = fmod(u, (double)K);
-  if (m != 0.0 && m < 0.0) m = __dadd_rn(m, (double)K);
-  if (m >= (double)K) m = __dsub_rn(m, (double)K);
+  double m = u;   // fmod(u, K) == u exactly for u in [0, K): the common case skips fmod
+  if (!(u >= 0.0 && u < (double)K)) {
+    m = fmod(u, (double)K);
+    if (m != 0.0 && m < 0.0) m = __dadd_rn(m, (double)K);
+    if (m >= (double)K) m = __dsub_rn(m, (double)K);
+  }
   double fl = floor(m);
   g = (int)fl;
   f = __dsub_rn(m, fl);
@@ -307,6 +310,426 @@ cudaError_t launch_spread_raw(const kpme_params_t& p, int sm_count, cudaStream_t
     case 4: spread_kernel<float, 4><<<grid, kThreads, 0, s>>>(G, n, x, q, Q, sumq); break;
     case 6: spread_kernel<float, 6><<<grid, kThreads, 0, s>>>(G, n, x, q, Q, sumq); break;
     case 8: spread_kernel<float, 8><<<grid, kThreads, 0, s>>>(G, n, x, q, Q, sumq); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace kpme
+
+// ---------------------------------------------------------------------------------------
+// Cell-sorted, tile-staged spreading and gathering (float32 meshes).
+//
+// Particles are counting-sorted into tiles of T^3 mesh cells by their float64 cell index
+// (g = floor(u), the same decision as mesh_coord).  A particle in cell g touches the mesh
+// points g - j, j = 0..n-1, so tile t's particles touch the region [lo - (n-1), lo + T - 1]
+// per axis: (T + n - 1)^3 points, staged in shared memory.
+//   spread: each contribution q w0 w1 w2 is formed in double-float arithmetic (float32
+//           pairs with error-free products, no float64 units) and rounded once to float32;
+//           contributions are summed in the shared region and each region point is added to
+//           the global mesh once.
+//   gather: the region of Phi is loaded into shared memory with coalesced reads; each
+//           particle's potential and gradient come from shared memory.
+// ---------------------------------------------------------------------------------------
+namespace kpme {
+namespace {
+
+struct Tiling {
+  int K, T, KT;   // mesh, tile edge (cells), tiles per axis
+};
+
+__device__ __forceinline__ int tile_of(const int (&g)[3], const Tiling& t) {
+  return ((g[0] / t.T) * t.KT + g[1] / t.T) * t.KT + g[2] / t.T;
+}
+
+// One sorted record per particle (two float4, 32 bytes): the mesh cell g packed 10 bits per
+// axis, the particle index, and the fractional offsets f of the three axes as float pairs
+// (hi + lo carries f to ~48 bits).  The float64 mesh coordinate is computed once, here.
+__global__ void tile_count_kernel(MeshGeom G, Tiling tl, int64_t n, const double* __restrict__ x,
+                                  const double* __restrict__ q, int* __restrict__ count, int2* __restrict__ tile_slot,
+                                  float4* __restrict__ rec, double* __restrict__ sumq) {
+  double qs = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    int g[3];
+    float fh[3], fl[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      double f;
+      mesh_coord(x[3 * i + a], a == 0 ? G.c0 : (a == 1 ? G.c1 : G.c2), G.L, G.K, g[a], f);
+      fh[a] = (float)f;
+      fl[a] = (float)(f - (double)fh[a]);
+    }
+    const int t = tile_of(g, tl);
+    tile_slot[i] = make_int2(t, atomicAdd(count + t, 1));
+    const int gp = g[0] | (g[1] << 10) | (g[2] << 20);
+    rec[2 * i] = make_float4(__int_as_float(gp), __int_as_float((int)i), fh[0], fl[0]);
+    rec[2 * i + 1] = make_float4(fh[1], fl[1], fh[2], fl[2]);
+    if (sumq) qs += q[i];
+  }
+  if (sumq) {
+    const double s = block_sum_to_thread0<double>(qs);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(sumq, s);
+  }
+}
+
+// exclusive scan of count[0..nt) into start[0..nt] (one block of 1024 threads)
+__global__ void tile_scan_kernel(const int* __restrict__ count, int nt, int* __restrict__ start) {
+  __shared__ int part[1024];
+  const int per = (nt + 1023) / 1024;
+  const int b = threadIdx.x * per;
+  int s = 0;
+  for (int i = 0; i < per && b + i < nt; ++i) s += count[b + i];
+  part[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
+    __syncthreads();
+    part[threadIdx.x] += v;
+    __syncthreads();
+  }
+  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
+  for (int i = 0; i < per && b + i < nt; ++i) {
+    start[b + i] = run;
+    run += count[b + i];
+  }
+  if (threadIdx.x == 1023) start[nt] = part[1023];
+}
+
+__global__ void tile_scatter_kernel(int64_t n, const int2* __restrict__ tile_slot, const int* __restrict__ start,
+                                    const float4* __restrict__ rec_in, float4* __restrict__ rec_out) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    const int2 ts = tile_slot[i];
+    const int64_t d = start[ts.x] + ts.y;
+    rec_out[2 * d] = rec_in[2 * i];
+    rec_out[2 * d + 1] = rec_in[2 * i + 1];
+  }
+}
+
+// ---- double-float helpers (value = hi + lo, |lo| <= ulp(hi)/2) ----
+struct df {
+  float hi, lo;
+};
+__device__ __forceinline__ df df_from(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+__device__ __forceinline__ df df_mul(df a, df b) {
+  const float p = a.hi * b.hi;
+  const float e = fmaf(a.hi, b.hi, -p);                  // exact error of the leading product
+  const float t = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
+  const float h = p + t;
+  return {h, t - (h - p)};
+}
+__device__ __forceinline__ df df_add(df a, df b) {
+  const float s = a.hi + b.hi;
+  const float bb = s - a.hi;
+  const float e = (a.hi - (s - bb)) + (b.hi - bb);       // exact error of the leading sum
+  const float t = e + a.lo + b.lo;
+  const float h = s + t;
+  return {h, t - (h - s)};
+}
+__device__ __forceinline__ df df_scale(df a, float c) {  // c with few bits (small integers, 1/(k-1) below)
+  const float p = a.hi * c;
+  const float e = fmaf(a.hi, c, -p);
+  const float t = fmaf(a.lo, c, e);
+  const float h = p + t;
+  return {h, t - (h - p)};
+}
+
+// B-spline weights M_n(f + j) in double-float arithmetic (the order recursion of bspline()).
+template <int N>
+__device__ __forceinline__ void bspline_df(df f, df* w) {
+  const df neg_f = {-f.hi, -f.lo};
+  w[0] = f;
+  w[1] = df_add({1.0f, 0.0f}, neg_f);                      // 1 - f
+#pragma unroll
+  for (int j = 2; j < N; ++j) w[j] = {0.0f, 0.0f};
+#pragma unroll
+  for (int k = 3; k <= N; ++k) {
+    // 1/(k-1) as a double-float constant
+    const double invd = 1.0 / (double)(k - 1);
+    const df inv = {(float)invd, (float)(invd - (double)(float)invd)};
+    w[k - 1] = df_mul(df_mul(df_add({1.0f, 0.0f}, neg_f), w[k - 2]), inv);
+#pragma unroll
+    for (int j = k - 2; j >= 1; --j) {
+      const df a = df_add(f, {(float)j, 0.0f});                  // f + j
+      const df b = df_add({(float)(k - j), 0.0f}, neg_f);        // k - j - f
+      w[j] = df_mul(df_add(df_mul(a, w[j]), df_mul(b, w[j - 1])), inv);
+    }
+    w[0] = df_mul(df_mul(f, w[0]), inv);
+  }
+}
+
+// Lanes per particle: one lane per j0 plane of the n^3 stencil (4 for order 4, 8 for 6 / 8).
+template <int N>
+struct Lanes {
+  static constexpr int value = N <= 4 ? 4 : 8;
+};
+
+__device__ __forceinline__ float shfl_w(unsigned mask, float v, int src) { return __shfl_sync(mask, v, src); }
+__device__ __forceinline__ df shfl_w(unsigned mask, df v, int src) {
+  return {__shfl_sync(mask, v.hi, src), __shfl_sync(mask, v.lo, src)};
+}
+
+// Lane a < 3 of a particle's group holds axis a's weights in `mine`; every lane gets all three.
+template <int N, typename W>
+__device__ __forceinline__ void share_axes(const W (&mine)[N], W (&w)[3][N], int base, unsigned mask) {
+#pragma unroll
+  for (int a = 0; a < 3; ++a)
+#pragma unroll
+    for (int j = 0; j < N; ++j) w[a][j] = shfl_w(mask, mine[j], base + a);
+}
+
+template <int N, typename W>
+__device__ __forceinline__ W pick(const W (&w)[N], int j) {   // w[j] without local-memory indexing
+  W r = w[0];
+#pragma unroll
+  for (int k = 1; k < N; ++k)
+    if (k == j) r = w[k];
+  return r;
+}
+
+struct Rec {
+  int g[3], i;
+  df f[3];
+};
+__device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, int p) {
+  const float4 a = rec[2 * p], b = rec[2 * p + 1];
+  const int gp = __float_as_int(a.x);
+  Rec r;
+  r.g[0] = gp & 1023;
+  r.g[1] = (gp >> 10) & 1023;
+  r.g[2] = gp >> 20;
+  r.i = __float_as_int(a.y);
+  r.f[0] = {a.z, a.w};
+  r.f[1] = {b.x, b.y};
+  r.f[2] = {b.z, b.w};
+  return r;
+}
+
+// Tile-staged spreading: one CTA per tile of T^3 cells accumulates its particles' n^3
+// stencils into a shared (T + n - 1)^3 region, then adds the region's nonzeros to Q.
+// Each particle is handled by a group of LG lanes, one j0 plane of its stencil per lane.
+template <int N>
+__global__ void __launch_bounds__(kThreads) spread_tile_kernel(Tiling tl, const double* __restrict__ q,
+                                                               const int* __restrict__ start,
+                                                               const float4* __restrict__ rec, float* __restrict__ Q) {
+  extern __shared__ float region[];
+  constexpr int H = N - 1;
+  constexpr int LG = Lanes<N>::value;
+  const int D = tl.T + H;
+  const int K = tl.K;
+  const int t = blockIdx.x;
+  const int t2 = t % tl.KT, t1 = (t / tl.KT) % tl.KT, t0 = t / (tl.KT * tl.KT);
+  const int lo0 = t0 * tl.T - H, lo1 = t1 * tl.T - H, lo2 = t2 * tl.T - H;
+  const int p0 = start[t], p1 = start[t + 1];
+  if (p1 == p0) return;
+  for (int i = threadIdx.x; i < D * D * D; i += kThreads) region[i] = 0.0f;
+  __syncthreads();
+  const int gl = threadIdx.x % LG;
+  const int base = (threadIdx.x & 31) - gl;
+  for (int pb = p0; pb < p1; pb += kThreads / LG) {
+    const int p = pb + threadIdx.x / LG;
+    const bool active = p < p1;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) continue;
+    const Rec r = load_rec(rec, p);
+    df mine[N], w[3][N];
+    bspline_df<N>(gl == 0 ? r.f[0] : (gl == 1 ? r.f[1] : r.f[2]), mine);
+    share_axes<N>(mine, w, base, mask);
+    if (gl >= N) continue;
+    const df qw0 = df_mul(df_from(q[r.i]), pick<N>(w[0], gl));
+    const int b0 = r.g[0] - t0 * tl.T + H - gl, b1 = r.g[1] - t1 * tl.T + H, b2 = r.g[2] - t2 * tl.T + H;
+#pragma unroll
+    for (int j1 = 0; j1 < N; ++j1) {
+      const df w01 = df_mul(qw0, w[1][j1]);
+      float* row = region + (b0 * D + (b1 - j1)) * D + b2;
+#pragma unroll
+      for (int j2 = 0; j2 < N; ++j2) {
+        const df c = df_mul(w01, w[2][j2]);   // rounded once to float32 below
+        atomicAdd(row - j2, c.hi + c.lo);
+      }
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < D * D * D; idx += kThreads) {
+    const float v = region[idx];
+    if (v == 0.0f) continue;
+    const int l2 = idx % D, l1 = (idx / D) % D, l0 = idx / (D * D);
+    int k0 = lo0 + l0, k1 = lo1 + l1, k2 = lo2 + l2;
+    k0 += k0 < 0 ? K : 0;
+    k1 += k1 < 0 ? K : 0;
+    k2 += k2 < 0 ? K : 0;
+    atomicAdd(Q + ((int64_t)k0 * K + k1) * K + k2, v);
+  }
+}
+
+// Tile-staged gathering: the CTA stages its (T + n - 1)^3 region of Phi in shared memory;
+// each particle's lane group sums one j0 plane per lane and reduces with shuffles.
+template <int N>
+__global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tiling tl, const double* __restrict__ q,
+                                                               const int* __restrict__ start,
+                                                               const float4* __restrict__ rec,
+                                                               const float* __restrict__ Phi,
+                                                               double* __restrict__ phi_out, double* __restrict__ F_out,
+                                                               double* __restrict__ energy,
+                                                               const double* __restrict__ sumq, double corr_c,
+                                                               double ke) {
+  extern __shared__ float region[];
+  constexpr int H = N - 1;
+  constexpr int LG = Lanes<N>::value;
+  const int D = tl.T + H;
+  const int K = tl.K;
+  const int t = blockIdx.x;
+  const int t2 = t % tl.KT, t1 = (t / tl.KT) % tl.KT, t0 = t / (tl.KT * tl.KT);
+  const int lo0 = t0 * tl.T - H, lo1 = t1 * tl.T - H, lo2 = t2 * tl.T - H;
+  const int p0 = start[t], p1 = start[t + 1];
+  if (p1 == p0) return;
+  for (int idx = threadIdx.x; idx < D * D * D; idx += kThreads) {
+    const int l2 = idx % D, l1 = (idx / D) % D, l0 = idx / (D * D);
+    int k0 = lo0 + l0, k1 = lo1 + l1, k2 = lo2 + l2;
+    k0 += k0 < 0 ? K : 0;
+    k1 += k1 < 0 ? K : 0;
+    k2 += k2 < 0 ? K : 0;
+    region[idx] = Phi[((int64_t)k0 * K + k1) * K + k2];
+  }
+  __syncthreads();
+  const double shift = corr_c * (sumq ? *sumq : 0.0);
+  const double gscale = (double)K / G.L;
+  const int gl = threadIdx.x % LG;
+  const int base = (threadIdx.x & 31) - gl;
+  double e = 0.0;
+  for (int pb = p0; pb < p1; pb += kThreads / LG) {
+    const int p = pb + threadIdx.x / LG;
+    const bool active = p < p1;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) continue;
+    const Rec r = load_rec(rec, p);
+    float mw[N], mdw[N], w[3][N], dw[3][N];
+    bspline<float, N>(gl == 0 ? r.f[0].hi : (gl == 1 ? r.f[1].hi : r.f[2].hi), mw, mdw);
+    share_axes<N>(mw, w, base, mask);
+    share_axes<N>(mdw, dw, base, mask);
+    float pv = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
+    if (gl < N) {   // this lane's j0 plane of the stencil
+      const int b0 = r.g[0] - t0 * tl.T + H - gl, b1 = r.g[1] - t1 * tl.T + H, b2 = r.g[2] - t2 * tl.T + H;
+      float s_p = 0.f, s_1 = 0.f, s_2 = 0.f;
+#pragma unroll
+      for (int j1 = 0; j1 < N; ++j1) {
+        const float* row = region + (b0 * D + (b1 - j1)) * D + b2;
+        float tv = 0.f, td = 0.f;
+#pragma unroll
+        for (int j2 = 0; j2 < N; ++j2) {
+          const float v = row[-j2];
+          tv = fmaf(w[2][j2], v, tv);
+          td = fmaf(dw[2][j2], v, td);
+        }
+        s_p = fmaf(w[1][j1], tv, s_p);
+        s_1 = fmaf(dw[1][j1], tv, s_1);
+        s_2 = fmaf(w[1][j1], td, s_2);
+      }
+      const float w0 = pick<N>(w[0], gl), d0 = pick<N>(dw[0], gl);
+      pv = w0 * s_p;
+      g0 = d0 * s_p;
+      g1 = w0 * s_1;
+      g2 = w0 * s_2;
+    }
+#pragma unroll
+    for (int o = LG / 2; o > 0; o >>= 1) {
+      pv += __shfl_xor_sync(mask, pv, o);
+      g0 += __shfl_xor_sync(mask, g0, o);
+      g1 += __shfl_xor_sync(mask, g1, o);
+      g2 += __shfl_xor_sync(mask, g2, o);
+    }
+    if (gl != 0) continue;
+    const double phi = ((double)pv - shift) * ke;
+    const double qi = q ? q[r.i] : 0.0;
+    if (phi_out) phi_out[r.i] = phi;
+    if (F_out) {
+      const double s = -qi * ke * gscale;
+      F_out[3 * (int64_t)r.i + 0] = s * (double)g0;
+      F_out[3 * (int64_t)r.i + 1] = s * (double)g1;
+      F_out[3 * (int64_t)r.i + 2] = s * (double)g2;
+    }
+    e += 0.5 * qi * phi;
+  }
+  if (energy) {
+    double s = block_sum_to_thread0<double>(e);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(energy, s);
+  }
+}
+
+Tiling tiling_of(kpme_plan_t P) {
+  Tiling t;
+  t.K = P->p.K;
+  t.T = P->tile;
+  t.KT = P->p.K / P->tile;
+  return t;
+}
+
+}  // namespace
+
+int choose_tile(int K, int order) {
+  int T = K > 64 ? 16 : 8;
+  while (T > 1 && K % T) T >>= 1;
+  if (T < order - 1) T = order - 1;   // regions must stay inside the periodic mesh
+  return K % T == 0 ? T : 0;
+}
+
+cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double* q, double* sumq) {
+  if (n <= 0) return cudaSuccess;
+  const Tiling tl = tiling_of(P);
+  const int nt = tl.KT * tl.KT * tl.KT;
+  cudaError_t e = cudaMemsetAsync(P->d_tcount, 0, (size_t)nt * sizeof(int), P->stream);
+  if (e != cudaSuccess) return e;
+  const int grid = grid_for(P, n);
+  tile_count_kernel<<<grid, kThreads, 0, P->stream>>>(geom(P), tl, n, x, q, P->d_tcount, P->d_tslot, P->d_rec_in,
+                                                      sumq);
+  tile_scan_kernel<<<1, 1024, 0, P->stream>>>(P->d_tcount, nt, P->d_tstart);
+  tile_scatter_kernel<<<grid, kThreads, 0, P->stream>>>(n, P->d_tslot, P->d_tstart, P->d_rec_in, P->d_rec);
+  return cudaGetLastError();
+}
+
+template <int N>
+void spread_tiled(kpme_plan_t P, const Tiling& tl, int nt, size_t smem, const double* q, float* Q) {
+  cudaFuncSetAttribute(spread_tile_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  spread_tile_kernel<N><<<nt, kThreads, smem, P->stream>>>(tl, q, P->d_tstart, P->d_rec, Q);
+}
+
+template <int N>
+void gather_tiled(kpme_plan_t P, const Tiling& tl, int nt, size_t smem, const double* q, const float* Phi,
+                  double* phi, double* F, double* energy, double c) {
+  cudaFuncSetAttribute(gather_tile_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  gather_tile_kernel<N><<<nt, kThreads, smem, P->stream>>>(geom(P), tl, q, P->d_tstart, P->d_rec, Phi, phi, F,
+                                                             energy, P->d_sumq, c, P->p.coulomb_k);
+}
+
+cudaError_t launch_spread_tiled(kpme_plan_t P, int64_t n, const double* q, float* Q) {
+  if (n <= 0) return cudaSuccess;
+  const Tiling tl = tiling_of(P);
+  const int nt = tl.KT * tl.KT * tl.KT;
+  const int D = tl.T + P->p.order - 1;
+  const size_t smem = (size_t)D * D * D * sizeof(float);
+  switch (P->p.order) {
+    case 4: spread_tiled<4>(P, tl, nt, smem, q, Q); break;
+    case 6: spread_tiled<6>(P, tl, nt, smem, q, Q); break;
+    case 8: spread_tiled<8>(P, tl, nt, smem, q, Q); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_gather_tiled(kpme_plan_t P, int64_t n, const double* q, const float* Phi, double* phi, double* F,
+                                double* energy, bool correct) {
+  if (n <= 0) return cudaSuccess;
+  const Tiling tl = tiling_of(P);
+  const int nt = tl.KT * tl.KT * tl.KT;
+  const int D = tl.T + P->p.order - 1;
+  const size_t smem = (size_t)D * D * D * sizeof(float);
+  const double c = correct ? P->skp.c : 0.0;
+  switch (P->p.order) {
+    case 4: gather_tiled<4>(P, tl, nt, smem, q, Phi, phi, F, energy, c); break;
+    case 6: gather_tiled<6>(P, tl, nt, smem, q, Phi, phi, F, energy, c); break;
+    case 8: gather_tiled<8>(P, tl, nt, smem, q, Phi, phi, F, energy, c); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -28,6 +28,6 @@ def test_large_box_against_fft_pme():
     e_W = abs(out["virial"].item() - ref["W"]) / abs(ref["W"])
     print(f"large: R={R} skp err {err:.2e} | vs FFT-PME phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e} W {e_W:.2e}")
     assert e_phi < 2e-6 and e_f < 1e-5 and e_E < 2e-6 and e_W < 2e-6
-    # charge conservation of the mesh at full size
+    # charge conservation of the float32 mesh at full size (rounding of K^3 values)
     Q = host(plan.spread(x, q))
-    assert abs(Q.sum() - s.q.sum()) < 1e-6
+    assert abs(Q.sum() - s.q.sum()) < 1e-6 * np.abs(Q).sum()
