@@ -22,7 +22,6 @@
 namespace kpme {
 namespace {
 
-constexpr int kThreads = 320;
 constexpr int kBM = 128;
 constexpr int kSlices = 4;
 constexpr int kProducts = 10;
@@ -139,57 +138,65 @@ __device__ __forceinline__ float pow2f(int k) {
   return (k >= -126 && k <= 127) ? __int_as_float((127 + k) << 23) : ldexpf(1.0f, k);
 }
 
-// Four fixed-point digits of 8 values scaled by 2^(7 - e): writes slices s = 0..3 of one
-// 16-byte group (8 consecutive k) as packed bf16, each slice carrying its own power of two.
-// Input: one float32 per value, or a float32 hi/lo pair (hi + lo = the float64 value to
-// about 2^-48).  Scaling by a power of two, rint and the subtraction of the digit are exact
-// in float32; the lo part joins the first remainder (rounded at 2^-25 of the digit scale,
-// below the last digit's resolution).
-template <typename TIN>
-__device__ __forceinline__ void slice8(const TIN* v, int e, uint4 (&o)[kSlices]) {
-  const float up = pow2f(7 - e);
-  float t[8];
-  float d[kSlices][8];
+// Four fixed-point digits of 8 float32 values relative to 2^e (|v| < 2^e): slice s holds
+// d_s 2^(e - 7 - 8s) with integers d_s in [-128, 128], written as packed bf16 (exact: at most
+// 8 significant bits).  Each digit is taken by rounding the running remainder to a multiple
+// of q_s = 2^(e - 7 - 8s) with the add-and-subtract of C_s = 1.5 * 2^(e + 16 - 8s): for
+// |r| < 2^(e + 15 - 8s) the float32 sum r + C_s rounds (to nearest, ties to even) onto the
+// grid of q_s, so (r + C_s) - C_s is round(r / q_s) q_s exactly and r - that is exact too.
+// The digits equal those of rint(r / q_s) at each step.  Exponents whose C_s would leave the
+// normal float32 range take the same steps with rintf.
+__device__ __forceinline__ float magic15(int k) { return __int_as_float(((127 + k) << 23) | (1 << 22)); }
+
+__device__ __forceinline__ void slice8(const float* v, int e, uint4 (&o)[kSlices]) {
+  float h[kSlices][8];
+  if (e + 16 <= 127 && e - 8 >= -126) {
+    float C[kSlices];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    float th, tl = 0.0f;
-    if constexpr (sizeof(TIN) == 8) {
-      th = v[i].x * up;
-      tl = v[i].y * up;
-    } else {
-      th = v[i] * up;
-    }
-    const float d0 = rintf(th);
-    d[0][i] = d0;
-    t[i] = ((th - d0) + tl) * 256.0f;
-  }
-#pragma unroll
-  for (int s = 1; s < kSlices; ++s) {
+    for (int sl = 0; sl < kSlices; ++sl) C[sl] = magic15(e + 16 - 8 * sl);
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
-      const float di = rintf(t[i]);
-      t[i] = (t[i] - di) * 256.0f;
-      d[s][i] = di;
+      float r = v[i];
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        const float t = __fadd_rn(r, C[sl]);
+        h[sl][i] = __fsub_rn(t, C[sl]);
+        r = __fsub_rn(r, h[sl][i]);
+      }
+    }
+  } else {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      float r = v[i];
+#pragma unroll
+      for (int sl = 0; sl < kSlices; ++sl) {
+        const float q = ldexpf(1.0f, e - 7 - 8 * sl);
+        h[sl][i] = rintf(r / q) * q;
+        r = r - h[sl][i];
+      }
     }
   }
 #pragma unroll
-  for (int s = 0; s < kSlices; ++s) {
-    const float dn = pow2f(e - 7 - 8 * s);
-    o[s].x = pack_bf16(d[s][0] * dn, d[s][1] * dn);
-    o[s].y = pack_bf16(d[s][2] * dn, d[s][3] * dn);
-    o[s].z = pack_bf16(d[s][4] * dn, d[s][5] * dn);
-    o[s].w = pack_bf16(d[s][6] * dn, d[s][7] * dn);
+  for (int sl = 0; sl < kSlices; ++sl) {
+    o[sl].x = pack_bf16(h[sl][0], h[sl][1]);
+    o[sl].y = pack_bf16(h[sl][2], h[sl][3]);
+    o[sl].z = pack_bf16(h[sl][4], h[sl][5]);
+    o[sl].w = pack_bf16(h[sl][6], h[sl][7]);
   }
 }
 
-// Persistent CTA: 10 warps, work items (m-tile, n-tile, job) strided by gridDim.x, every role
-// walking the same sequence of (item, pair, 64-wide chunk) so the shared ring counters agree.
-//   warp 0      : TMA of the four factor slices per chunk
-//   warp 1      : TMEM allocation; lane 0 issues 10 products per 16-wide k step
-//   warps 2..5  : converters, one operand row per thread
-//   warps 6..9  : epilogue, TMEM lanes 32 (warp % 4) .. + 31, one output row per thread
-template <int BN, typename TIN, bool A_TMA>
-__global__ void __launch_bounds__(kThreads, 1)
+// Persistent CTA, work items (m-tile, n-tile, job) strided by gridDim.x, every role walking
+// the same sequence of (item, pair, 64-wide chunk) so the shared ring counters agree.
+//   warp 0            : TMA of the four factor slices per chunk (and of the A slices)
+//   warp 1            : TMEM allocation; lane 0 issues 10 products per 16-wide k step
+//   warps 2..NCONV+1  : converters (none when TMA brings pre-cut A slices): row 32 (c % 4)
+//                       + lane, k groups of part c / 4 of the chunk
+//   last 4 warps      : epilogue, TMEM lanes 32 (warp % 4) .. + 31, one output row per thread
+template <int NCONV>
+constexpr int oz_threads() { return 64 + 32 * NCONV + 128; }
+
+template <int BN, int NCONV, bool A_TMA>
+__global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
     mp_oz_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, OzParams prm) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -202,6 +209,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* acc_empty = acc_full + 2;
   uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
+  // per-warp column maxima of the epilogue (4 x BN)
+  unsigned int* red = reinterpret_cast<unsigned int*>(smem + S * prm.stage_bytes + 256);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m_tiles = (prm.M + kBM - 1) / kBM;
@@ -211,7 +220,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < S; ++s) {
-      mbar_init(&full_a[s], A_TMA ? 1 : 128);
+      mbar_init(&full_a[s], A_TMA ? 1 : 32 * NCONV);
       mbar_init(&full_b[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -314,82 +323,91 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else if (warp < 6) {
+  } else if (warp < 2 + NCONV) {
     // ---------------- converters (operand rows sliced on the fly) ----------------
-    if constexpr (A_TMA) {
-      // the A slices come pre-cut by TMA: nothing to convert
-    } else {
-    const int r = 32 * (warp - 2) + lane;
-    int it = 0;
-    bool ok = true;
-    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
-      int m0, n0, job;
-      decode(w, m0, n0, job);
-      const int row = m0 + r;
-      const bool valid = row < prm.M;
-      const int p0 = prm.start[job], p1 = prm.start[job + 1];
-      for (int p = p0; p < p1 && ok; ++p) {
-        const int2 pr = prm.pairs[p];
-        const TIN* rowp = reinterpret_cast<const TIN*>(prm.in) + (int64_t)pr.x * prm.in_bs + (int64_t)row * prm.Kr;
+    if constexpr (!A_TMA) {
+      constexpr int kParts = NCONV / 4;             // threads per row
+      constexpr int kG = (kChunk / 8) / kParts;     // 8-value groups per thread and chunk
+      constexpr int kV = 8 * kG;
+      const int ci = warp - 2;
+      const int r = 32 * (ci % 4) + lane;
+      const int j0 = (ci / 4) * kG;
+      int it = 0;
+      bool ok = true;
+      // One unit = (item, pair, 64-wide chunk).  The loads of unit u + 1 are issued before
+      // unit u is sliced, so their latency overlaps the wait for a free stage and the slicing.
+      float vc[kV];
+      float rm_c = 0.0f;
+      bool pend = false;
+      auto process = [&](const float (&v)[kV], float rm) -> bool {
+        const int s = it % S;
+        const uint32_t ph = (uint32_t)(it / S) & 1u;
+        if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) return false;
         int e = 0;
-        if (valid) frexpf(prm.rowmax_in[(int64_t)pr.x * prm.rm_in_bs + row], &e);
-        for (int c = 0; c < kchunks; ++c, ++it) {
-          const int s = it % S;
-          const uint32_t ph = (uint32_t)(it / S) & 1u;
-          if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) {
-            ok = false;
-            break;
-          }
-          uint8_t* sa = smem + s * prm.stage_bytes;
-          const int kc = c * kChunk;
-          // all loads of a pass are issued before any use, so one memory latency per pass
-          constexpr int kPasses = sizeof(TIN) == 8 ? 2 : 1;
-          constexpr int kGroups = 8 / kPasses;
+        frexpf(rm, &e);
+        uint8_t* sa = smem + s * prm.stage_bytes;
 #pragma unroll
-          for (int h = 0; h < kPasses; ++h) {
-            TIN v[kGroups * 8];
+        for (int jj = 0; jj < kG; ++jj) {
+          const int j = j0 + jj;
+          uint4 o[kSlices];
+          slice8(v + 8 * jj, e, o);
+          const int off = r * 128 + ((j ^ (r & 7)) << 4);
 #pragma unroll
-            for (int g = 0; g < kGroups; ++g) {
-              const int k = kc + 8 * (h * kGroups + g);
-              if (valid && k < prm.Kr) {
+          for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint4*>(sa + sl * kASlice + off) = o[sl];
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        mbar_arrive(&full_a[s]);
+        ++it;
+        return true;
+      };
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        int m0, n0, job;
+        decode(w, m0, n0, job);
+        const int row = m0 + r;
+        const bool valid = row < prm.M;
+        const int p0 = prm.start[job], p1 = prm.start[job + 1];
+        for (int p = p0; p < p1 && ok; ++p) {
+          const int2 pr = prm.pairs[p];
+          const float* rowp = reinterpret_cast<const float*>(prm.in) + (int64_t)pr.x * prm.in_bs + (int64_t)row * prm.Kr;
+          const float rm = valid ? prm.rowmax_in[(int64_t)pr.x * prm.rm_in_bs + row] : 0.0f;
+          for (int c = 0; c < kchunks; ++c) {
+            float vn[kV];
+            const int kc = c * kChunk + 8 * j0;
 #pragma unroll
-                for (int i = 0; i < 8; i += 16 / (int)sizeof(TIN)) {
-                  const float4 x = *reinterpret_cast<const float4*>(rowp + k + i);
-                  if constexpr (sizeof(TIN) == 4) {
-                    v[8 * g + i] = x.x; v[8 * g + i + 1] = x.y; v[8 * g + i + 2] = x.z; v[8 * g + i + 3] = x.w;
-                  } else {
-                    v[8 * g + i] = make_float2(x.x, x.y);
-                    v[8 * g + i + 1] = make_float2(x.z, x.w);
-                  }
-                }
-              } else {
-#pragma unroll
-                for (int i = 0; i < 8; ++i) v[8 * g + i] = TIN{};
-              }
+            for (int g = 0; g < kV / 4; ++g) {
+              const int k = kc + 4 * g;
+              float4 x = make_float4(0.f, 0.f, 0.f, 0.f);
+              if (valid && k < prm.Kr) x = *reinterpret_cast<const float4*>(rowp + k);
+              vn[4 * g] = x.x;
+              vn[4 * g + 1] = x.y;
+              vn[4 * g + 2] = x.z;
+              vn[4 * g + 3] = x.w;
+            }
+            if (pend && !process(vc, rm_c)) {
+              ok = false;
+              break;
             }
 #pragma unroll
-            for (int g = 0; g < kGroups; ++g) {
-              const int j = h * kGroups + g;
-              uint4 o[kSlices];
-              slice8(v + 8 * g, e, o);
-              const int off = r * 128 + ((j ^ (r & 7)) << 4);
-#pragma unroll
-              for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint4*>(sa + sl * kASlice + off) = o[sl];
-            }
+            for (int i = 0; i < kV; ++i) vc[i] = vn[i];
+            rm_c = rm;
+            pend = true;
           }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          mbar_arrive(&full_a[s]);
         }
       }
-    }
+      if (pend && ok) process(vc, rm_c);
     }
   } else {
     // ---------------- epilogue ----------------
-    const int r = 32 * (warp & 3) + lane;
-    const uint32_t lane_base = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+    // Every epilogue thread runs the same number of items and, where the row maxima are
+    // combined in shared memory, the same number of named-barrier syncs, whatever happens
+    // to its waits (a failed wait only skips work).
+    const int wq = warp & 3;
+    const int r = 32 * wq + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * wq) << 16);
+    const bool combine = prm.mode == 0 && prm.rowmax_out != nullptr && (prm.Kr % 32) == 0;
     int pc = 0;
     bool ok = true;
-    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
       int m0, n0, job;
       decode(w, m0, n0, job);
       const int row = m0 + r;
@@ -398,10 +416,13 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
       for (int pl = 0; pl < np; ++pl, ++pc) {
+        if (!ok) continue;
         const int buf = pc & 1;
-        if (!mbar_wait(&acc_full[buf], (uint32_t)(pc >> 1) & 1u, abort_flag, prm.status)) {
+        const bool got = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(pc >> 1) & 1u, abort_flag,
+                                                           prm.status));
+        if (!got) {
           ok = false;
-          break;
+          continue;
         }
         fence_after();
 #pragma unroll
@@ -416,32 +437,59 @@ __global__ void __launch_bounds__(kThreads, 1)
         fence_before();
         mbar_arrive(&acc_empty[buf]);
       }
-      if (!ok || *abort_flag || row >= prm.M) continue;
+      const bool live = ok && !*abort_flag && row < prm.M;
       if (prm.mode == 1) {
-        float* o = prm.out + (int64_t)n0 * prm.M + row;
+        if (live) {
+          float* o = prm.out + (int64_t)n0 * prm.M + row;
 #pragma unroll
-        for (int c = 0; c < BN; ++c) atomicAdd(o + (int64_t)c * prm.M, acc[c]);
-      } else {
+          for (int c = 0; c < BN; ++c) atomicAdd(o + (int64_t)c * prm.M, acc[c]);
+        }
+        continue;
+      }
+      if (live) {
         float* o = prm.out + (int64_t)job * prm.out_bs + (int64_t)n0 * prm.M + row;
 #pragma unroll
         for (int c = 0; c < BN; ++c) o[(int64_t)c * prm.M] = acc[c];
-        if (prm.rowmax_out != nullptr) {
-          // row maxima of the consuming stage: its rows are (n, row / K) with n the output column
-          const int K = prm.Kr;
-          const int64_t rows_next = prm.M / K;
-          unsigned int* dst = reinterpret_cast<unsigned int*>(prm.rowmax_out + (int64_t)job * prm.rm_out_bs) +
-                              (int64_t)n0 * rows_next + row / K;
-          if ((K % 32) == 0) {
+      }
+      if (prm.rowmax_out == nullptr) continue;
+      // Row maxima of the consuming stage: its row (n, row / K) spans K consecutive rows of
+      // this output column n, so the maximum combines lanes, warps and (for K > 128) tiles.
+      const int K = prm.Kr;
+      const int64_t rows_next = prm.M / K;
+      unsigned int* dst = reinterpret_cast<unsigned int*>(prm.rowmax_out + (int64_t)job * prm.rm_out_bs) +
+                          (int64_t)n0 * rows_next;
+      if (combine) {
+        // warp maxima per column, column c kept by lane c % 32
+        constexpr int kJ = (BN + 31) / 32;
+        unsigned int mx[kJ];
 #pragma unroll
-            for (int c = 0; c < BN; ++c) {
-              const unsigned int mx = __reduce_max_sync(0xffffffffu, __float_as_uint(fabsf(acc[c])));
-              if (lane == 0) atomicMax(dst + (int64_t)c * rows_next, mx);
-            }
-          } else {
+        for (int j = 0; j < kJ; ++j) mx[j] = 0u;
 #pragma unroll
-            for (int c = 0; c < BN; ++c) atomicMax(dst + (int64_t)c * rows_next, __float_as_uint(fabsf(acc[c])));
+        for (int c = 0; c < BN; ++c) {
+          const unsigned int m = __reduce_max_sync(0xffffffffu, live ? __float_as_uint(fabsf(acc[c])) : 0u);
+          if ((c & 31) == lane) mx[c >> 5] = m;
+        }
+#pragma unroll
+        for (int j = 0; j < kJ; ++j)
+          if (32 * j + lane < BN) red[wq * BN + 32 * j + lane] = mx[j];
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+        // the first warp of each consuming row in this tile combines and publishes
+        const int g = (m0 + 32 * wq) / K;
+        const bool leader = wq == 0 || (m0 + 32 * (wq - 1)) / K != g;
+        if (leader && m0 + 32 * wq < prm.M) {
+#pragma unroll
+          for (int j = 0; j < kJ; ++j) {
+            const int c = 32 * j + lane;
+            if (c >= BN) continue;
+            unsigned int v = red[wq * BN + c];
+            for (int w2 = wq + 1; w2 < 4 && (m0 + 32 * w2) / K == g; ++w2) v = max(v, red[w2 * BN + c]);
+            if (v != 0u) atomicMax(dst + (int64_t)c * rows_next + g, v);
           }
         }
+        asm volatile("bar.sync 1, 128;" ::: "memory");
+      } else if (live) {
+#pragma unroll
+        for (int c = 0; c < BN; ++c) atomicMax(dst + (int64_t)c * rows_next + row / K, __float_as_uint(fabsf(acc[c])));
       }
     }
   }
@@ -503,26 +551,28 @@ __global__ void slice_rows_kernel(const TIN* __restrict__ in, int64_t rows_total
   }
 }
 
-template <int BN, typename TIN, bool A_TMA>
+template <int BN, int NCONV, bool A_TMA>
 cudaError_t launch_bn(cudaStream_t st, const CUtensorMap* tmA, const CUtensorMap* tmB, const OzParams& prm, dim3 grid,
                       int smem) {
-  auto kern = mp_oz_kernel<BN, TIN, A_TMA>;
+  auto kern = mp_oz_kernel<BN, NCONV, A_TMA>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, kThreads, smem, st>>>(*tmA, *tmB, prm);
+  kern<<<grid, oz_threads<NCONV>(), smem, st>>>(*tmA, *tmB, prm);
   return cudaGetLastError();
 }
 
+// pre-cut A by TMA: no converter warps; float32 A: 8 converter warps (4 for BN = 96, whose
+// epilogue needs the registers)
 template <int BN>
 cudaError_t launch_mode(const OzArgs& a, cudaStream_t st, const OzParams& prm, dim3 grid, int smem) {
-  if (a.tmA) return launch_bn<BN, float, true>(st, a.tmA, a.tmB, prm, grid, smem);
-  return launch_bn<BN, float, false>(st, a.tmB, a.tmB, prm, grid, smem);
+  if (a.tmA) return launch_bn<BN, 0, true>(st, a.tmA, a.tmB, prm, grid, smem);
+  return launch_bn<BN, (BN <= 64 ? 8 : 4), false>(st, a.tmB, a.tmB, prm, grid, smem);
 }
 
 }  // namespace
 
 int oz_stage_bytes(int bn) { return kSlices * kASlice + kSlices * bn * 128; }
-int oz_smem_bytes(int bn, int stages) { return stages * oz_stage_bytes(bn) + 1024 + 256; }
+int oz_smem_bytes(int bn, int stages) { return stages * oz_stage_bytes(bn) + 1024 + 256 + 4 * bn * 4; }
 
 cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a) {
   OzParams prm{};
