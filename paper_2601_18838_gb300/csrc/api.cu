@@ -3,6 +3,7 @@
 // float64 reductions), with the mode products ordered as the three reshaped steps of
 // Algorithm 2.
 #include "kpme_internal.cuh"
+#include <climits>
 
 #include <algorithm>
 #include <cmath>
@@ -242,8 +243,25 @@ kpme_status_t install_skp(kpme_plan_t P) {
     const int nt = g.t1 - g.t0;
     for (int t = g.t0; t <= g.t1; ++t) g.stage2.h_start.push_back(t - g.t0);
     for (int t = g.t0; t < g.t1; ++t) g.stage2.h_pairs.push_back(make_int2(S.outer_of[t], t));
+    // split-K over terms.  Floating-slice tensor forms accumulate a split's terms in the
+    // tensor core's truncating float32 accumulator, so they keep many short splits.  The
+    // other forms (error-free split: one drain per term; CUDA cores) take the split count
+    // with the smallest makespan: ceil(items / SMs) rounds of ceil(nt / splits) terms, plus
+    // about one term's worth of per-item work (the final atomic accumulation).
     int splits = (2 * P->sm_count + m_tiles * n_tiles - 1) / (m_tiles * n_tiles);
     splits = std::max(1, std::min(splits, nt));
+    if (!pi.tensor || pi.oz) {
+      const int64_t tiles = (int64_t)m_tiles * n_tiles;
+      int64_t best = INT64_MAX;
+      for (int sp = 1; sp <= nt; ++sp) {
+        const int64_t rounds = (tiles * sp + P->sm_count - 1) / P->sm_count;
+        const int64_t cost = rounds * ((nt + sp - 1) / sp + 1);
+        if (cost < best) {
+          best = cost;
+          splits = sp;
+        }
+      }
+    }
     g.splits = splits;
     int pos = 0;
     g.stage3.h_start.push_back(0);
@@ -411,7 +429,8 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
   return KPME_OK;
 }
 
-kpme_status_t virial(kpme_plan_t P, MeshRef Q, const double* energy, double* out) {
+// Virial mesh part: Ψ = Q ×1 V ×2 V ×3 V with the separable kernel T' and ⟨Q, Ψ⟩ into d_qpsi.
+kpme_status_t virial_mesh(kpme_plan_t P, MeshRef Q) {
   const int K = P->p.K, M = K * K;
   const int64_t k3 = K3(P);
   const bool dbl = P->prec.fp64;
@@ -427,6 +446,11 @@ kpme_status_t virial(kpme_plan_t P, MeshRef Q, const double* energy, double* out
   KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp2, 0, P->d_facv, P->d_Psi, 0, M, K, K, P->single, 0, P->stream));
   KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_qpsi, 0, sizeof(double), P->stream));
   KPME_CUDA_TRY(P, launch_dot(P, Qv, P->d_Psi, k3, P->d_qpsi));
+  return KPME_OK;
+}
+
+// W = E − (2π²/β²)·½(⟨Q,Ψ⟩ − T'(0)(Σq)²) from the energy and the mesh part.
+kpme_status_t virial_finish(kpme_plan_t P, const double* energy, double* out) {
   const double L = 2.0 * P->p.radius;
   const double t0 = 1.0 / (M_PI * L * L * L);
   const double coef = 2.0 * M_PI * M_PI / (P->p.beta * P->p.beta);
@@ -552,6 +576,10 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->sm_count = prop.multiProcessorCount;
   P->cc_major = prop.major;
   P->cc_minor = prop.minor;
+  if (cudaStreamCreateWithFlags(&P->side_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&P->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(KPME_ERR_CUDA);
   if (P->prec.tensor && (P->cc_major != 10 || p.K % 16 != 0)) {
     P->last_error = "tensor-core precisions need an sm_103 device and K divisible by 16";
     kpme_destroy(P);
@@ -601,6 +629,12 @@ void kpme_destroy(kpme_plan_t P) {
   cudaStreamSynchronize(P->stream);
   drop_graph(P);
   if (P->capture_stream) cudaStreamDestroy(P->capture_stream);
+  if (P->side_stream) {
+    cudaStreamSynchronize(P->side_stream);
+    cudaStreamDestroy(P->side_stream);
+  }
+  if (P->ev_fork) cudaEventDestroy(P->ev_fork);
+  if (P->ev_join) cudaEventDestroy(P->ev_join);
   release_skp_buffers(P);
   release_mesh_buffers(P);
   free_joblist(P->single);
@@ -752,6 +786,19 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
     StepScope sc(P, STEP_SPREAD, n > 0 ? (tiled(P) ? 4 : 1) : 0);
     if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
   }
+  // the virial's mesh part only reads Q: outside profiling it runs on a forked branch,
+  // concurrently with the SKP stages, and joins before the finalisation
+  const bool fork = vir && n > 0 && !P->profiling && P->side_stream;
+  if (fork) {
+    KPME_CUDA_TRY(P, cudaEventRecord(P->ev_fork, P->stream));
+    KPME_CUDA_TRY(P, cudaStreamWaitEvent(P->side_stream, P->ev_fork, 0));
+    cudaStream_t main_stream = P->stream;
+    P->stream = P->side_stream;
+    st = virial_mesh(P, m);
+    P->stream = main_stream;
+    if (st != KPME_OK) return st;
+    KPME_CUDA_TRY(P, cudaEventRecord(P->ev_join, P->side_stream));
+  }
   if (n > 0) {
     if ((st = contract(P, m, P->d_Phi)) != KPME_OK) return st;
     StepScope sc(P, STEP_GATHER, 1);
@@ -759,7 +806,11 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
   }
   if (vir) {
     if (n > 0) {
-      if ((st = virial(P, m, energy, vir)) != KPME_OK) return st;
+      if (fork)
+        KPME_CUDA_TRY(P, cudaStreamWaitEvent(P->stream, P->ev_join, 0));
+      else if ((st = virial_mesh(P, m)) != KPME_OK)
+        return st;
+      if ((st = virial_finish(P, energy, vir)) != KPME_OK) return st;
     } else {
       KPME_CUDA_TRY(P, cudaMemsetAsync(vir, 0, sizeof(double), P->stream));
     }

@@ -135,6 +135,9 @@ struct kpme_plan_s {
 
   // CUDA graph of kpme_energy_forces, keyed by its arguments; replayed on the caller's stream
   cudaStream_t capture_stream = nullptr;
+  // the virial's mesh part runs on a branch forked after spreading (it only reads Q)
+  cudaStream_t side_stream = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaGraphExec_t graph_exec = nullptr;
   int64_t graph_key[8] = {};
   bool use_graphs = true;
