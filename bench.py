@@ -300,7 +300,9 @@ def main(argv=None):
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     if args.precision.startswith("tf32"):
         peak = peak / 2.0   # dense tf32 rate is half the bf16 rate
-    roof = {"bound": "tensor", "kernel": "mp_tc_kernel (SKP mode products, tcgen05)",
+    kname = ("mp_oz_kernel (SKP mode products, error-free split, tcgen05)" if args.precision == "bf16x10"
+             else "mp_tc_kernel (SKP mode products, tcgen05)")
+    roof = {"bound": "tensor", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": (achieved / peak) if achieved else None, "traffic": None,
             "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 1/2 (tf32 nominal ratio)" if args.precision.startswith("tf32") else ""),

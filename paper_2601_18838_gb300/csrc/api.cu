@@ -384,17 +384,20 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       KPME_CUDA_TRY(P, launch_slice_rows(P, Q.p, Q.dbl, k2, 1, K, P->d_Qsl));
     }
     {
-      StepScope sc(P, STEP_SKP1, 2);
+      StepScope sc(P, STEP_SKP1, 1);
       OzArgs a{&P->tm_f3, &P->tm_Q, 1, nullptr, false, 0, nullptr, 0, (float*)P->d_Y, k3, nullptr, 0, M, K, K, 0,
                &P->stage1};
       KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+    }
+    {
+      StepScope sc(P, STEP_SPLIT, 1);
       KPME_CUDA_TRY(P, launch_slice_rows(P, P->d_Y, false, k2, S.r0, K, P->d_Ysl));
     }
     KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
     for (const auto& g : P->groups) {
+      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
       {
         StepScope sc(P, STEP_SKP2, 1);
-        KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
         OzArgs a{&P->tm_f2, &P->tm_Y, S.r0, nullptr, false, 0, nullptr, 0, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K, K,
                  0, &g.stage2};
         KPME_CUDA_TRY(P, launch_mp_oz(P, a));
