@@ -21,7 +21,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libkpme.so")
-SOURCES = ["api.cu", "particles.cu", "skp_build.cu", "gemm_simt.cu", "gemm_tc.cu", "gemm_oz.cu", "noalloc.cu", "batch.cu"]
+SOURCES = ["api.cu", "particles.cu", "skp_build.cu", "gemm_simt.cu", "gemm_tc.cu", "gemm_oz.cu", "gemm_ozt.cu", "gemm_ozf.cu", "noalloc.cu", "batch.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -57,7 +57,8 @@ def build(verbose: bool = False, force: bool = False) -> str:
     nvcc = _nvcc()
     os.makedirs(BUILD, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
-    deps = srcs + [os.path.join(CSRC, "kpme_internal.cuh"), os.path.join(INCLUDE, "kpme.h")]
+    headers = sorted(os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh"))
+    deps = srcs + headers + [os.path.join(INCLUDE, "kpme.h")]
     stamp = os.path.join(BUILD, "libkpme.stamp")
     dig = _digest(deps)
     if not force and os.path.exists(LIB) and os.path.exists(stamp):

@@ -95,10 +95,15 @@ void release_skp_buffers(kpme_plan_t P) {
   dfree(P->d_Qsl);
   dfree(P->d_Ysl);
   dfree(P->d_rmZ);
+  dfree(P->d_rmQ);
+  dfree(P->d_rmY);
   free_joblist(P->stage1);
+  free_joblist(P->stage1_res);
+  free_joblist(P->stage23);
   for (auto& g : P->groups) {
     free_joblist(g.stage2);
     free_joblist(g.stage3);
+    free_joblist(g.stage2_res);
   }
   P->groups.clear();
 }
@@ -123,7 +128,7 @@ void choose_tc_tiles(kpme_plan_t P) {
   const int K = P->p.K;
   if (P->prec.oz) {
     // error-free split: four A slices (64 KB) + four B slices per stage, two stages
-    P->tc_bn = K <= 96 ? K : 64;
+    P->tc_bn = K % 64 == 0 ? 64 : K == 96 ? 48 : K <= 96 ? K : 64;
     P->tc_stages = 2;
     while (P->tc_stages > 1 && oz_smem_bytes(P->tc_bn, P->tc_stages) > 227 * 1024) --P->tc_stages;
     return;
@@ -176,6 +181,45 @@ kpme_status_t alloc_meshes(kpme_plan_t P) {
 
 // Materialise the installed SKP in the plan's arithmetic: factors, intermediates, job lists
 // and (tensor path) TMA descriptors.
+bool getenv_flag(const char* name, bool dflt) {
+  const char* e = getenv(name);
+  if (!e || !*e) return dflt;
+  return e[0] != '0';
+}
+
+// Jobs over runs of pairs that share their A operand: every run [a, b) is cut into pieces
+// of at most J pairs, J chosen so that the persistent grid's makespan, rounds of
+// ceil(items / SMs) times (J + 1) (one pair's worth for cutting A), is smallest.
+template <typename PairOf>
+void build_run_jobs(kpme_plan_t P, const std::vector<std::pair<int, int>>& runs, int64_t tiles, PairOf pair_of,
+                    JobList& jl) {
+  int maxlen = 1;
+  for (const auto& r : runs) maxlen = std::max(maxlen, r.second - r.first);
+  int bestJ = maxlen;
+  int64_t best = INT64_MAX;
+  for (int J = 1; J <= maxlen; ++J) {
+    int64_t jobs = 0;
+    for (const auto& r : runs) jobs += (r.second - r.first + J - 1) / J;
+    const int64_t rounds = (tiles * jobs + P->sm_count - 1) / P->sm_count;
+    const int64_t cost = rounds * (J + 1);
+    if (cost < best) {
+      best = cost;
+      bestJ = J;
+    }
+  }
+  jl.h_start.assign(1, 0);
+  jl.h_pairs.clear();
+  for (const auto& r : runs) {
+    const int len = r.second - r.first;
+    const int pieces = (len + bestJ - 1) / bestJ;
+    for (int k = 0; k < pieces; ++k) {
+      const int a = r.first + (int)((int64_t)len * k / pieces), b = r.first + (int)((int64_t)len * (k + 1) / pieces);
+      for (int t = a; t < b; ++t) jl.h_pairs.push_back(pair_of(t));
+      jl.h_start.push_back((int)jl.h_pairs.size());
+    }
+  }
+}
+
 kpme_status_t install_skp(kpme_plan_t P) {
   drop_graph(P);
   release_skp_buffers(P);
@@ -216,15 +260,28 @@ kpme_status_t install_skp(kpme_plan_t P) {
   P->group_terms = G;
   if (pi.tensor && !pi.oz && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_Y, (size_t)islices * r0 * k3 * ieb)) != KPME_OK) return st;
-  if ((st = dalloc(P, &P->d_Z, (size_t)islices * G * k3 * ieb)) != KPME_OK) return st;
+  if (pi.tensor) choose_tc_tiles(P);
+  P->ozt_res = pi.oz && ozt_supported(K, P->tc_bn, true);
+  P->ozt_pp = pi.oz && ozt_supported(K, P->tc_bn, false);
+  P->ozf = P->ozt_res && ozf_supported(K) && P->tc_bn == K && getenv_flag("KPME_FUSED", true);
   if (pi.oz) {
-    // Q and Y are read by several jobs each: they are cut into fixed-point slices once and
-    // fed by TMA; Z is read once and is sliced on the fly from float32 with its row maxima
     const size_t k2 = (size_t)K * K;
-    if ((st = dalloc(P, &P->d_Qsl, (size_t)4 * k3 * sizeof(__nv_bfloat16))) != KPME_OK) return st;
-    if ((st = dalloc(P, &P->d_Ysl, (size_t)4 * r0 * k3 * sizeof(__nv_bfloat16))) != KPME_OK) return st;
-    if ((st = dalloc(P, (void**)&P->d_rmZ, (size_t)G * k2 * sizeof(float))) != KPME_OK) return st;
+    if (P->ozt_res) {
+      // A in tensor memory: Q and Y stay float32 and are cut by converter warps once per
+      // item (shared by the item's pairs) with their row maxima
+      if ((st = dalloc(P, (void**)&P->d_rmQ, k2 * sizeof(float))) != KPME_OK) return st;
+      if ((st = dalloc(P, (void**)&P->d_rmY, (size_t)r0 * k2 * sizeof(float))) != KPME_OK) return st;
+    } else {
+      // Q and Y are read by several jobs each: they are cut into fixed-point slices once and
+      // fed by TMA
+      if ((st = dalloc(P, &P->d_Qsl, (size_t)4 * k3 * sizeof(__nv_bfloat16))) != KPME_OK) return st;
+      if ((st = dalloc(P, &P->d_Ysl, (size_t)4 * r0 * k3 * sizeof(__nv_bfloat16))) != KPME_OK) return st;
+    }
+    // Z is read once per term and is cut on the fly from float32 with its row maxima (the
+    // fused kernel keeps Z on the SM)
+    if (!P->ozf && (st = dalloc(P, (void**)&P->d_rmZ, (size_t)G * k2 * sizeof(float))) != KPME_OK) return st;
   }
+  if (!(pi.oz && P->ozf) && (st = dalloc(P, &P->d_Z, (size_t)islices * G * k3 * ieb)) != KPME_OK) return st;
 
   // job lists
   P->stage1.h_start.clear();
@@ -233,7 +290,6 @@ kpme_status_t install_skp(kpme_plan_t P) {
   for (int i = 0; i < r0; ++i) P->stage1.h_pairs.push_back(make_int2(0, i));
   if ((st = upload_joblist(P, P->stage1)) != KPME_OK) return st;
 
-  if (pi.tensor) choose_tc_tiles(P);
   const int m_tiles = pi.tensor ? (K * K + 127) / 128 : (K * K + 63) / 64;
   const int n_tiles = pi.tensor ? K / P->tc_bn : (K + 63) / 64;
   for (int t0 = 0; t0 < R; t0 += G) {
@@ -271,23 +327,68 @@ kpme_status_t install_skp(kpme_plan_t P) {
       pos += b - a;
       g.stage3.h_start.push_back(pos);
     }
+    if (P->ozt_res) {
+      // runs of consecutive terms of one outer index share Y_i: chunked for a balanced grid
+      std::vector<std::pair<int, int>> runs;   // [first term, end)
+      for (int t = g.t0; t < g.t1;) {
+        int e = t + 1;
+        while (e < g.t1 && S.outer_of[e] == S.outer_of[t]) ++e;
+        runs.push_back({t, e});
+        t = e;
+      }
+      build_run_jobs(P, runs, (int64_t)m_tiles * n_tiles, [&](int t) { return make_int2(S.outer_of[t], t); },
+                     g.stage2_res);
+      if ((st = upload_joblist(P, g.stage2_res)) != KPME_OK) return st;
+    }
     if ((st = upload_joblist(P, g.stage2)) != KPME_OK) return st;
     if ((st = upload_joblist(P, g.stage3)) != KPME_OK) return st;
     P->groups.push_back(std::move(g));
+  }
+  if (P->ozt_res) {
+    build_run_jobs(P, {{0, r0}}, (int64_t)m_tiles * n_tiles, [&](int i) { return make_int2(0, i); }, P->stage1_res);
+    if ((st = upload_joblist(P, P->stage1_res)) != KPME_OK) return st;
+  }
+  if (P->ozf) {
+    // fused stages 2 and 3: contiguous term ranges; makespan = rounds x (terms per range +
+    // 2 for the range's cuts of Y_i tiles and its atomic Phi update)
+    int splits = 1;
+    int64_t best = INT64_MAX;
+    for (int sp = 1; sp <= R; ++sp) {
+      const int64_t rounds = ((int64_t)m_tiles * sp + P->sm_count - 1) / P->sm_count;
+      const int64_t cost = rounds * ((R + sp - 1) / sp + 2);
+      if (cost < best) {
+        best = cost;
+        splits = sp;
+      }
+    }
+    P->stage23.h_start.assign(1, 0);
+    P->stage23.h_pairs.clear();
+    for (int k = 0; k < splits; ++k) {
+      const int a = (int)((int64_t)R * k / splits), b = (int)((int64_t)R * (k + 1) / splits);
+      for (int t = a; t < b; ++t) P->stage23.h_pairs.push_back(make_int2(S.outer_of[t], t));
+      P->stage23.h_start.push_back((int)P->stage23.h_pairs.size());
+    }
+    if ((st = upload_joblist(P, P->stage23)) != KPME_OK) return st;
   }
 
   if (pi.tensor) {
     const bool f32 = pi.tf32;
     const uint32_t box0 = 128 / pi.elem_bytes;
     const uint64_t KK = (uint64_t)K * K;
-    bool ok = (pi.oz ? (encode_tmap(P, &P->tm_Q, P->d_Qsl, 2, false, K, KK, 4, 64, 128) &&
-                        encode_tmap(P, &P->tm_Y, P->d_Ysl, 2, false, K, KK, (uint64_t)4 * r0, 64, 128))
+    bool ok = (pi.oz ? (P->ozt_res || (encode_tmap(P, &P->tm_Q, P->d_Qsl, 2, false, K, KK, 4, 64, 128) &&
+                                        encode_tmap(P, &P->tm_Y, P->d_Ysl, 2, false, K, KK, (uint64_t)4 * r0, 64, 128)))
                      : (encode_tmap(P, &P->tm_Q, P->d_Qs, pi.elem_bytes, f32, K, KK, (uint64_t)slices, box0, 128) &&
                 encode_tmap(P, &P->tm_Y, P->d_Y, pi.elem_bytes, f32, K, KK, (uint64_t)slices * r0, box0, 128) &&
                 encode_tmap(P, &P->tm_Z, P->d_Z, pi.elem_bytes, f32, K, KK, (uint64_t)slices * G, box0, 128))) &&
               encode_tmap(P, &P->tm_f3, P->d_fac3, pi.elem_bytes, f32, K, (uint64_t)r0 * K, slices, box0, P->tc_bn) &&
               encode_tmap(P, &P->tm_f2, P->d_fac2, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn) &&
               encode_tmap(P, &P->tm_f1, P->d_fac1, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn);
+    if (ok && pi.oz && (P->ozt_res || P->ozt_pp)) {
+      // float32 A operands for the tensor-memory kernel: 128 rows x 32 values per box
+      ok = (P->ozf || encode_tmap(P, &P->tmF_Z, P->d_Z, 4, true, K, KK, (uint64_t)G, 32, 128)) &&
+           (!P->ozt_res || (encode_tmap(P, &P->tmF_Q, P->d_Qf, 4, true, K, KK, 1, 32, 128) &&
+                            encode_tmap(P, &P->tmF_Y, P->d_Y, 4, true, K, KK, (uint64_t)r0, 32, 128)));
+    }
     if (!ok) return KPME_ERR_CUDA;
   }
   KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
@@ -379,17 +480,44 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
   }
   if (pi.oz) {
     const int64_t k2 = (int64_t)K * K;
-    {
+    const bool res = P->ozt_res;
+    if (res) {
+      // float32 charge mesh and its row maxima (rows of stage 1)
+      StepScope sc(P, STEP_SPLIT, Q.dbl ? 2 : 1);
+      if (Q.dbl) KPME_CUDA_TRY(P, launch_convert(Q.p, true, P->d_Qf, false, k3, P->stream));
+      KPME_CUDA_TRY(P, launch_rowmax_rows(P, P->d_Qf, k2, K, P->d_rmQ));
+    } else {
       StepScope sc(P, STEP_SPLIT, 1);
       KPME_CUDA_TRY(P, launch_slice_rows(P, Q.p, Q.dbl, k2, 1, K, P->d_Qsl));
     }
-    {
-      StepScope sc(P, STEP_SKP1, 1);
-      OzArgs a{&P->tm_f3, &P->tm_Q, 1, nullptr, false, 0, nullptr, 0, (float*)P->d_Y, k3, nullptr, 0, M, K, K, 0,
-               &P->stage1};
-      KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+    if (res && P->ozf) {
+      // stage 1, then stages 2 and 3 fused (Z stays on the SM; its rows' powers of two are
+      // taken by the fused kernel itself, so stage 1 publishes no row maxima)
+      {
+        StepScope sc(P, STEP_SKP1, 1);
+        OztArgs a{&P->tmF_Q, &P->tm_f3, P->d_rmQ, 0, (float*)P->d_Y, k3, 0, nullptr, 0, M, K, K, 2, true,
+                  &P->stage1_res};
+        KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
+      }
+      KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
+      StepScope sc(P, STEP_SKP2, 1);
+      OzfArgs a{&P->tmF_Y, &P->tm_f2, &P->tm_f1, (float*)Phi, K, &P->stage23};
+      KPME_CUDA_TRY(P, launch_mp_ozf(P, a));
+      return KPME_OK;
     }
-    {
+    if (res) {
+      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmY, 0, (size_t)S.r0 * k2 * sizeof(float), P->stream));
+      StepScope sc(P, STEP_SKP1, 1);
+      OztArgs a{&P->tmF_Q, &P->tm_f3, P->d_rmQ, 0, (float*)P->d_Y, k3, 0, P->d_rmY, k2, M, K, K, 2, true,
+                &P->stage1_res};
+      KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
+    } else {
+      {
+        StepScope sc(P, STEP_SKP1, 1);
+        OzArgs a{&P->tm_f3, &P->tm_Q, 1, nullptr, false, 0, nullptr, 0, (float*)P->d_Y, k3, nullptr, 0, M, K, K, 0,
+                 &P->stage1};
+        KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+      }
       StepScope sc(P, STEP_SPLIT, 1);
       KPME_CUDA_TRY(P, launch_slice_rows(P, P->d_Y, false, k2, S.r0, K, P->d_Ysl));
     }
@@ -398,14 +526,25 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
       {
         StepScope sc(P, STEP_SKP2, 1);
-        OzArgs a{&P->tm_f2, &P->tm_Y, S.r0, nullptr, false, 0, nullptr, 0, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K, K,
-                 0, &g.stage2};
-        KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+        if (res) {
+          OztArgs a{&P->tmF_Y, &P->tm_f2, P->d_rmY, k2, (float*)P->d_Z, k3, g.t0, P->d_rmZ, k2, M, K, K, 2, true,
+                    &g.stage2_res};
+          KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
+        } else {
+          OzArgs a{&P->tm_f2, &P->tm_Y, S.r0, nullptr, false, 0, nullptr, 0, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K,
+                   K, 0, &g.stage2};
+          KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+        }
       }
       StepScope sc(P, STEP_SKP3, 1);
-      OzArgs a{&P->tm_f1, nullptr, 0, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1,
-               &g.stage3};
-      KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+      if (P->ozt_pp) {
+        OztArgs a{&P->tmF_Z, &P->tm_f1, P->d_rmZ, k2, (float*)Phi, 0, 0, nullptr, 0, M, K, K, 1, false, &g.stage3};
+        KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
+      } else {
+        OzArgs a{&P->tm_f1, nullptr, 0, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1,
+                 &g.stage3};
+        KPME_CUDA_TRY(P, launch_mp_oz(P, a));
+      }
     }
     return KPME_OK;
   }

@@ -18,13 +18,14 @@
 // epilogue drains one Kronecker term while the MMAs of the next run.
 // All waits are bounded; a wait that runs out raises the device status word.
 #include "kpme_internal.cuh"
+#include "tc_common.cuh"
 
 namespace kpme {
 namespace {
 
+using namespace tc;
+
 constexpr int kBM = 128;
-constexpr int kSlices = 4;
-constexpr int kProducts = 10;
 constexpr int kChunk = 64;                 // k values per chunk = one 128-byte bf16 row
 constexpr int kASlice = kBM * 128;         // 16 KB
 
@@ -42,148 +43,10 @@ struct OzParams {
   int64_t rm_out_bs;
   const int* start;
   const int2* pairs;
-  int n_jobs;
+  int n_jobs, n_pairs;
   int nbatch_a;      // batches per slice plane of the pre-sliced A (TMA mode)
   int* status;
 };
-
-// products ordered (0,0) | (0,1) (1,0) | (0,2) (1,1) (2,0) | (0,3) (1,2) (2,1) (3,0)
-__host__ __device__ constexpr int pa(int p) {
-  return p == 0 ? 0 : p == 1 ? 0 : p == 2 ? 1 : p == 3 ? 0 : p == 4 ? 1 : p == 5 ? 2 : p == 6 ? 0 : p == 7 ? 1 : p == 8 ? 2 : 3;
-}
-__host__ __device__ constexpr int pb(int p) {
-  return p == 0 ? 0 : p == 1 ? 1 : p == 2 ? 0 : p == 3 ? 2 : p == 4 ? 1 : p == 5 ? 0 : p == 6 ? 3 : p == 7 ? 2 : p == 8 ? 1 : 0;
-}
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  const long long t0 = clock64();
-  while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
-      *abort_flag = 1;
-      atomicExch(status, DEV_TIMEOUT);
-      return false;
-    }
-  }
-  return true;
-}
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "
-      "[%2];" ::"r"(smem_u32(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-      : "memory");
-}
-__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ uint64_t sdesc(uint32_t saddr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;
-  d |= (uint64_t)(1024 >> 4) << 32;
-  d |= (uint64_t)1 << 46;
-  d |= (uint64_t)2 << 61;
-  return d;
-}
-__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
-}
-__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t id, uint32_t acc) {
-  asm volatile(
-      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\ttcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(id), "r"(acc)
-      : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
-        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
-
-__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
-  __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&h);
-}
-
-// 2^k as a float32 (exact): a bit pattern for normal exponents, ldexpf outside.
-__device__ __forceinline__ float pow2f(int k) {
-  return (k >= -126 && k <= 127) ? __int_as_float((127 + k) << 23) : ldexpf(1.0f, k);
-}
-
-// Four fixed-point digits of 8 float32 values relative to 2^e (|v| < 2^e): slice s holds
-// d_s 2^(e - 7 - 8s) with integers d_s in [-128, 128], written as packed bf16 (exact: at most
-// 8 significant bits).  Each digit is taken by rounding the running remainder to a multiple
-// of q_s = 2^(e - 7 - 8s) with the add-and-subtract of C_s = 1.5 * 2^(e + 16 - 8s): for
-// |r| < 2^(e + 15 - 8s) the float32 sum r + C_s rounds (to nearest, ties to even) onto the
-// grid of q_s, so (r + C_s) - C_s is round(r / q_s) q_s exactly and r - that is exact too.
-// The digits equal those of rint(r / q_s) at each step.  Exponents whose C_s would leave the
-// normal float32 range take the same steps with rintf.
-__device__ __forceinline__ float magic15(int k) { return __int_as_float(((127 + k) << 23) | (1 << 22)); }
-
-__device__ __forceinline__ void slice8(const float* v, int e, uint4 (&o)[kSlices]) {
-  float h[kSlices][8];
-  if (e + 16 <= 127 && e - 8 >= -126) {
-    float C[kSlices];
-#pragma unroll
-    for (int sl = 0; sl < kSlices; ++sl) C[sl] = magic15(e + 16 - 8 * sl);
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float r = v[i];
-#pragma unroll
-      for (int sl = 0; sl < kSlices; ++sl) {
-        const float t = __fadd_rn(r, C[sl]);
-        h[sl][i] = __fsub_rn(t, C[sl]);
-        r = __fsub_rn(r, h[sl][i]);
-      }
-    }
-  } else {
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      float r = v[i];
-#pragma unroll
-      for (int sl = 0; sl < kSlices; ++sl) {
-        const float q = ldexpf(1.0f, e - 7 - 8 * sl);
-        h[sl][i] = rintf(r / q) * q;
-        r = r - h[sl][i];
-      }
-    }
-  }
-#pragma unroll
-  for (int sl = 0; sl < kSlices; ++sl) {
-    o[sl].x = pack_bf16(h[sl][0], h[sl][1]);
-    o[sl].y = pack_bf16(h[sl][2], h[sl][3]);
-    o[sl].z = pack_bf16(h[sl][4], h[sl][5]);
-    o[sl].w = pack_bf16(h[sl][6], h[sl][7]);
-  }
-}
 
 // Persistent CTA, work items (m-tile, n-tile, job) strided by gridDim.x, every role walking
 // the same sequence of (item, pair, 64-wide chunk) so the shared ring counters agree.
@@ -211,6 +74,11 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
   // per-warp column maxima of the epilogue (4 x BN)
   unsigned int* red = reinterpret_cast<unsigned int*>(smem + S * prm.stage_bytes + 256);
+  // the job tables live in shared memory: every role reads them for every item and pair
+  int2* s_pairs = reinterpret_cast<int2*>(red + 4 * BN);
+  int* s_start = reinterpret_cast<int*>(s_pairs + prm.n_pairs);
+  for (int i = threadIdx.x; i < prm.n_pairs; i += blockDim.x) s_pairs[i] = prm.pairs[i];
+  for (int i = threadIdx.x; i <= prm.n_jobs; i += blockDim.x) s_start[i] = prm.start[i];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m_tiles = (prm.M + kBM - 1) / kBM;
@@ -258,9 +126,9 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
       for (int w = blockIdx.x; w < n_items && !*abort_flag; w += gridDim.x) {
         int m0, n0, job;
         decode(w, m0, n0, job);
-        const int p0 = prm.start[job], p1 = prm.start[job + 1];
+        const int p0 = s_start[job], p1 = s_start[job + 1];
         for (int p = p0; p < p1; ++p) {
-          const int2 pr = prm.pairs[p];
+          const int2 pr = s_pairs[p];
           for (int c = 0; c < kchunks; ++c, ++it) {
             const int s = it % S;
             const uint32_t ph = (uint32_t)(it / S) & 1u;
@@ -289,7 +157,7 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
       for (int w = blockIdx.x; w < n_items && !*abort_flag; w += gridDim.x) {
         int m0, n0, job;
         decode(w, m0, n0, job);
-        const int np = prm.start[job + 1] - prm.start[job];
+        const int np = s_start[job + 1] - s_start[job];
         for (int pl = 0; pl < np && !*abort_flag; ++pl, ++pc) {
           const int buf = pc & 1;
           if (pc >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((pc >> 1) - 1) & 1u, abort_flag, prm.status)) break;
@@ -303,19 +171,28 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
             fence_after();
             int ksteps = (prm.Kr - c * kChunk + 15) / 16;
             ksteps = ksteps > 4 ? 4 : ksteps;
+            // one descriptor per operand and stage; digit planes and k steps are compile-time
+            // offsets added to the 14-bit address field (addresses stay below 256 KB: no carry)
             const uint32_t sa = smem_u32(smem + s * prm.stage_bytes);
-            const uint32_t sb = sa + kSlices * kASlice;
-            for (int kk = 0; kk < ksteps; ++kk) {
-              const bool first = (c == 0 && kk == 0);
+            const uint64_t da0 = sdesc(sa), db0 = sdesc(sa + kSlices * kASlice);
+            auto kstep = [&](int kk, bool first) {
 #pragma unroll
               for (int p = 0; p < kProducts; ++p) {
-                const uint64_t da = sdesc(sa + pa(p) * kASlice + kk * 32);
-                const uint64_t db = sdesc(sb + pb(p) * kBSlice + kk * 32);
+                const uint64_t da = da0 + (uint64_t)((pa(p) * kASlice + kk * 32) >> 4);
+                const uint64_t db = db0 + (uint64_t)((pb(p) * kBSlice + kk * 32) >> 4);
                 if (p == 0)
                   mma_bf16(d0, da, db, id, first ? 0u : 1u);
                 else
                   mma_bf16(d1, da, db, id, (first && p == 1) ? 0u : 1u);
               }
+            };
+            if (ksteps == 4) {
+              kstep(0, c == 0);
+              kstep(1, false);
+              kstep(2, false);
+              kstep(3, false);
+            } else {
+              for (int kk = 0; kk < ksteps; ++kk) kstep(kk, c == 0 && kk == 0);
             }
             mma_commit(&empty[s]);
           }
@@ -365,9 +242,9 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
         decode(w, m0, n0, job);
         const int row = m0 + r;
         const bool valid = row < prm.M;
-        const int p0 = prm.start[job], p1 = prm.start[job + 1];
+        const int p0 = s_start[job], p1 = s_start[job + 1];
         for (int p = p0; p < p1 && ok; ++p) {
-          const int2 pr = prm.pairs[p];
+          const int2 pr = s_pairs[p];
           const float* rowp = reinterpret_cast<const float*>(prm.in) + (int64_t)pr.x * prm.in_bs + (int64_t)row * prm.Kr;
           const float rm = valid ? prm.rowmax_in[(int64_t)pr.x * prm.rm_in_bs + row] : 0.0f;
           for (int c = 0; c < kchunks; ++c) {
@@ -411,7 +288,7 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
       int m0, n0, job;
       decode(w, m0, n0, job);
       const int row = m0 + r;
-      const int np = prm.start[job + 1] - prm.start[job];
+      const int np = s_start[job + 1] - s_start[job];
       float acc[BN];
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
@@ -598,7 +475,10 @@ cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a) {
   prm.n_jobs = a.jobs->n_jobs;
   prm.nbatch_a = a.nbatch_a;
   prm.status = P->d_status;
-  const int smem = oz_smem_bytes(P->tc_bn, P->tc_stages);
+  prm.n_pairs = (int)a.jobs->h_pairs.size();
+  const int smem = oz_smem_bytes(P->tc_bn, P->tc_stages) + prm.n_pairs * (int)sizeof(int2) +
+                   (prm.n_jobs + 1) * (int)sizeof(int);
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
   const int items = ((a.M + kBM - 1) / kBM) * (a.N / P->tc_bn) * a.jobs->n_jobs;
   dim3 grid(items < P->sm_count ? items : P->sm_count);
   switch (P->tc_bn) {

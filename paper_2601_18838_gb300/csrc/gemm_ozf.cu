@@ -1,0 +1,448 @@
+// Fused second and third mode products of the SKP for K = 32 and K = 64 (KPME_BF16X10).
+//
+// For one 128-row tile of Y_i (rows (k3', k1) with k1 fastest, K/... of them per k3') and
+// a range of terms t, every term runs both remaining steps of Algorithm 2 on the SM:
+//     Z_t = Y_i x_2 B_t      (tile rows (k3', k1), columns k2')
+//     Phi += Z_t x_1 A_t     (rows (k2', k3'), contraction over k1, columns k1')
+// Z_t never leaves the SM: the epilogue warps drain the first product's accumulators and
+// write Z_t transposed (rows (k3', k2'), k1 fastest) into a shared-memory tile; converter
+// warps cut each row into four fixed-point bf16 digits with the power of two above the row's
+// own maximum (a full row is one thread's 64 values) and store them into tensor memory as
+// the A operand of the second product.  Both products use the error-free split of
+// gemm_oz.cu / gemm_ozt.cu (ten digit products, exact leading accumulator D0, cross terms
+// D1; Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012), drained per term.  The
+// Phi tile is summed over the item's terms in registers and added to the mesh atomically.
+//
+// Tensor memory (512 columns): D of step 2 (2 BN), D of step 3 (2 BN), A of step 2 (Y_i
+// digits, 128), A of step 3 (Z_t digits, 128).  The tensor pipe alternates step 2 of term
+// j + 1 and step 3 of term j, and the transposed Z tile is double-buffered, so cutting term
+// j's digits overlaps the MMAs of term j + 1's first step.
+// All waits are bounded; a wait that runs out raises the device status word.
+#include "kpme_internal.cuh"
+#include "tc_common.cuh"
+
+namespace kpme {
+namespace {
+
+using namespace tc;
+
+constexpr int kBM = 128;
+constexpr int kFBox = kBM * 128;        // 128 rows x 32 floats, 128-byte swizzle: 16 KB
+constexpr int kTile = 2 * kFBox;        // 128 rows x 64 floats: 32 KB
+constexpr int kACols = kSlices * 32;    // tensor-memory columns of one 64-wide A row's digits
+constexpr int kBarBytes = 512;
+constexpr int kThreads = 10 * 32;       // TMA, MMA, 4 converters, 4 epilogue warps
+
+struct OzfParams {
+  int K, M, sb;
+  float* phi;
+  const int* start;
+  const int2* pairs;   // (outer index, term)
+  int n_jobs, n_pairs;
+  int* status;
+};
+
+// float offset of (row, k) in a 128 x 64 float tile stored as two swizzled 128 x 32 boxes
+__device__ __forceinline__ int tile_off(int row, int k) {
+  return (k >> 5) * (kFBox / 4) + row * 32 + ((((k & 31) >> 2) ^ (row & 7)) << 2) + (k & 3);
+}
+
+// 4 floats (k = 4j .. 4j + 3) of one tile row
+__device__ __forceinline__ float4 row_quad(const float* tile, int row, int j) {
+  return *reinterpret_cast<const float4*>(tile + (j >> 3) * (kFBox / 4) + row * 32 + (((j & 7) ^ (row & 7)) << 2));
+}
+
+// Digits of one tile row into tensor memory columns taddr..: first the power of two above the
+// row's maximum, then every group of 8 values gives four words of each digit plane (4 columns
+// per plane).  The row is read from shared memory twice instead of being held in registers.
+template <int K>
+__device__ __forceinline__ void cut_row(const float* tile, int row, uint32_t taddr) {
+  float m = 0.0f;
+#pragma unroll
+  for (int j = 0; j < K / 4; ++j) {
+    const float4 x = row_quad(tile, row, j);
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+  }
+  int e = 0;
+  frexpf(m, &e);
+  // kept rolled: the kernel's roles share the SM's instruction cache
+#pragma unroll 1
+  for (int g = 0; g < K / 8; ++g) {
+    const float4 x0 = row_quad(tile, row, 2 * g), x1 = row_quad(tile, row, 2 * g + 1);
+    const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+    uint4 o[kSlices];
+    slice8(v, e, o);
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl) tmem_st4(taddr + (uint32_t)(sl * 32 + 4 * g), o[sl]);
+  }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kThreads, 1)
+    mp_ozf_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmB2,
+                  const __grid_constant__ CUtensorMap tmB1, OzfParams prm) {
+  constexpr int BN = K;                 // both products have N = K
+  constexpr int kBSlice = BN * 128;
+  constexpr int kKSteps = K / 16;
+  constexpr int kSub = kBM / K;         // k3' values per tile
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const int bstage = kSlices * kBSlice;
+  uint8_t* ring_b = smem;
+  float* ftile = reinterpret_cast<float*>(ring_b + prm.sb * bstage);   // Y_i rows (TMA)
+  float* ztile = ftile + kTile / 4;                                      // Z_t transposed, 2 buffers
+  uint64_t* bars = reinterpret_cast<uint64_t*>(ztile + 2 * (kTile / 4));
+  uint64_t* full_b = bars;
+  uint64_t* empty_b = full_b + prm.sb;
+  uint64_t* full_f = empty_b + prm.sb;
+  uint64_t* empty_f = full_f + 1;
+  uint64_t* full_a2 = empty_f + 1;
+  uint64_t* empty_a2 = full_a2 + 1;
+  uint64_t* full_c2 = empty_a2 + 1;
+  uint64_t* empty_c2 = full_c2 + 1;
+  uint64_t* full_z = empty_c2 + 1;     // [2]
+  uint64_t* empty_z = full_z + 2;      // [2]
+  uint64_t* full_a3 = empty_z + 2;
+  uint64_t* empty_a3 = full_a3 + 1;
+  uint64_t* full_c3 = empty_a3 + 1;
+  uint64_t* empty_c3 = full_c3 + 1;
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty_c3 + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
+  int2* s_pairs = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
+  int* s_start = reinterpret_cast<int*>(s_pairs + prm.n_pairs);
+  for (int i = threadIdx.x; i < prm.n_pairs; i += blockDim.x) s_pairs[i] = prm.pairs[i];
+  for (int i = threadIdx.x; i <= prm.n_jobs; i += blockDim.x) s_start[i] = prm.start[i];
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m_tiles = prm.M / kBM;
+  const int n_items = m_tiles * prm.n_jobs;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < prm.sb; ++s) {
+      mbar_init(&full_b[s], 1);
+      mbar_init(&empty_b[s], 1);
+    }
+    mbar_init(full_f, 1);
+    mbar_init(empty_f, 128);
+    mbar_init(full_a2, 128);
+    mbar_init(empty_a2, 1);
+    mbar_init(full_c2, 1);
+    mbar_init(empty_c2, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&full_z[b], 128);
+      mbar_init(&empty_z[b], 128);
+    }
+    mbar_init(full_a3, 128);
+    mbar_init(empty_a3, 1);
+    mbar_init(full_c3, 1);
+    mbar_init(empty_c3, 128);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(taddr_slot)),
+                 "r"(512)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *taddr_slot;
+  const uint32_t c_d2 = 0, c_d3 = 2 * BN, c_a2 = 4 * BN, c_a3 = 4 * BN + kACols;
+
+  // step order of one item with n terms: S2(0), then S2(j), S3(j - 1) for j = 1..n-1, then
+  // S3(n - 1); op o in [0, 2n): o = 0 -> S2(0), o = 2n - 1 -> S3(n - 1), else odd o -> S2((o+1)/2),
+  // even o -> S3(o/2 - 1)
+  auto op_of = [](int o, int n, bool& s2, int& j) {
+    if (o == 0) {
+      s2 = true;
+      j = 0;
+    } else if (o == 2 * n - 1) {
+      s2 = false;
+      j = n - 1;
+    } else if (o & 1) {
+      s2 = true;
+      j = (o + 1) / 2;
+    } else {
+      s2 = false;
+      j = o / 2 - 1;
+    }
+  };
+  auto new_outer = [&](int p0, int j) { return j == 0 || s_pairs[p0 + j].x != s_pairs[p0 + j - 1].x; };
+
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA: Y_i rows (at every change of outer index) and factor digits ----------------
+      int ib = 0, jf = 0;
+      bool ok = true;
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        const int job = w / m_tiles, m0 = (w % m_tiles) * kBM;
+        const int p0 = s_start[job], n = s_start[job + 1] - p0;
+        for (int o = 0; o < 2 * n && ok; ++o) {
+          bool s2;
+          int j;
+          op_of(o, n, s2, j);
+          const int2 pr = s_pairs[p0 + j];
+          if (s2 && new_outer(p0, j)) {
+            if (jf >= 1 && !mbar_wait(empty_f, ((uint32_t)jf & 1u) ^ 1u, abort_flag, prm.status)) {
+              ok = false;
+              break;
+            }
+            mbar_expect_tx(full_f, (uint32_t)((K / 32) * kFBox));
+            for (int h = 0; h < K / 32; ++h)
+              tma_load_3d(reinterpret_cast<uint8_t*>(ftile) + h * kFBox, &tmY, full_f, 32 * h, m0, pr.x);
+            ++jf;
+          }
+          const int s = ib % prm.sb;
+          if (ib >= prm.sb &&
+              !mbar_wait(&empty_b[s], ((uint32_t)(ib / prm.sb) & 1u) ^ 1u, abort_flag, prm.status)) {
+            ok = false;
+            break;
+          }
+          uint8_t* dst = ring_b + s * bstage;
+          mbar_expect_tx(&full_b[s], (uint32_t)(kSlices * kBSlice));
+#pragma unroll
+          for (int b = 0; b < kSlices; ++b)
+            tma_load_3d(dst + b * kBSlice, s2 ? &tmB2 : &tmB1, &full_b[s], 0, pr.y * K, b);
+          ++ib;
+        }
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issue ----------------
+      const uint32_t id = idesc_bf16(kBM, BN);
+      int ib = 0, ia2 = 0, j2 = 0, ja3 = 0, j3 = 0;
+      bool ok = true;
+      auto run = [&](uint32_t a, uint32_t d, int s) {
+        const uint64_t db0 = sdesc(smem_u32(ring_b + s * bstage));
+#pragma unroll
+        for (int kk = 0; kk < kKSteps; ++kk)
+#pragma unroll
+          for (int p = 0; p < kProducts; ++p) {
+            const uint32_t at = a + (uint32_t)(pa(p) * 32 + kk * 8);
+            const uint64_t db = db0 + (uint64_t)((pb(p) * kBSlice + kk * 32) >> 4);
+            const uint32_t acc = (kk == 0 && p <= 1) ? 0u : 1u;
+            mma_bf16_ta(p == 0 ? d : d + BN, at, db, id, acc);
+          }
+      };
+      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+        const int job = w / m_tiles;
+        const int p0 = s_start[job], n = s_start[job + 1] - p0;
+        bool held = false;
+        for (int o = 0; o < 2 * n && ok; ++o) {
+          bool s2;
+          int j;
+          op_of(o, n, s2, j);
+          if (s2) {
+            if (new_outer(p0, j)) {
+              if (held) mma_commit(empty_a2);
+              if (!mbar_wait(full_a2, (uint32_t)ia2 & 1u, abort_flag, prm.status)) {
+                ok = false;
+                break;
+              }
+              ++ia2;
+              held = true;
+            }
+            if (j2 >= 1 && !mbar_wait(empty_c2, (uint32_t)(j2 - 1) & 1u, abort_flag, prm.status)) {
+              ok = false;
+              break;
+            }
+          } else {
+            if (!mbar_wait(full_a3, (uint32_t)ja3 & 1u, abort_flag, prm.status) ||
+                (j3 >= 1 && !mbar_wait(empty_c3, (uint32_t)(j3 - 1) & 1u, abort_flag, prm.status))) {
+              ok = false;
+              break;
+            }
+          }
+          const int s = ib % prm.sb;
+          if (!mbar_wait(&full_b[s], (uint32_t)(ib / prm.sb) & 1u, abort_flag, prm.status)) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          if (s2) {
+            run(tmem + c_a2, tmem + c_d2, s);
+            mma_commit(&empty_b[s]);
+            mma_commit(full_c2);
+            ++j2;
+          } else {
+            run(tmem + c_a3, tmem + c_d3, s);
+            mma_commit(&empty_b[s]);
+            mma_commit(empty_a3);
+            mma_commit(full_c3);
+            ++ja3;
+            ++j3;
+          }
+          ++ib;
+        }
+        if (ok && held) mma_commit(empty_a2);
+      }
+    }
+  } else if (warp < 6) {
+    // ---------------- converters: digits of Y_i rows and of Z_t rows into tensor memory ----------------
+    const int qd = warp & 3;
+    const int r = 32 * qd + lane;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+    int jf = 0, ia2 = 0, jz = 0, ja3 = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
+      const int job = w / m_tiles;
+      const int p0 = s_start[job], n = s_start[job + 1] - p0;
+      for (int j = 0; j < n && ok; ++j) {
+        if (new_outer(p0, j)) {
+          if (!__all_sync(0xffffffffu, mbar_wait(full_f, (uint32_t)jf & 1u, abort_flag, prm.status)) ||
+              (ia2 >= 1 &&
+               !__all_sync(0xffffffffu, mbar_wait(empty_a2, ((uint32_t)ia2 & 1u) ^ 1u, abort_flag, prm.status)))) {
+            ok = false;
+            break;
+          }
+          fence_after();
+          cut_row<K>(ftile, r, lane_base + c_a2);
+          mbar_arrive(empty_f);
+          ++jf;
+          tmem_wait_st();
+          fence_before();
+          mbar_arrive(full_a2);
+          ++ia2;
+        }
+        const int zb = jz & 1;
+        if (!__all_sync(0xffffffffu, mbar_wait(&full_z[zb], (uint32_t)(jz >> 1) & 1u, abort_flag, prm.status)) ||
+            (ja3 >= 1 &&
+             !__all_sync(0xffffffffu, mbar_wait(empty_a3, ((uint32_t)ja3 & 1u) ^ 1u, abort_flag, prm.status)))) {
+          ok = false;
+          break;
+        }
+        fence_after();
+        cut_row<K>(ztile + zb * (kTile / 4), r, lane_base + c_a3);
+        mbar_arrive(&empty_z[zb]);
+        ++jz;
+        tmem_wait_st();
+        fence_before();
+        mbar_arrive(full_a3);
+        ++ja3;
+      }
+    }
+  } else {
+    // ---------------- epilogue, in the MMA's op order ----------------
+    // step 2 of term j: Z_t = D0 + D1 written transposed (thread = tile row m = (k3' = m / K,
+    // k1 = m % K); Z_t(m, k2') to row k3' K + k2', column k1);
+    // step 3 of term j: the Phi tile rows rho = (k3' = rho / K, k2' = rho % K), columns k1',
+    // summed over the item's terms in registers and added atomically at the item's end.
+    const int qd = warp & 3;
+    const int m = 32 * qd + lane;
+    const int sub = m / K, k1 = m % K;
+    const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+    int j2 = 0, jz = 0, j3 = 0;
+    bool ok = true;
+    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
+      const int job = w / m_tiles, m0 = (w % m_tiles) * kBM;
+      const int n = s_start[job + 1] - s_start[job];
+      float acc[BN];
+#pragma unroll
+      for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
+      for (int o = 0; o < 2 * n; ++o) {
+        bool s2;
+        int j;
+        op_of(o, n, s2, j);
+        if (!ok) continue;
+        if (s2) {
+          const int zb = jz & 1;
+          float* zt = ztile + zb * (kTile / 4);
+          if (!__all_sync(0xffffffffu, mbar_wait(full_c2, (uint32_t)j2 & 1u, abort_flag, prm.status)) ||
+              (jz >= 2 && !__all_sync(0xffffffffu, mbar_wait(&empty_z[zb], ((uint32_t)(jz >> 1) & 1u) ^ 1u,
+                                                              abort_flag, prm.status)))) {
+            ok = false;
+            continue;
+          }
+          fence_after();
+#pragma unroll 1
+          for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t a0[16], a1[16];
+            tmem_ld16(lane_base + c_d2 + (uint32_t)c0, a0);
+            tmem_ld16(lane_base + c_d2 + (uint32_t)(BN + c0), a1);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i)
+              zt[tile_off(sub * K + c0 + i, k1)] = __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
+          }
+          fence_before();
+          mbar_arrive(empty_c2);
+          ++j2;
+          mbar_arrive(&full_z[zb]);
+          ++jz;
+        } else {
+          if (!__all_sync(0xffffffffu, mbar_wait(full_c3, (uint32_t)j3 & 1u, abort_flag, prm.status))) {
+            ok = false;
+            continue;
+          }
+          fence_after();
+#pragma unroll
+          for (int c0 = 0; c0 < BN; c0 += 16) {
+            uint32_t a0[16], a1[16];
+            tmem_ld16(lane_base + c_d3 + (uint32_t)c0, a0);
+            tmem_ld16(lane_base + c_d3 + (uint32_t)(BN + c0), a1);
+            tmem_wait_ld();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) acc[c0 + i] += __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
+          }
+          fence_before();
+          mbar_arrive(empty_c3);
+          ++j3;
+        }
+      }
+      if (!ok || *abort_flag) continue;
+      // Phi[k1'][k2'][k3'] for this thread's row rho = m: k3' = m0 / K + m / K, k2' = m % K
+      const int k3 = m0 / K + sub, k2 = k1;
+      float* out = prm.phi + (int64_t)k2 * K + k3;
+#pragma unroll
+      for (int c = 0; c < BN; ++c) atomicAdd(out + (int64_t)c * K * K, acc[c]);
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(512) : "memory");
+  }
+  (void)kSub;
+}
+
+template <int K>
+cudaError_t launch_k(kpme_plan_t P, const OzfArgs& a, OzfParams prm) {
+  const int bstage = kSlices * K * 128;
+  prm.sb = (K == 64) ? 3 : 6;
+  const int smem = prm.sb * bstage + 3 * kTile + kBarBytes + prm.n_pairs * (int)sizeof(int2) +
+                   (prm.n_jobs + 1) * (int)sizeof(int) + 1024;
+  if (smem > 227 * 1024) return cudaErrorInvalidValue;
+  auto kern = mp_ozf_kernel<K>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  const int items = (prm.M / kBM) * prm.n_jobs;
+  dim3 grid(items < P->sm_count ? items : P->sm_count);
+  kern<<<grid, kThreads, smem, P->stream>>>(*a.tmY, *a.tmB2, *a.tmB1, prm);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool ozf_supported(int K) { return K == 32 || K == 64; }
+
+cudaError_t launch_mp_ozf(kpme_plan_t P, const OzfArgs& a) {
+  OzfParams prm{};
+  prm.K = a.K;
+  prm.M = a.K * a.K;
+  prm.phi = a.phi;
+  prm.start = a.jobs->d_start;
+  prm.pairs = a.jobs->d_pairs;
+  prm.n_jobs = a.jobs->n_jobs;
+  prm.n_pairs = (int)a.jobs->h_pairs.size();
+  prm.status = P->d_status;
+  if (a.K == 64) return launch_k<64>(P, a, prm);
+  if (a.K == 32) return launch_k<32>(P, a, prm);
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace kpme

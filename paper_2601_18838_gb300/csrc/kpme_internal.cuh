@@ -41,6 +41,7 @@ struct TermGroup {
   int t0 = 0, t1 = 0;       // terms [t0, t1)
   JobList stage2;           // one job per term: (outer index of the term, term)
   JobList stage3;           // split-K jobs: (term - t0, term)
+  JobList stage2_res;       // A-resident jobs: runs of terms of one outer index, (outer, term)
   int splits = 1;
 };
 
@@ -113,6 +114,14 @@ struct kpme_plan_s {
   void* d_Qsl = nullptr;           // error-free split: fixed-point slices of Q [4][K^2][K]
   void* d_Ysl = nullptr;           // error-free split: fixed-point slices of Y [4][r0][K^2][K]
   float* d_rmZ = nullptr;          // error-free split: row maxima of Z (rows of stage 3)
+  float* d_rmQ = nullptr;          // row maxima of the float32 charge mesh (rows of stage 1)
+  float* d_rmY = nullptr;          // row maxima of Y (rows of stage 2)
+  bool ozt_res = false;            // stages 1 and 2 by the A-in-tensor-memory kernel, A resident
+  bool ozt_pp = false;             // stage 3 by the A-in-tensor-memory kernel, A per pair
+  bool ozf = false;                // stages 2 and 3 fused on the SM (K = 32, 64)
+  kpme::JobList stage23;           // fused jobs: term ranges, pairs (outer index, term)
+  kpme::JobList stage1_res;        // A-resident stage-1 jobs: runs of outer factors, (0, i)
+  CUtensorMap tmF_Q{}, tmF_Y{}, tmF_Z{};   // float32 A operands, 128 x 32 boxes
   int group_terms = 0;             // capacity of d_Z in terms
   kpme::JobList stage1;
   std::vector<kpme::TermGroup> groups;
@@ -207,6 +216,34 @@ struct OzArgs {
   int M, N, Kr, mode;
   const JobList* jobs;
 };
+struct OztArgs {
+  const CUtensorMap* tmF;    // float32 A rows (planes x K^2 rows x K)
+  const CUtensorMap* tmB;    // factor digits
+  const float* rowmax_in;
+  int64_t rm_in_bs;
+  float* out;
+  int64_t out_bs;
+  int out_base;
+  float* rowmax_out;
+  int64_t rm_out_bs;
+  int M, N, Kr;
+  int mode;                  // 1: sum of the item's pairs (atomics), 2: one plane per pair
+  bool a_res;
+  const JobList* jobs;
+};
+struct OzfArgs {
+  const CUtensorMap* tmY;    // float32 Y (r0 planes x K^2 rows x K), 128 x 32 boxes
+  const CUtensorMap* tmB2;   // digits of the axis-1 factors B_t
+  const CUtensorMap* tmB1;   // digits of the axis-0 factors A_t
+  float* phi;
+  int K;
+  const JobList* jobs;       // items: runs of terms, pairs (outer index, term)
+};
+bool ozf_supported(int K);
+cudaError_t launch_mp_ozf(kpme_plan_t P, const OzfArgs& a);
+bool ozt_supported(int K, int bn, bool a_res);
+cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a);
+cudaError_t launch_rowmax_rows(kpme_plan_t P, const float* in, int64_t rows, int K, float* out);
 cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a);
 cudaError_t launch_slice_rows(kpme_plan_t P, const void* in, bool in_double, int64_t rows_per_batch, int nbatch,
                               int K, void* out);
