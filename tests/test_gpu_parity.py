@@ -138,19 +138,29 @@ def test_energy_forces_water_box(torch, prec):
     assert e_phi < tp and e_f < tf
 
 
-@pytest.mark.parametrize("K,order,n,L", [(32, 4, 1001, 18.0), (48, 4, 2050, 30.0), (96, 6, 4003, 70.0)])
-def test_error_free_split_sizes(torch, K, order, n, L):
-    # ragged particle counts, K not a multiple of 32 (row maxima across warp boundaries),
-    # several 64-wide reduction chunks (K = 96)
+@pytest.mark.parametrize("K,order,n,L,fused", [
+    (32, 4, 1001, 18.0, "1"),    # fused stages 2-3, BN = 32 (four k3' per tile)
+    (32, 4, 1001, 18.0, "0"),    # tensor-memory A, resident and per pair
+    (48, 4, 2050, 30.0, "1"),    # K % 32 != 0: shared-memory A kernel, row maxima across warps
+    (64, 4, 3001, 40.0, "1"),    # fused, BN = 64
+    (64, 4, 3001, 40.0, "0"),
+    (96, 6, 4003, 70.0, "1"),    # tensor-memory A, two 64-wide chunks (second half empty)
+    (128, 4, 5003, 90.0, "1"),   # tensor-memory A, two full chunks, two column tiles
+])
+def test_error_free_split_sizes(torch, monkeypatch, K, order, n, L, fused):
+    # ragged particle counts and the kernel variants of the error-free split
+    monkeypatch.setenv("KPME_FUSED", fused)
     s = wl.random_system(n, L, K, order, seed=K + n)
     o = _oracle_skp(s)
     ref = skp.reciprocal(s.x, s.q, s.box, K, order, s.beta, s.skp_tol, skp=o)
     plan = _plan(s, "bf16x10")
     plan.set_skp(*skp.generators(o))
-    out = plan.energy_forces(dev(torch, s.x), dev(torch, s.q))
+    out = plan.energy_forces(dev(torch, s.x), dev(torch, s.q), virial=True)
     e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
-    print(f"bf16x10 K={K}: phi {e_phi:.2e} F {e_f:.2e}")
-    assert e_phi < 1e-6 and e_f < 1e-5
+    e_E = abs(host(out["energy"])[0] - ref["E"]) / abs(ref["E"])
+    e_W = abs(host(out["virial"])[0] - ref["W"]) / abs(ref["W"])
+    print(f"bf16x10 K={K} fused={fused}: phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e} W {e_W:.2e}")
+    assert e_phi < 1e-6 and e_f < 1e-5 and e_E < 1e-6 and e_W < 1e-5
 
 
 def test_potential_targets_differ_from_sources(torch):
