@@ -331,7 +331,8 @@ def main(argv=None):
     peak = peaks.get("bf16_tflops_sustained", 1700.0)
     if args.precision.startswith("tf32"):
         peak = peak / 2.0   # dense tf32 rate is half the bf16 rate
-    kname = ("mp_oz_kernel (SKP mode products, error-free split, tcgen05)" if args.precision == "bf16x10"
+    kname = ("SKP mode products, error-free split on tcgen05 (mp_ozt_kernel stage 1, mp_ozf_kernel fused "
+             "stages 2-3 for K = 32/64; mp_ozt/mp_oz_kernel otherwise)" if args.precision == "bf16x10"
              else "mp_tc_kernel (SKP mode products, tcgen05)")
     roof = {"bound": "tensor", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
