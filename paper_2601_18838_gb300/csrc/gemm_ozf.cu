@@ -13,10 +13,11 @@
 // D1; Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012), drained per term.  The
 // Phi tile is summed over the item's terms in registers and added to the mesh atomically.
 //
-// Tensor memory (512 columns): D of step 2 (2 BN), D of step 3 (2 BN), A of step 2 (Y_i
-// digits, 128), A of step 3 (Z_t digits, 128).  The tensor pipe alternates step 2 of term
-// j + 1 and step 3 of term j, and the transposed Z tile is double-buffered, so cutting term
-// j's digits overlaps the MMAs of term j + 1's first step.
+// Tensor memory (512 columns): one accumulator (2 BN) used by the two steps in turn, A of
+// step 2 (Y_i digits, 128) and two slots of A of step 3 (Z_t digits, 2 x 128).  The tensor
+// pipe alternates step 2 of term j + 1 and step 3 of term j; the transposed Z tile and the
+// Z_t digit slots are double-buffered, so cutting term j + 1's digits overlaps the MMAs of
+// term j.
 // All waits are bounded; a wait that runs out raises the device status word.
 #include "kpme_internal.cuh"
 #include "tc_common.cuh"
@@ -98,15 +99,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty_f = full_f + 1;
   uint64_t* full_a2 = empty_f + 1;
   uint64_t* empty_a2 = full_a2 + 1;
-  uint64_t* full_c2 = empty_a2 + 1;
-  uint64_t* empty_c2 = full_c2 + 1;
-  uint64_t* full_z = empty_c2 + 1;     // [2]
+  uint64_t* d_full = empty_a2 + 1;     // the accumulator shared by both steps
+  uint64_t* d_empty = d_full + 1;
+  uint64_t* full_z = d_empty + 1;      // [2]
   uint64_t* empty_z = full_z + 2;      // [2]
-  uint64_t* full_a3 = empty_z + 2;
-  uint64_t* empty_a3 = full_a3 + 1;
-  uint64_t* full_c3 = empty_a3 + 1;
-  uint64_t* empty_c3 = full_c3 + 1;
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty_c3 + 1);
+  uint64_t* full_a3 = empty_z + 2;     // [2] tensor-memory slots for Z_t digits
+  uint64_t* empty_a3 = full_a3 + 2;    // [2]
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty_a3 + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
   int2* s_pairs = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
   int* s_start = reinterpret_cast<int*>(s_pairs + prm.n_pairs);
@@ -126,16 +125,16 @@ __global__ void __launch_bounds__(kThreads, 1)
     mbar_init(empty_f, 128);
     mbar_init(full_a2, 128);
     mbar_init(empty_a2, 1);
-    mbar_init(full_c2, 1);
-    mbar_init(empty_c2, 128);
+    mbar_init(d_full, 1);
+    mbar_init(d_empty, 128);
     for (int b = 0; b < 2; ++b) {
       mbar_init(&full_z[b], 128);
       mbar_init(&empty_z[b], 128);
     }
-    mbar_init(full_a3, 128);
-    mbar_init(empty_a3, 1);
-    mbar_init(full_c3, 1);
-    mbar_init(empty_c3, 128);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&full_a3[b], 128);
+      mbar_init(&empty_a3[b], 1);
+    }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -150,7 +149,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *taddr_slot;
-  const uint32_t c_d2 = 0, c_d3 = 2 * BN, c_a2 = 4 * BN, c_a3 = 4 * BN + kACols;
+  // accumulator (both steps, in turn), Y_i digits, two slots of Z_t digits
+  const uint32_t c_d = 0, c_a2 = 2 * BN;
+  auto c_a3 = [&](int slot) { return (uint32_t)(2 * BN + kACols + slot * kACols); };
 
   // step order of one item with n terms: S2(0), then S2(j), S3(j - 1) for j = 1..n-1, then
   // S3(n - 1); op o in [0, 2n): o = 0 -> S2(0), o = 2n - 1 -> S3(n - 1), else odd o -> S2((o+1)/2),
@@ -214,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     if (lane == 0) {
       // ---------------- MMA issue ----------------
       const uint32_t id = idesc_bf16(kBM, BN);
-      int ib = 0, ia2 = 0, j2 = 0, ja3 = 0, j3 = 0;
+      int ib = 0, ia2 = 0, ja3 = 0, jd = 0;
       bool ok = true;
       auto run = [&](uint32_t a, uint32_t d, int s) {
         const uint64_t db0 = sdesc(smem_u32(ring_b + s * bstage));
@@ -236,6 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           bool s2;
           int j;
           op_of(o, n, s2, j);
+          const int slot = ja3 & 1;
           if (s2) {
             if (new_outer(p0, j)) {
               if (held) mma_commit(empty_a2);
@@ -246,16 +248,13 @@ __global__ void __launch_bounds__(kThreads, 1)
               ++ia2;
               held = true;
             }
-            if (j2 >= 1 && !mbar_wait(empty_c2, (uint32_t)(j2 - 1) & 1u, abort_flag, prm.status)) {
-              ok = false;
-              break;
-            }
-          } else {
-            if (!mbar_wait(full_a3, (uint32_t)ja3 & 1u, abort_flag, prm.status) ||
-                (j3 >= 1 && !mbar_wait(empty_c3, (uint32_t)(j3 - 1) & 1u, abort_flag, prm.status))) {
-              ok = false;
-              break;
-            }
+          } else if (!mbar_wait(&full_a3[slot], (uint32_t)(ja3 >> 1) & 1u, abort_flag, prm.status)) {
+            ok = false;
+            break;
+          }
+          if (jd >= 1 && !mbar_wait(d_empty, (uint32_t)(jd - 1) & 1u, abort_flag, prm.status)) {
+            ok = false;
+            break;
           }
           const int s = ib % prm.sb;
           if (!mbar_wait(&full_b[s], (uint32_t)(ib / prm.sb) & 1u, abort_flag, prm.status)) {
@@ -264,18 +263,16 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           fence_after();
           if (s2) {
-            run(tmem + c_a2, tmem + c_d2, s);
+            run(tmem + c_a2, tmem + c_d, s);
             mma_commit(&empty_b[s]);
-            mma_commit(full_c2);
-            ++j2;
           } else {
-            run(tmem + c_a3, tmem + c_d3, s);
+            run(tmem + c_a3(slot), tmem + c_d, s);
             mma_commit(&empty_b[s]);
-            mma_commit(empty_a3);
-            mma_commit(full_c3);
+            mma_commit(&empty_a3[slot]);
             ++ja3;
-            ++j3;
           }
+          mma_commit(d_full);
+          ++jd;
           ++ib;
         }
         if (ok && held) mma_commit(empty_a2);
@@ -308,20 +305,20 @@ __global__ void __launch_bounds__(kThreads, 1)
           mbar_arrive(full_a2);
           ++ia2;
         }
-        const int zb = jz & 1;
+        const int zb = jz & 1, slot = ja3 & 1;
         if (!__all_sync(0xffffffffu, mbar_wait(&full_z[zb], (uint32_t)(jz >> 1) & 1u, abort_flag, prm.status)) ||
-            (ja3 >= 1 &&
-             !__all_sync(0xffffffffu, mbar_wait(empty_a3, ((uint32_t)ja3 & 1u) ^ 1u, abort_flag, prm.status)))) {
+            (ja3 >= 2 && !__all_sync(0xffffffffu, mbar_wait(&empty_a3[slot], ((uint32_t)(ja3 >> 1) & 1u) ^ 1u,
+                                                            abort_flag, prm.status)))) {
           ok = false;
           break;
         }
         fence_after();
-        cut_row<K>(ztile + zb * (kTile / 4), r, lane_base + c_a3);
+        cut_row<K>(ztile + zb * (kTile / 4), r, lane_base + c_a3(slot));
         mbar_arrive(&empty_z[zb]);
         ++jz;
         tmem_wait_st();
         fence_before();
-        mbar_arrive(full_a3);
+        mbar_arrive(&full_a3[slot]);
         ++ja3;
       }
     }
@@ -335,7 +332,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int m = 32 * qd + lane;
     const int sub = m / K, k1 = m % K;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
-    int j2 = 0, jz = 0, j3 = 0;
+    int jd = 0, jz = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
       const int job = w / m_tiles, m0 = (w % m_tiles) * kBM;
@@ -348,49 +345,44 @@ __global__ void __launch_bounds__(kThreads, 1)
         int j;
         op_of(o, n, s2, j);
         if (!ok) continue;
+        const int zb = jz & 1;
+        if ((s2 && jz >= 2 &&
+             !__all_sync(0xffffffffu, mbar_wait(&empty_z[zb], ((uint32_t)(jz >> 1) & 1u) ^ 1u, abort_flag,
+                                                prm.status))) ||
+            !__all_sync(0xffffffffu, mbar_wait(d_full, (uint32_t)jd & 1u, abort_flag, prm.status))) {
+          ok = false;
+          continue;
+        }
+        fence_after();
         if (s2) {
-          const int zb = jz & 1;
           float* zt = ztile + zb * (kTile / 4);
-          if (!__all_sync(0xffffffffu, mbar_wait(full_c2, (uint32_t)j2 & 1u, abort_flag, prm.status)) ||
-              (jz >= 2 && !__all_sync(0xffffffffu, mbar_wait(&empty_z[zb], ((uint32_t)(jz >> 1) & 1u) ^ 1u,
-                                                              abort_flag, prm.status)))) {
-            ok = false;
-            continue;
-          }
-          fence_after();
 #pragma unroll 1
           for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t a0[16], a1[16];
-            tmem_ld16(lane_base + c_d2 + (uint32_t)c0, a0);
-            tmem_ld16(lane_base + c_d2 + (uint32_t)(BN + c0), a1);
+            tmem_ld16(lane_base + c_d + (uint32_t)c0, a0);
+            tmem_ld16(lane_base + c_d + (uint32_t)(BN + c0), a1);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i)
               zt[tile_off(sub * K + c0 + i, k1)] = __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
           }
-          fence_before();
-          mbar_arrive(empty_c2);
-          ++j2;
-          mbar_arrive(&full_z[zb]);
-          ++jz;
         } else {
-          if (!__all_sync(0xffffffffu, mbar_wait(full_c3, (uint32_t)j3 & 1u, abort_flag, prm.status))) {
-            ok = false;
-            continue;
-          }
-          fence_after();
 #pragma unroll
           for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t a0[16], a1[16];
-            tmem_ld16(lane_base + c_d3 + (uint32_t)c0, a0);
-            tmem_ld16(lane_base + c_d3 + (uint32_t)(BN + c0), a1);
+            tmem_ld16(lane_base + c_d + (uint32_t)c0, a0);
+            tmem_ld16(lane_base + c_d + (uint32_t)(BN + c0), a1);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[c0 + i] += __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
           }
-          fence_before();
-          mbar_arrive(empty_c3);
-          ++j3;
+        }
+        fence_before();
+        mbar_arrive(d_empty);
+        ++jd;
+        if (s2) {
+          mbar_arrive(&full_z[zb]);
+          ++jz;
         }
       }
       if (!ok || *abort_flag) continue;
