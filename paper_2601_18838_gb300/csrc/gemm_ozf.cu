@@ -332,6 +332,11 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int m = 32 * qd + lane;
     const int sub = m / K, k1 = m % K;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
+    // float offsets of (row sub K + c, column k1) in a Z tile: c * 32 + zoff[c % 8]
+    // (the 16-byte chunk index is XORed with row % 8 = c % 8, since K % 8 == 0)
+    int zoff[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) zoff[c] = tile_off(sub * K + c, k1) - c * 32;
     int jd = 0, jz = 0;
     bool ok = true;
     for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
@@ -362,9 +367,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             tmem_ld16(lane_base + c_d + (uint32_t)c0, a0);
             tmem_ld16(lane_base + c_d + (uint32_t)(BN + c0), a1);
             tmem_wait_ld();
+            float* zc = zt + c0 * 32;
 #pragma unroll
-            for (int i = 0; i < 16; ++i)
-              zt[tile_off(sub * K + c0 + i, k1)] = __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
+            for (int i = 0; i < 16; ++i) zc[i * 32 + zoff[i & 7]] = __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
           }
         } else {
 #pragma unroll
