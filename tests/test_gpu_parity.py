@@ -31,6 +31,31 @@ def _oracle_skp(s):
     return skp.build(s.K, s.order, s.box, s.beta, s.skp_tol)
 
 
+@pytest.mark.parametrize("prec", ["fp64", "bf16x10"])
+def test_sinc_skp_build_matches_oracle(torch, prec):
+    # §2.1.2: the GPU picks the same node count as the oracle's search and its energy, potentials
+    # and forces (with the m = 0 correction of the rule) match the oracle's sinc evaluation
+    s = wl.small()
+    plan = _plan(s, prec, skp_method="sinc")
+    R, err = plan.build_skp()
+    o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol, method="sinc")
+    assert R == o.R
+    assert err <= s.skp_tol
+    g = plan.get_skp()
+    assert g["r0"] == R and list(g["r1"]) == [1] * R
+    np.testing.assert_allclose(g["c"], o.c, rtol=1e-9)
+    ref = skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+    out = plan.energy_forces(dev(torch, s.x), dev(torch, s.q))
+    e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
+    e_E = abs(host(out["energy"])[0] - ref["E"]) / abs(ref["E"])
+    print(f"sinc {prec}: R={R} err={err:.2e} phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e}")
+    tp = 1e-9 if prec == "fp64" else 1e-6
+    assert e_phi < tp and e_f < 10 * tp and e_E < tp
+    # and it approximates the same operator as the SVD form
+    sv = skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=_oracle_skp(s))
+    assert rel(host(out["dEdq"]), sv["phi"]) < 1e-6
+
+
 @pytest.mark.parametrize("prec,order,n", [("fp64", 4, 999), ("fp32", 4, 999), ("fp64", 6, 1001), ("fp32", 8, 257)])
 def test_spread(torch, prec, order, n):
     s = wl.random_system(n, 17.0, 32, order, seed=n)
