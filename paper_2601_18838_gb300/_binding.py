@@ -219,6 +219,10 @@ class Plan:
         return dict(r0=r0.value, R=R.value, r1=r1, gen3=g3, gen2=g2, gen1=g1, sigma_outer=so,
                     sigma_inner=si, c=c.value)
 
+    def skp_c(self) -> float:
+        """The m = 0 correction constant c of the installed SKP (0 for the SVD form)."""
+        return float(self.get_skp()["c"])
+
     def set_precision(self, precision: str):
         self._call("kpme_set_precision", C.c_int(PRECISIONS[precision]))
         self.precision = precision

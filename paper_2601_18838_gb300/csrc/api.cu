@@ -898,10 +898,7 @@ kpme_status_t kpme_apply(kpme_plan_t P, const double* Q, double* Phi) {
   }
   if ((st = contract(P, m, P->d_Phi)) != KPME_OK) return st;
   KPME_CUDA_TRY(P, launch_convert(P->d_Phi, P->prec.fp64, Phi, true, k3, P->stream));
-  if (P->skp.c != 0.0) {
-    P->last_error = "kpme_apply with a non-zero correction constant is not supported";
-    return KPME_ERR_UNSUPPORTED;
-  }
+  if (P->skp.c != 0.0) KPME_CUDA_TRY(P, launch_mesh_correction(P, Q, Phi, k3, P->skp.c, P->d_qpsi));
   return KPME_OK;
 }
 

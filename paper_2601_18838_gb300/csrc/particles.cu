@@ -258,6 +258,35 @@ cudaError_t launch_gather(kpme_plan_t P, int64_t n, const double* x, const doubl
   return gather_t<float>(P, n, x, q, (const float*)Phi, phi, F, energy, ke);
 }
 
+namespace {
+// sum of a float64 array (one float64 atomic per block)
+__global__ void sum_kernel(const double* __restrict__ a, int64_t count, double* __restrict__ out) {
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+    acc += a[i];
+  const double s = block_sum_to_thread0<double>(acc);
+  if (threadIdx.x == 0 && s != 0.0) atomicAdd(out, s);
+}
+// a[i] -= c * (*sum)
+__global__ void shift_kernel(double* __restrict__ a, int64_t count, double c, const double* __restrict__ sum) {
+  const double d = c * *sum;
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+    a[i] -= d;
+}
+}  // namespace
+
+// Phi -= c * sum(Q) (the m = 0 correction of the quadrature SKP, applied on the mesh);
+// scratch: one float64 of device memory.
+cudaError_t launch_mesh_correction(kpme_plan_t P, const double* Q, double* Phi, int64_t count, double c,
+                                   double* scratch) {
+  cudaError_t e = cudaMemsetAsync(scratch, 0, sizeof(double), P->stream);
+  if (e != cudaSuccess) return e;
+  const int grid = grid_for(P, count);
+  sum_kernel<<<grid, kThreads, 0, P->stream>>>(Q, count, scratch);
+  shift_kernel<<<grid, kThreads, 0, P->stream>>>(Phi, count, c, scratch);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_dot(kpme_plan_t P, const void* a, const void* b, int64_t count, double* out) {
   const int grid = grid_for(P, count);
   if (P->prec.fp64)

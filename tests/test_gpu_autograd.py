@@ -76,3 +76,49 @@ def test_mixed_charges_forces_tensor_path(torch):
     e_f, e_phi = rel(-host(x.grad), ref["F"]), rel(host(q.grad), ref["phi"])
     print(f"mixed bf16x10: F {e_f:.2e} phi {e_phi:.2e} E {abs(E.item() - ref['E']) / abs(ref['E']):.2e}")
     assert e_f < 1e-5 and e_phi < 1e-6
+
+
+@pytest.mark.parametrize("method", ["svd", "sinc"])
+def test_potential_autograd_matches_oracle(torch, method):
+    # p = potentials at targets x of charges q at sources y (§1.1); L = sum(g p)
+    from oracle import spme
+    from paper_2601_18838_gb300 import Plan, reciprocal_potential
+    s = wl.random_system(96, 14.0, 32, 6, seed=41)
+    rng = np.random.default_rng(5)
+    xt = rng.uniform(-2.0, 16.0, (40, 3))
+    g = rng.normal(size=40)
+    o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol, method=method)
+    plan = Plan(s.box, s.K, s.order, s.beta, precision="fp64", skp_tol=s.skp_tol, max_n=s.n, skp_method=method)
+    if method == "svd":
+        plan.set_skp(*skp.generators(o))
+    else:
+        plan.build_skp()
+    y = dev(torch, s.x).requires_grad_(True)
+    q = dev(torch, s.q).requires_grad_(True)
+    x = dev(torch, xt).requires_grad_(True)
+    p = reciprocal_potential(y, q, x, plan)
+    (p * dev(torch, g)).sum().backward()
+
+    def pot(ys, qs, xs):
+        Phi = skp.apply(spme.spread(ys, qs, s.box, s.K, s.order), o)
+        return spme.gather(xs, np.zeros(len(xs)), s.box, s.K, s.order, Phi)[0]
+
+    assert rel(host(p), pot(s.x, s.q, xt)) < 1e-11
+    # dL/dq: the adjoint problem (charges g at the targets, potentials at the sources)
+    assert rel(host(q.grad), pot(xt, g, s.x)) < 1e-11
+    # dL/dx and dL/dy: central differences of the float64 oracle, h = 1e-4 A
+    h = 1e-4
+    L0 = lambda ys, xs: float(np.dot(g, pot(ys, s.q, xs)))
+    gx, gy = host(x.grad), host(y.grad)
+    for i, a in [(0, 0), (21, 1), (39, 2)]:
+        xp, xm = xt.copy(), xt.copy()
+        xp[i, a] += h
+        xm[i, a] -= h
+        fd = (L0(s.x, xp) - L0(s.x, xm)) / (2 * h)
+        assert abs(fd - gx[i, a]) < 1e-7 * np.abs(gx).max()
+    for j, a in [(2, 0), (50, 2), (95, 1)]:
+        yp, ym = s.x.copy(), s.x.copy()
+        yp[j, a] += h
+        ym[j, a] -= h
+        fd = (L0(yp, xt) - L0(ym, xt)) / (2 * h)
+        assert abs(fd - gy[j, a]) < 1e-7 * np.abs(gy).max()
