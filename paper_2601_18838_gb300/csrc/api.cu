@@ -751,8 +751,8 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
     const int kt = p.K / P->tile;
     const size_t nt = (size_t)kt * kt * kt;
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
-    if ((st = dalloc(P, (void**)&P->d_tcount, nt * sizeof(int))) != KPME_OK) return fail(st);
-    if ((st = dalloc(P, (void**)&P->d_tstart, (nt + 1) * sizeof(int))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_tcount, nt * kTileCounters * sizeof(int))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_tstart, (nt * kTileCounters + 1) * sizeof(int))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_rec_in, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_rec, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);

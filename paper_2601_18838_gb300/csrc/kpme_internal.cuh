@@ -168,6 +168,7 @@ cudaError_t launch_convert(const void* src, bool src_double, void* dst, bool dst
 cudaError_t launch_spread_raw(const kpme_params_t& p, int sm_count, cudaStream_t s, int64_t n, const double* x,
                               const double* q, float* Q, double* sumq);
 int choose_tile(int K, int order);
+constexpr int kTileCounters = 8;   // counters per tile of the cell sort (sub-ranges per tile)
 cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double* q, double* sumq);
 cudaError_t launch_spread_tiled(kpme_plan_t P, int64_t n, const double* q, float* Q);
 cudaError_t launch_gather_tiled(kpme_plan_t P, int64_t n, const double* q, const float* Phi, double* phi, double* F,

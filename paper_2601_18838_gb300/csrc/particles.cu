@@ -366,6 +366,7 @@ namespace {
 struct Tiling {
   int K, T, KT;   // mesh, tile edge (cells), tiles per axis
 };
+constexpr int kTileSub = kTileCounters;
 
 __device__ __forceinline__ int tile_of(const int (&g)[3], const Tiling& t) {
   return ((g[0] / t.T) * t.KT + g[1] / t.T) * t.KT + g[2] / t.T;
@@ -389,7 +390,10 @@ __global__ void tile_count_kernel(MeshGeom G, Tiling tl, int64_t n, const double
       fl[a] = (float)(f - (double)fh[a]);
     }
     const int t = tile_of(g, tl);
-    tile_slot[i] = make_int2(t, atomicAdd(count + t, 1));
+    // 8 counters per tile (chosen by the particle index) cut the contention of the returned
+    // atomics 8-fold; the sub-ranges of a tile are adjacent after the scan
+    const int c = t * kTileSub + (int)(i & (kTileSub - 1));
+    tile_slot[i] = make_int2(c, atomicAdd(count + c, 1));
     const int gp = g[0] | (g[1] << 10) | (g[2] << 20);
     rec[2 * i] = make_float4(__int_as_float(gp), __int_as_float((int)i), fh[0], fl[0]);
     rec[2 * i + 1] = make_float4(fh[1], fl[1], fh[2], fl[2]);
@@ -551,7 +555,7 @@ __global__ void __launch_bounds__(kThreads) spread_tile_kernel(Tiling tl, const 
   const int t = blockIdx.x;
   const int t2 = t % tl.KT, t1 = (t / tl.KT) % tl.KT, t0 = t / (tl.KT * tl.KT);
   const int lo0 = t0 * tl.T - H, lo1 = t1 * tl.T - H, lo2 = t2 * tl.T - H;
-  const int p0 = start[t], p1 = start[t + 1];
+  const int p0 = start[t * kTileSub], p1 = start[(t + 1) * kTileSub];
   if (p1 == p0) return;
   for (int i = threadIdx.x; i < D * D * D; i += kThreads) region[i] = 0.0f;
   __syncthreads();
@@ -612,7 +616,7 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
   const int t = blockIdx.x;
   const int t2 = t % tl.KT, t1 = (t / tl.KT) % tl.KT, t0 = t / (tl.KT * tl.KT);
   const int lo0 = t0 * tl.T - H, lo1 = t1 * tl.T - H, lo2 = t2 * tl.T - H;
-  const int p0 = start[t], p1 = start[t + 1];
+  const int p0 = start[t * kTileSub], p1 = start[(t + 1) * kTileSub];
   if (p1 == p0) return;
   for (int idx = threadIdx.x; idx < D * D * D; idx += kThreads) {
     const int l2 = idx % D, l1 = (idx / D) % D, l0 = idx / (D * D);
@@ -707,7 +711,7 @@ int choose_tile(int K, int order) {
 cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double* q, double* sumq) {
   if (n <= 0) return cudaSuccess;
   const Tiling tl = tiling_of(P);
-  const int nt = tl.KT * tl.KT * tl.KT;
+  const int nt = tl.KT * tl.KT * tl.KT * kTileSub;
   cudaError_t e = cudaMemsetAsync(P->d_tcount, 0, (size_t)nt * sizeof(int), P->stream);
   if (e != cudaSuccess) return e;
   const int grid = grid_for(P, n);
