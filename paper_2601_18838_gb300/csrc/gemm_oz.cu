@@ -364,6 +364,36 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
           }
         }
         asm volatile("bar.sync 1, 128;" ::: "memory");
+      } else if ((K % 16) == 0 && K >= 32) {
+        // K not a multiple of 32: a warp's 32 rows fall into at most two consuming rows
+        // glo and glo + 1; one masked warp maximum per part and column, kept by lane c % 32,
+        // published 32 columns per instruction
+        constexpr int kJ = (BN + 31) / 32;
+        const int glo = (m0 + 32 * wq) / K;
+        const bool hi = (row / K) != glo;
+        const bool two = __any_sync(0xffffffffu, hi);
+        unsigned int mlo[kJ], mhi[kJ];
+#pragma unroll
+        for (int j = 0; j < kJ; ++j) mlo[j] = mhi[j] = 0u;
+#pragma unroll
+        for (int c = 0; c < BN; ++c) {
+          const unsigned int v = live ? __float_as_uint(fabsf(acc[c])) : 0u;
+          const unsigned int a = __reduce_max_sync(0xffffffffu, hi ? 0u : v);
+          const unsigned int b = two ? __reduce_max_sync(0xffffffffu, hi ? v : 0u) : 0u;
+          if ((c & 31) == lane) {
+            mlo[c >> 5] = a;
+            mhi[c >> 5] = b;
+          }
+        }
+        if (m0 + 32 * wq < prm.M) {
+#pragma unroll
+          for (int j = 0; j < kJ; ++j) {
+            const int c = 32 * j + lane;
+            if (c >= BN) continue;
+            if (mlo[j] != 0u) atomicMax(dst + (int64_t)c * rows_next + glo, mlo[j]);
+            if (mhi[j] != 0u) atomicMax(dst + (int64_t)c * rows_next + glo + 1, mhi[j]);
+          }
+        }
       } else if (live) {
 #pragma unroll
         for (int c = 0; c < BN; ++c) atomicMax(dst + (int64_t)c * rows_next + row / K, __float_as_uint(fabsf(acc[c])));
