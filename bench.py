@@ -181,6 +181,7 @@ def run_batched(args):
     mine = [systems[i] for i in parts[rank]]
     ms = 0.0
     ranks = []
+    tuned = 0
     clocks = None
     if mine:
         batch = Batch([dict(box=s.box, K=s.K, order=s.order, beta=s.beta, skp_tol=s.skp_tol, max_n=s.n)
@@ -189,6 +190,7 @@ def run_batched(args):
         offsets = np.cumsum([0] + [s.n for s in mine])
         x = torch.tensor(np.concatenate([s.x for s in mine]), device=dev)
         q = torch.tensor(np.concatenate([s.q for s in mine]), device=dev)
+        tuned = batch.autotune(x, q, offsets)   # per class of systems, before any timed step
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         stream = torch.cuda.current_stream()
         for _ in range(args.warmup):
@@ -222,6 +224,7 @@ def run_batched(args):
             "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT["batched"], "precision": args.precision, "systems": n_sys,
                        "particles": int(sum(s.n for s in systems)), "skp_ranks_rank0": [int(r) for r in ranks],
+                       "autotune": {"systems_timed_rank0": int(tuned) if mine else 0},
                        "parallelism": f"systems sharded over {ws} ranks (longest processing time first)"
                        if ws > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write outside the timed events)"},
@@ -273,6 +276,7 @@ def main(argv=None):
     info = plan.info()
     x = torch.tensor(s.x, device=dev)
     q = torch.tensor(s.q, device=dev)
+    tune = plan.autotune(x, q)   # launch configuration picked by timing (before any timed step)
     out = {"energy": torch.empty(1, dtype=torch.float64, device=dev),
            "forces": torch.empty((s.n, 3), dtype=torch.float64, device=dev),
            "dEdq": torch.empty(s.n, dtype=torch.float64, device=dev),
@@ -403,6 +407,7 @@ def main(argv=None):
             "vs_baseline": None, "dtype": DTYPE.get(args.precision, args.precision), "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": args.precision,
                        "skp_rank": R, "skp_r0": info["r0"], "skp_rel_err": skp_err,
+                       "autotune": {k: tune[k] for k in ("tile", "fused", "split", "ms_per_eval")},
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "tflops_useful": useful / (ms_step * 1e-3) / 1e12,

@@ -239,6 +239,42 @@ kpme_status_t kpme_batch_energy_forces(kpme_batch_t batch, const int64_t* offset
 
 const char* kpme_batch_last_error(kpme_batch_t batch);
 
+/* ---- autotuning of the launch configuration ----
+ * The knobs change only the schedule (every setting gives the same result up to the
+ * order of floating-point sums):
+ *   tile     - edge T of the cell-sort tiles of spreading and gathering (T divides K,
+ *              T >= order - 1, the staged region (T + order - 1)^3 float32 <= 200 KB);
+ *              0 = untiled path (float64 meshes), not tunable;
+ *   fused    - 1: SKP stages 2 and 3 fused on the SM where the kernel exists (error-free
+ *              split, K = 32 or 64), 0: separate stages;
+ *   split    - split-K multiplier of the term ranges: 1 (half), 2 (the cost model's
+ *              choice), 4 (double). */
+typedef struct {
+  int tile, fused, split;
+  int from_cache;        /* 1: taken from the cache file, not timed                   */
+  double ms_per_eval;    /* measured (or cached) time of one kpme_energy_forces        */
+} kpme_tune_t;
+
+/* Time kpme_energy_forces for the n particles x, q (DEVICE, as in kpme_energy_forces) by
+ * coordinate descent over the knobs (each candidate: 2 warm-up and 5 timed evaluations,
+ * CUDA events on the plan's stream), leave the plan configured with the fastest and
+ * report it in *out.  cache_path (may be NULL): a text file with one line per problem key
+ * (K, order, precision, log2 n, SM count, compute capability); a matching entry is applied
+ * without timing, a new result is appended.  Needs a built SKP (else KPME_ERR_NOT_BUILT).
+ * Allocates scratch for the outputs; synchronises the stream. */
+kpme_status_t kpme_autotune(kpme_plan_t plan, int64_t n, const double* x, const double* q, const char* cache_path,
+                            kpme_tune_t* out);
+
+/* Apply a configuration (tile, fused, split of *t) to a plan. */
+kpme_status_t kpme_set_tune(kpme_plan_t plan, const kpme_tune_t* t);
+
+/* Autotune a batch: the first system of each class (K, order, precision, log2 n) is tuned
+ * with kpme_autotune on its own particles (offsets, x, q as in kpme_batch_energy_forces);
+ * the others of the class take its configuration.  n_tuned (may be NULL): number of
+ * systems timed.  The batch's graph is captured again at the next evaluation. */
+kpme_status_t kpme_batch_autotune(kpme_batch_t batch, const int64_t* offsets, const double* x, const double* q,
+                                  const char* cache_path, int* n_tuned);
+
 typedef struct {
   int K, order, precision, r0, R;
   double skp_rel_err;

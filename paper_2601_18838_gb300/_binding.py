@@ -23,7 +23,8 @@ EXPORTS = [
     "kpme_spread", "kpme_apply", "kpme_gather", "kpme_set_profiling", "kpme_get_profile",
     "kpme_get_info", "kpme_status_string", "kpme_last_error", "kpme_spread_noalloc",
     "kpme_batch_create", "kpme_batch_destroy", "kpme_batch_set_stream", "kpme_batch_build_skp",
-    "kpme_batch_energy_forces", "kpme_batch_last_error",
+    "kpme_batch_energy_forces", "kpme_batch_last_error", "kpme_autotune", "kpme_set_tune",
+    "kpme_batch_autotune",
 ]
 
 
@@ -33,6 +34,15 @@ class Params(C.Structure):
         ("order", C.c_int), ("K", C.c_int), ("skp_tol", C.c_double), ("skp_method", C.c_int),
         ("precision", C.c_int), ("max_n", C.c_int64), ("coulomb_k", C.c_double),
     ]
+
+
+class Tune(C.Structure):
+    _fields_ = [("tile", C.c_int), ("fused", C.c_int), ("split", C.c_int), ("from_cache", C.c_int),
+                ("ms_per_eval", C.c_double)]
+
+
+def _tune_dict(t):
+    return {f: getattr(t, f) for f, _ in Tune._fields_}
 
 
 class Info(C.Structure):
@@ -92,6 +102,9 @@ def lib():
         "kpme_batch_build_skp": (st, [_vp, _ip]),
         "kpme_batch_energy_forces": (st, [_vp, C.POINTER(C.c_int64), _vp, _vp, _vp, _vp, _vp, _vp]),
         "kpme_batch_last_error": (C.c_char_p, [_vp]),
+        "kpme_autotune": (st, [_vp, _i64, _vp, _vp, C.c_char_p, C.POINTER(Tune)]),
+        "kpme_set_tune": (st, [_vp, C.POINTER(Tune)]),
+        "kpme_batch_autotune": (st, [_vp, C.POINTER(C.c_int64), _vp, _vp, C.c_char_p, _ip]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -218,6 +231,20 @@ class Plan:
                    _np_ptr(g1), _np_ptr(so), _np_ptr(si), C.byref(c))
         return dict(r0=r0.value, R=R.value, r1=r1, gen3=g3, gen2=g2, gen1=g1, sigma_outer=so,
                     sigma_inner=si, c=c.value)
+
+    def autotune(self, x, q, cache: str | None = None) -> dict:
+        """kpme_autotune on the particles x, q: leaves the plan on the fastest configuration."""
+        import torch
+        n = x.shape[0]
+        _check_dev(x, "x", torch.float64, (n, 3))
+        _check_dev(q, "q", torch.float64, (n,))
+        t = Tune()
+        self._call("kpme_autotune", C.c_int64(n), _ptr(x), _ptr(q), cache.encode() if cache else None, C.byref(t))
+        return _tune_dict(t)
+
+    def set_tune(self, tile: int, fused: int, split: int):
+        t = Tune(tile, fused, split, 0, 0.0)
+        self._call("kpme_set_tune", C.byref(t))
 
     def skp_c(self) -> float:
         """The m = 0 correction constant c of the installed SKP (0 for the SVD form)."""
@@ -347,6 +374,19 @@ class Batch:
         r = np.zeros(self.n_sys, np.int32)
         self._call("kpme_batch_build_skp", r.ctypes.data_as(_ip))
         return r
+
+    def autotune(self, x, q, offsets, cache: str | None = None) -> int:
+        """kpme_batch_autotune: returns the number of systems that were timed."""
+        import numpy as np
+        import torch
+        n = x.shape[0]
+        _check_dev(x, "x", torch.float64, (n, 3))
+        _check_dev(q, "q", torch.float64, (n,))
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        k = C.c_int()
+        self._call("kpme_batch_autotune", off.ctypes.data_as(C.POINTER(C.c_int64)), _ptr(x), _ptr(q),
+                   cache.encode() if cache else None, C.byref(k))
+        return k.value
 
     def energy_forces(self, x, q, offsets, forces: bool = True, dEdq: bool = True, virial: bool = False):
         import numpy as np

@@ -187,6 +187,33 @@ bool getenv_flag(const char* name, bool dflt) {
   return e[0] != '0';
 }
 
+}  // namespace
+
+// Spreading tile edge T: divides K, covers the stencil halo (T >= n - 1) and its staged
+// region (T + n - 1)^3 float32 fits in shared memory.
+bool kpme::tile_ok(int K, int order, int T) {
+  const int D = T + order - 1;
+  return T >= 1 && K % T == 0 && T >= order - 1 && (size_t)D * D * D * sizeof(float) <= 200 * 1024;
+}
+
+// (Re)allocate the cell-sort counters for tile edge T (8 counters per tile).
+kpme_status_t kpme::set_tile(kpme_plan_t P, int T) {
+  if (!tile_ok(P->p.K, P->p.order, T)) return KPME_ERR_INVALID_ARG;
+  if (T == P->tile && P->d_tcount) return KPME_OK;
+  dfree(P->d_tcount);
+  dfree(P->d_tstart);
+  const int kt = P->p.K / T;
+  const size_t nt = (size_t)kt * kt * kt;
+  kpme_status_t st;
+  if ((st = dalloc(P, (void**)&P->d_tcount, nt * kTileCounters * sizeof(int))) != KPME_OK) return st;
+  if ((st = dalloc(P, (void**)&P->d_tstart, (nt * kTileCounters + 1) * sizeof(int))) != KPME_OK) return st;
+  P->tile = T;
+  drop_graph(P);
+  return KPME_OK;
+}
+
+namespace kpme {
+
 // Jobs over runs of pairs that share their A operand: every run [a, b) is cut into pieces
 // of at most J pairs, J chosen so that the persistent grid's makespan, rounds of
 // ceil(items / SMs) times (J + 1) (one pair's worth for cutting A), is smallest.
@@ -263,7 +290,7 @@ kpme_status_t install_skp(kpme_plan_t P) {
   if (pi.tensor) choose_tc_tiles(P);
   P->ozt_res = pi.oz && ozt_supported(K, P->tc_bn, true);
   P->ozt_pp = pi.oz && ozt_supported(K, P->tc_bn, false);
-  P->ozf = P->ozt_res && ozf_supported(K) && P->tc_bn == K && getenv_flag("KPME_FUSED", true);
+  P->ozf = P->ozt_res && ozf_supported(K) && P->tc_bn == K && P->allow_fused;
   if (pi.oz) {
     const size_t k2 = (size_t)K * K;
     if (P->ozt_res) {
@@ -318,6 +345,7 @@ kpme_status_t install_skp(kpme_plan_t P) {
         }
       }
     }
+    splits = std::max(1, std::min(nt, splits * P->tune_split / 2));
     g.splits = splits;
     int pos = 0;
     g.stage3.h_start.push_back(0);
@@ -361,6 +389,7 @@ kpme_status_t install_skp(kpme_plan_t P) {
         splits = sp;
       }
     }
+    splits = std::max(1, std::min(R, splits * P->tune_split / 2));
     P->stage23.h_start.assign(1, 0);
     P->stage23.h_pairs.clear();
     for (int k = 0; k < splits; ++k) {
@@ -644,7 +673,7 @@ kpme_status_t common_checks(kpme_plan_t P, int64_t n) {
   return KPME_OK;
 }
 
-}  // namespace
+}  // namespace kpme
 
 namespace kpme {
 kpme_status_t plan_install_skp(kpme_plan_t P, const SkpHost& S) {
@@ -746,13 +775,11 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->d_sumq = acc;
   P->d_energy = acc + 1;
   P->d_qpsi = acc + 2;
-  P->tile = choose_tile(p.K, p.order);
-  if (P->tile > 0) {
-    const int kt = p.K / P->tile;
-    const size_t nt = (size_t)kt * kt * kt;
+  P->allow_fused = getenv_flag("KPME_FUSED", true);
+  P->tile = 0;
+  if (choose_tile(p.K, p.order) > 0) {
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
-    if ((st = dalloc(P, (void**)&P->d_tcount, nt * kTileCounters * sizeof(int))) != KPME_OK) return fail(st);
-    if ((st = dalloc(P, (void**)&P->d_tstart, (nt * kTileCounters + 1) * sizeof(int))) != KPME_OK) return fail(st);
+    if ((st = set_tile(P, choose_tile(p.K, p.order))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_rec_in, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_rec, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);

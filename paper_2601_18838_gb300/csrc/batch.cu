@@ -6,6 +6,8 @@
 #include "kpme_internal.cuh"
 
 #include <algorithm>
+#include <cmath>
+#include <string>
 #include <cstring>
 #include <map>
 #include <new>
@@ -164,6 +166,43 @@ kpme_status_t kpme_batch_energy_forces(kpme_batch_t B, const int64_t* offsets, c
   }
   cudaError_t e = cudaGraphLaunch(B->exec, B->stream);
   if (e != cudaSuccess) return fail(B, "cudaGraphLaunch", e);
+  return KPME_OK;
+}
+
+kpme_status_t kpme_batch_autotune(kpme_batch_t B, const int64_t* offsets, const double* x, const double* q,
+                                  const char* cache_path, int* n_tuned) {
+  if (!B || !offsets) return KPME_ERR_INVALID_ARG;
+  std::map<std::tuple<int, int, int, int>, kpme_tune_t> tuned;
+  int timed = 0;
+  for (size_t s = 0; s < B->plans.size(); ++s) {
+    kpme_plan_t P = B->plans[s];
+    const int64_t o = offsets[s], n = offsets[s + 1] - offsets[s];
+    if (n < 0) return KPME_ERR_INVALID_ARG;
+    const int nb = n > 0 ? (int)std::floor(std::log2((double)n)) : 0;
+    const auto key = std::make_tuple(P->p.K, P->p.order, P->p.precision, nb);
+    auto it = tuned.find(key);
+    kpme_status_t st;
+    if (it != tuned.end()) {
+      st = kpme_set_tune(P, &it->second);
+    } else {
+      kpme_tune_t t{};
+      st = kpme_autotune(P, n, x ? x + 3 * o : nullptr, q ? q + o : nullptr, cache_path, &t);
+      if (st == KPME_OK) {
+        tuned[key] = t;
+        if (!t.from_cache) ++timed;
+      }
+    }
+    if (st != KPME_OK) {
+      B->last_error = std::string("autotune of system ") + std::to_string(s) + ": " + kpme_last_error(P);
+      return st;
+    }
+  }
+  if (B->exec) {
+    cudaGraphExecDestroy(B->exec);
+    B->exec = nullptr;
+  }
+  B->key.clear();
+  if (n_tuned) *n_tuned = timed;
   return KPME_OK;
 }
 

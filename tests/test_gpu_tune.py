@@ -1,0 +1,68 @@
+"""The autotuner: every configuration it may pick gives the same evaluation (up to summation
+order), the chosen one is reported and cached, and a batch is tuned per class of systems."""
+import numpy as np
+import pytest
+
+from oracle import skp
+from paper_2601_18838_gb300 import workloads as wl
+from tests._gpu_util import cuda_or_skip, dev, host, rel
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = cuda_or_skip()
+    import __graft_entry__ as g
+    g.build()
+    return t
+
+
+@pytest.mark.parametrize("K,order,n,L", [(64, 4, 3000, 40.0), (48, 4, 2001, 30.0)])
+def test_autotune_keeps_results_and_caches(torch, tmp_path, K, order, n, L):
+    from paper_2601_18838_gb300 import Plan
+    s = wl.random_system(n, L, K, order, seed=K + 7)
+    o = skp.build(K, order, s.box, s.beta, s.skp_tol)
+    ref = skp.reciprocal(s.x, s.q, s.box, K, order, s.beta, s.skp_tol, skp=o)
+    x, q = dev(torch, s.x), dev(torch, s.q)
+    plan = Plan(s.box, K, order, s.beta, precision="bf16x10", skp_tol=s.skp_tol, max_n=n)
+    plan.set_skp(*skp.generators(o))
+    cache = str(tmp_path / "tune.txt")
+    t = plan.autotune(x, q, cache=cache)
+    assert t["from_cache"] == 0 and t["ms_per_eval"] > 0
+    assert t["split"] in (1, 2, 4) and t["fused"] in (0, 1) and t["tile"] in (4, 8, 16, 32)
+    out = plan.energy_forces(x, q)
+    assert rel(host(out["dEdq"]), ref["phi"]) < 1e-6 and rel(host(out["forces"]), ref["F"]) < 1e-5
+    # every knob setting evaluates the same operator
+    for tile, fused, split in [(8, 1, 1), (16, 0, 4), (4, 1, 2)]:
+        if K % tile or (K not in (32, 64) and fused):
+            continue
+        plan.set_tune(tile, fused, split)
+        o2 = plan.energy_forces(x, q)
+        assert rel(host(o2["dEdq"]), ref["phi"]) < 1e-6
+    # a second plan with the same problem key takes the cached choice without timing
+    p2 = Plan(s.box, K, order, s.beta, precision="bf16x10", skp_tol=s.skp_tol, max_n=n)
+    p2.set_skp(*skp.generators(o))
+    t2 = p2.autotune(x, q, cache=cache)
+    assert t2["from_cache"] == 1
+    assert (t2["tile"], t2["fused"], t2["split"]) == (t["tile"], t["fused"], t["split"])
+    assert open(cache).read().count("\n") == 1
+
+
+def test_batch_autotune_per_class(torch):
+    from paper_2601_18838_gb300 import Batch
+    systems = [wl.random_system(n, L, K, 4, seed=n) for n, L, K in
+               [(1500, 28.0, 32), (1700, 30.0, 32), (2300, 40.0, 48), (900, 26.0, 32)]]
+    batch = Batch([dict(box=s.box, K=s.K, order=s.order, beta=s.beta, skp_tol=s.skp_tol, max_n=s.n)
+                   for s in systems], precision="bf16x10")
+    batch.build_skp()
+    offsets = np.cumsum([0] + [s.n for s in systems])
+    x = dev(torch, np.concatenate([s.x for s in systems]))
+    q = dev(torch, np.concatenate([s.q for s in systems]))
+    before = batch.energy_forces(x, q, offsets)
+    timed = batch.autotune(x, q, offsets)
+    assert 1 <= timed <= len(systems)
+    after = batch.energy_forces(x, q, offsets)
+    np.testing.assert_allclose(host(after["energy"]), host(before["energy"]), rtol=1e-6)
+    assert rel(host(after["forces"]), host(before["forces"])) < 1e-5
+    batch.close()
