@@ -346,6 +346,19 @@ def main(argv=None):
             "ms_per_launch": per_launch_ms}
     if not tensor:
         roof = None
+    # spreading and gathering against HBM: algorithmic bytes per evaluation (positions and
+    # charges in float64, the float32 mesh written or read once, potentials and forces out)
+    hbm = peaks.get("hbm_gbs", 6800.0)
+    mesh_b = 4 * K ** 3
+    part = {}
+    for step, nbytes in (("spread", s.n * 32 + mesh_b), ("gather", mesh_b + s.n * 32 + s.n * 32)):
+        ms_k = prof[step][0] / args.steps if step in prof else 0.0
+        gbs = nbytes / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None
+        part[step] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs,
+                      "frac_hbm": (gbs / hbm) if gbs else None}
+    part["hbm_peak_gbs"] = hbm
+    part["note"] = ("spread includes the cell sort (count, scan, scatter) and the mesh clear; "
+                    "the kernels are bound by shared-memory atomics and latency at these sizes")
 
     # end to end through the public API with host buffers
     xh = torch.tensor(s.x).pin_memory()
@@ -411,7 +424,8 @@ def main(argv=None):
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "tflops_useful": useful / (ms_step * 1e-3) / 1e12,
-            "roofline": roof, "e2e": e2e, "gpu_launches": int(round(launches_per_step * args.steps)),
+            "roofline": roof, "particle_kernels": part, "e2e": e2e,
+            "gpu_launches": int(round(launches_per_step * args.steps)),
             "fp64_form": fp64, "clocks": clocks, "cpu_baseline": cb,
             "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         }
