@@ -351,10 +351,10 @@ def main(argv=None):
     hbm = peaks.get("hbm_gbs", 6800.0)
     mesh_b = 4 * K ** 3
     part = {}
-    for step, nbytes in (("spread", s.n * 32 + mesh_b), ("gather", mesh_b + s.n * 32 + s.n * 32)):
-        ms_k = prof[step][0] / args.steps if step in prof else 0.0
+    for kname, nbytes in (("spread", s.n * 32 + mesh_b), ("gather", mesh_b + s.n * 32 + s.n * 32)):
+        ms_k = prof[kname][0] / args.steps if kname in prof else 0.0
         gbs = nbytes / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None
-        part[step] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs,
+        part[kname] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs,
                       "frac_hbm": (gbs / hbm) if gbs else None}
     part["hbm_peak_gbs"] = hbm
     part["note"] = ("spread includes the cell sort (count, scan, scatter) and the mesh clear; "

@@ -244,7 +244,10 @@ const char* kpme_batch_last_error(kpme_batch_t batch);
  * order of floating-point sums):
  *   tile     - edge T of the cell-sort tiles of spreading and gathering (T divides K,
  *              T >= order - 1, the staged region (T + order - 1)^3 float32 <= 200 KB);
- *              0 = untiled path (float64 meshes), not tunable;
+ *              -1 = no cell sort (float64 atomics on the mesh, untiled gathering: fewer
+ *              launches, faster for few particles per mesh point), where T could be set;
+ *              0 = untiled path (float64 meshes) of a plan the tiling does not fit, not
+ *              tunable;
  *   fused    - 1: SKP stages 2 and 3 fused on the SM where the kernel exists (error-free
  *              split, K = 32 or 64), 0: separate stages;
  *   split    - split-K multiplier of the term ranges: 1 (half), 2 (the cost model's

@@ -13,11 +13,12 @@
 // D1; Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012), drained per term.  The
 // Phi tile is summed over the item's terms in registers and added to the mesh atomically.
 //
-// Tensor memory (512 columns): one accumulator (2 BN) used by the two steps in turn, A of
-// step 2 (Y_i digits, 128) and two slots of A of step 3 (Z_t digits, 2 x 128).  The tensor
-// pipe alternates step 2 of term j + 1 and step 3 of term j; the transposed Z tile and the
-// Z_t digit slots are double-buffered, so cutting term j + 1's digits overlaps the MMAs of
-// term j.
+// Tensor memory (512 columns): two accumulators (2 BN each) taken by the steps in turn, so
+// the epilogue drains one while the tensor pipe fills the other, A of step 2 (Y_i digits,
+// 128) and the slots of A of step 3 (Z_t digits, 128 each: one for K = 64, two for K = 32).
+// The tensor pipe alternates step 2 of term j + 1 and step 3 of term j; the transposed Z
+// tile is double-buffered, so cutting term j + 1's digits overlaps the MMAs of step 2 of
+// term j + 2.
 // All waits are bounded; a wait that runs out raises the device status word.
 #include "kpme_internal.cuh"
 #include "tc_common.cuh"
@@ -86,6 +87,8 @@ __global__ void __launch_bounds__(kThreads, 1)
   constexpr int kBSlice = BN * 128;
   constexpr int kKSteps = K / 16;
   constexpr int kSub = kBM / K;         // k3' values per tile
+  constexpr int kA3 = (512 - 4 * BN - kACols) / kACols;   // Z_t digit slots after 2 accumulators
+  static_assert(kA3 >= 1 && 4 * BN + (1 + kA3) * kACols <= 512, "tensor memory layout");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int bstage = kSlices * kBSlice;
@@ -99,9 +102,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty_f = full_f + 1;
   uint64_t* full_a2 = empty_f + 1;
   uint64_t* empty_a2 = full_a2 + 1;
-  uint64_t* d_full = empty_a2 + 1;     // the accumulator shared by both steps
-  uint64_t* d_empty = d_full + 1;
-  uint64_t* full_z = d_empty + 1;      // [2]
+  uint64_t* d_full = empty_a2 + 1;     // [2] accumulators, taken by the ops in turn
+  uint64_t* d_empty = d_full + 2;      // [2]
+  uint64_t* full_z = d_empty + 2;      // [2]
   uint64_t* empty_z = full_z + 2;      // [2]
   uint64_t* full_a3 = empty_z + 2;     // [2] tensor-memory slots for Z_t digits
   uint64_t* empty_a3 = full_a3 + 2;    // [2]
@@ -122,17 +125,19 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&empty_b[s], 1);
     }
     mbar_init(full_f, 1);
-    mbar_init(empty_f, 128);
-    mbar_init(full_a2, 128);
+    mbar_init(empty_f, 4);
+    mbar_init(full_a2, 4);
     mbar_init(empty_a2, 1);
-    mbar_init(d_full, 1);
-    mbar_init(d_empty, 128);
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&full_z[b], 128);
-      mbar_init(&empty_z[b], 128);
+      mbar_init(&d_full[b], 1);
+      mbar_init(&d_empty[b], 4);
     }
     for (int b = 0; b < 2; ++b) {
-      mbar_init(&full_a3[b], 128);
+      mbar_init(&full_z[b], 4);
+      mbar_init(&empty_z[b], 4);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&full_a3[b], 4);
       mbar_init(&empty_a3[b], 1);
     }
     *abort_flag = 0;
@@ -149,9 +154,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *taddr_slot;
-  // accumulator (both steps, in turn), Y_i digits, two slots of Z_t digits
-  const uint32_t c_d = 0, c_a2 = 2 * BN;
-  auto c_a3 = [&](int slot) { return (uint32_t)(2 * BN + kACols + slot * kACols); };
+  // two accumulators (ops in turn), Y_i digits, kA3 slots of Z_t digits
+  auto c_d = [](int b) { return (uint32_t)(b * 2 * BN); };
+  const uint32_t c_a2 = 4 * BN;
+  auto c_a3 = [&](int slot) { return (uint32_t)(4 * BN + kACols + slot * kACols); };
 
   // step order of one item with n terms: S2(0), then S2(j), S3(j - 1) for j = 1..n-1, then
   // S3(n - 1); op o in [0, 2n): o = 0 -> S2(0), o = 2n - 1 -> S3(n - 1), else odd o -> S2((o+1)/2),
@@ -214,45 +220,40 @@ __global__ void __launch_bounds__(kThreads, 1)
   } else if (warp == 1) {
     if (lane == 0) {
       // ---------------- MMA issue ----------------
+      // The Y_i digits are released right after the last step 2 that reads them, so the
+      // converters cut the next Y_i while step 3 of the previous term runs.
       const uint32_t id = idesc_bf16(kBM, BN);
       int ib = 0, ia2 = 0, ja3 = 0, jd = 0;
       bool ok = true;
-      auto run = [&](uint32_t a, uint32_t d, int s) {
-        const uint64_t db0 = sdesc(smem_u32(ring_b + s * bstage));
-#pragma unroll
-        for (int kk = 0; kk < kKSteps; ++kk)
-#pragma unroll
-          for (int p = 0; p < kProducts; ++p) {
-            const uint32_t at = a + (uint32_t)(pa(p) * 32 + kk * 8);
-            const uint64_t db = db0 + (uint64_t)((pb(p) * kBSlice + kk * 32) >> 4);
-            const uint32_t acc = (kk == 0 && p <= 1) ? 0u : 1u;
-            mma_bf16_ta(p == 0 ? d : d + BN, at, db, id, acc);
-          }
-      };
       for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
         const int job = w / m_tiles;
         const int p0 = s_start[job], n = s_start[job + 1] - p0;
-        bool held = false;
+        // bit j: term j starts a new outer index (read once per item, not between MMAs)
+        uint64_t nmask = 0;
+        if (n <= 64) {
+#pragma unroll 8
+          for (int j = 0; j < n; ++j) nmask |= (uint64_t)new_outer(p0, j) << j;
+        }
+        auto newo = [&](int j) { return n <= 64 ? ((nmask >> j) & 1u) != 0 : new_outer(p0, j); };
         for (int o = 0; o < 2 * n && ok; ++o) {
           bool s2;
           int j;
           op_of(o, n, s2, j);
-          const int slot = ja3 & 1;
+          const int slot = ja3 % kA3;
           if (s2) {
-            if (new_outer(p0, j)) {
-              if (held) mma_commit(empty_a2);
+            if (newo(j)) {
               if (!mbar_wait(full_a2, (uint32_t)ia2 & 1u, abort_flag, prm.status)) {
                 ok = false;
                 break;
               }
               ++ia2;
-              held = true;
             }
-          } else if (!mbar_wait(&full_a3[slot], (uint32_t)(ja3 >> 1) & 1u, abort_flag, prm.status)) {
+          } else if (!mbar_wait(&full_a3[slot], (uint32_t)(ja3 / kA3) & 1u, abort_flag, prm.status)) {
             ok = false;
             break;
           }
-          if (jd >= 1 && !mbar_wait(d_empty, (uint32_t)(jd - 1) & 1u, abort_flag, prm.status)) {
+          const int db = jd & 1;
+          if (jd >= 2 && !mbar_wait(&d_empty[db], ((uint32_t)(jd >> 1) & 1u) ^ 1u, abort_flag, prm.status)) {
             ok = false;
             break;
           }
@@ -262,20 +263,29 @@ __global__ void __launch_bounds__(kThreads, 1)
             break;
           }
           fence_after();
+          const uint32_t a = tmem + (s2 ? c_a2 : c_a3(slot));
+          const uint32_t d = tmem + c_d(db);
+          const uint64_t db0 = sdesc(smem_u32(ring_b + s * bstage));
+#pragma unroll
+          for (int kk = 0; kk < kKSteps; ++kk)
+#pragma unroll
+            for (int p = 0; p < kProducts; ++p) {
+              const uint32_t at = a + (uint32_t)(pa(p) * 32 + kk * 8);
+              const uint64_t dbp = db0 + (uint64_t)((pb(p) * kBSlice + kk * 32) >> 4);
+              const uint32_t acc = (kk == 0 && p <= 1) ? 0u : 1u;
+              mma_bf16_ta(p == 0 ? d : d + BN, at, dbp, id, acc);
+            }
+          mma_commit(&empty_b[s]);
           if (s2) {
-            run(tmem + c_a2, tmem + c_d, s);
-            mma_commit(&empty_b[s]);
+            if (j + 1 == n || newo(j + 1)) mma_commit(empty_a2);
           } else {
-            run(tmem + c_a3(slot), tmem + c_d, s);
-            mma_commit(&empty_b[s]);
             mma_commit(&empty_a3[slot]);
             ++ja3;
           }
-          mma_commit(d_full);
+          mma_commit(&d_full[db]);
           ++jd;
           ++ib;
         }
-        if (ok && held) mma_commit(empty_a2);
       }
     }
   } else if (warp < 6) {
@@ -288,8 +298,10 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
       const int job = w / m_tiles;
       const int p0 = s_start[job], n = s_start[job + 1] - p0;
-      for (int j = 0; j < n && ok; ++j) {
-        if (new_outer(p0, j)) {
+      // digits in the order the tensor pipe consumes them: Y_i of term t (when its outer index
+      // changes) before Z of term t - 1, since step 2 of term t precedes step 3 of term t - 1
+      for (int t = 0; t <= n && ok; ++t) {
+        if (t < n && new_outer(p0, t)) {
           if (!__all_sync(0xffffffffu, mbar_wait(full_f, (uint32_t)jf & 1u, abort_flag, prm.status)) ||
               (ia2 >= 1 &&
                !__all_sync(0xffffffffu, mbar_wait(empty_a2, ((uint32_t)ia2 & 1u) ^ 1u, abort_flag, prm.status)))) {
@@ -298,27 +310,28 @@ __global__ void __launch_bounds__(kThreads, 1)
           }
           fence_after();
           cut_row<K>(ftile, r, lane_base + c_a2);
-          mbar_arrive(empty_f);
+          mbar_arrive_warp(empty_f);
           ++jf;
           tmem_wait_st();
           fence_before();
-          mbar_arrive(full_a2);
+          mbar_arrive_warp(full_a2);
           ++ia2;
         }
-        const int zb = jz & 1, slot = ja3 & 1;
+        if (t == 0) continue;
+        const int zb = jz & 1, slot = ja3 % kA3;
         if (!__all_sync(0xffffffffu, mbar_wait(&full_z[zb], (uint32_t)(jz >> 1) & 1u, abort_flag, prm.status)) ||
-            (ja3 >= 2 && !__all_sync(0xffffffffu, mbar_wait(&empty_a3[slot], ((uint32_t)(ja3 >> 1) & 1u) ^ 1u,
-                                                            abort_flag, prm.status)))) {
+            (ja3 >= kA3 && !__all_sync(0xffffffffu, mbar_wait(&empty_a3[slot], ((uint32_t)(ja3 / kA3) & 1u) ^ 1u,
+                                                              abort_flag, prm.status)))) {
           ok = false;
           break;
         }
         fence_after();
         cut_row<K>(ztile + zb * (kTile / 4), r, lane_base + c_a3(slot));
-        mbar_arrive(&empty_z[zb]);
+        mbar_arrive_warp(&empty_z[zb]);
         ++jz;
         tmem_wait_st();
         fence_before();
-        mbar_arrive(&full_a3[slot]);
+        mbar_arrive_warp(&full_a3[slot]);
         ++ja3;
       }
     }
@@ -354,18 +367,19 @@ __global__ void __launch_bounds__(kThreads, 1)
         if ((s2 && jz >= 2 &&
              !__all_sync(0xffffffffu, mbar_wait(&empty_z[zb], ((uint32_t)(jz >> 1) & 1u) ^ 1u, abort_flag,
                                                 prm.status))) ||
-            !__all_sync(0xffffffffu, mbar_wait(d_full, (uint32_t)jd & 1u, abort_flag, prm.status))) {
+            !__all_sync(0xffffffffu, mbar_wait(&d_full[jd & 1], (uint32_t)(jd >> 1) & 1u, abort_flag, prm.status))) {
           ok = false;
           continue;
         }
         fence_after();
+        const uint32_t dcol = lane_base + c_d(jd & 1);
         if (s2) {
           float* zt = ztile + zb * (kTile / 4);
 #pragma unroll 1
           for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t a0[16], a1[16];
-            tmem_ld16(lane_base + c_d + (uint32_t)c0, a0);
-            tmem_ld16(lane_base + c_d + (uint32_t)(BN + c0), a1);
+            tmem_ld16(dcol + (uint32_t)c0, a0);
+            tmem_ld16(dcol + (uint32_t)(BN + c0), a1);
             tmem_wait_ld();
             float* zc = zt + c0 * 32;
 #pragma unroll
@@ -375,18 +389,18 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int c0 = 0; c0 < BN; c0 += 16) {
             uint32_t a0[16], a1[16];
-            tmem_ld16(lane_base + c_d + (uint32_t)c0, a0);
-            tmem_ld16(lane_base + c_d + (uint32_t)(BN + c0), a1);
+            tmem_ld16(dcol + (uint32_t)c0, a0);
+            tmem_ld16(dcol + (uint32_t)(BN + c0), a1);
             tmem_wait_ld();
 #pragma unroll
             for (int i = 0; i < 16; ++i) acc[c0 + i] += __uint_as_float(a0[i]) + __uint_as_float(a1[i]);
           }
         }
         fence_before();
-        mbar_arrive(d_empty);
+        mbar_arrive_warp(&d_empty[jd & 1]);
         ++jd;
         if (s2) {
-          mbar_arrive(&full_z[zb]);
+          mbar_arrive_warp(&full_z[zb]);
           ++jz;
         }
       }

@@ -121,6 +121,7 @@ struct kpme_plan_s {
   bool ozf = false;                // stages 2 and 3 fused on the SM (K = 32, 64)
   bool allow_fused = true;         // tuning knob: may the fused kernel be used
   int tune_split = 2;              // tuning knob: split-K counts x tune_split / 2
+  bool no_sort = false;            // tuning knob: float64-atomic spreading, untiled gathering
   kpme::JobList stage23;           // fused jobs: term ranges, pairs (outer index, term)
   kpme::JobList stage1_res;        // A-resident stage-1 jobs: runs of outer factors, (0, i)
   CUtensorMap tmF_Q{}, tmF_Y{}, tmF_Z{};   // float32 A operands, 128 x 32 boxes
@@ -172,6 +173,7 @@ cudaError_t launch_spread_raw(const kpme_params_t& p, int sm_count, cudaStream_t
 int choose_tile(int K, int order);
 bool tile_ok(int K, int order, int T);
 kpme_status_t set_tile(kpme_plan_t P, int T);
+kpme_status_t set_sorted(kpme_plan_t P, bool sorted);
 kpme_status_t install_skp(kpme_plan_t P);
 constexpr int kTileCounters = 8;   // counters per tile of the cell sort (sub-ranges per tile)
 cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double* q, double* sumq);

@@ -31,6 +31,13 @@ static __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t by
 static __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
+// One arrival for a whole warp (the barrier then counts warps, not threads): the lanes' earlier
+// shared-memory and tensor-memory work is ordered before lane 0's arrive by __syncwarp.  This
+// cuts the serialized updates of a barrier word 32-fold.
+static __device__ __forceinline__ void mbar_arrive_warp(uint64_t* bar) {
+  __syncwarp();
+  if ((threadIdx.x & 31) == 0) mbar_arrive(bar);
+}
 // A waiting thread is suspended (not polling, so it takes no issue slots from the warps that
 // do the work) until the phase completes or this many nanoseconds pass; the caller's cycle
 // budget is checked between suspensions.
@@ -45,7 +52,18 @@ static __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t par
       : "memory");
   return ok != 0;
 }
+// Non-blocking: has the phase with this parity completed?
+static __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
 static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;   // already complete: no clock read on this path
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;

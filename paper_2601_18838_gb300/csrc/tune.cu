@@ -2,7 +2,8 @@
 //
 // The knobs are the ones whose best value depends on the workload rather than on the
 // mathematics (every setting gives the same result up to summation order):
-//   tile   - edge T of the cell-sort tiles of spreading and gathering (T^3 cells per CTA);
+//   tile   - edge T of the cell-sort tiles of spreading and gathering (T^3 cells per CTA),
+//            or -1: no cell sort (float64 atomics on the mesh, untiled gathering);
 //   fused  - stages 2 and 3 of the SKP fused on the SM (K = 32, 64) or run separately;
 //   split  - split-K multiplier of the term ranges (x split / 2 of the cost-model choice).
 // kpme_autotune times kpme_energy_forces (graph replay, CUDA events on the plan's stream,
@@ -24,6 +25,7 @@ struct Config {
 
 kpme_status_t apply_config(kpme_plan_t P, const Config& c) {
   kpme_status_t st;
+  if (P->tile > 0 && (c.tile > 0 || c.tile == -1) && (st = kpme::set_sorted(P, c.tile > 0)) != KPME_OK) return st;
   if (c.tile > 0 && P->tile > 0 && c.tile != P->tile && (st = kpme::set_tile(P, c.tile)) != KPME_OK) return st;
   const bool reinstall = (c.fused != 0) != P->allow_fused || c.split != P->tune_split;
   P->allow_fused = c.fused != 0;
@@ -105,6 +107,7 @@ extern "C" {
 kpme_status_t kpme_set_tune(kpme_plan_t P, const kpme_tune_t* t) {
   if (!P || !t) return KPME_ERR_INVALID_ARG;
   if (t->tile > 0 && P->tile > 0 && !kpme::tile_ok(P->p.K, P->p.order, t->tile)) return KPME_ERR_INVALID_ARG;
+  if (t->tile < -1 || (t->tile == -1 && P->tile <= 0)) return KPME_ERR_INVALID_ARG;
   if (t->split != 1 && t->split != 2 && t->split != 4) return KPME_ERR_INVALID_ARG;
   KPME_CUDA_TRY(P, cudaSetDevice(P->device));
   KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
@@ -119,12 +122,12 @@ kpme_status_t kpme_autotune(kpme_plan_t P, int64_t n, const double* x, const dou
   const bool prof = P->profiling;
   P->profiling = false;
   const std::string key = key_of(P, n);
-  Config best{P->tile, P->allow_fused ? 1 : 0, P->tune_split};
+  Config best{P->tile > 0 && P->no_sort ? -1 : P->tile, P->allow_fused ? 1 : 0, P->tune_split};
   double best_ms = 0.0;
   kpme_status_t st = KPME_OK;
   Config cached{};
   if (cache_path && cache_lookup(cache_path, key, cached, best_ms) &&
-      (cached.tile <= 0 || P->tile <= 0 || kpme::tile_ok(P->p.K, P->p.order, cached.tile))) {
+      (cached.tile == 0 || P->tile <= 0 || cached.tile == -1 || kpme::tile_ok(P->p.K, P->p.order, cached.tile))) {
     st = apply_config(P, cached);
     if (st == KPME_OK) *out = kpme_tune_t{cached.tile, cached.fused, cached.split, 1, best_ms};
     P->profiling = prof;
@@ -150,11 +153,12 @@ kpme_status_t kpme_autotune(kpme_plan_t P, int64_t n, const double* x, const dou
   };
   // knob 1: fused stages 2-3 where the kernel exists
   if (P->ozt_res && P->tc_bn == P->p.K && (P->p.K == 32 || P->p.K == 64)) trial(Config{best.tile, 1 - best.fused, best.split});
-  // knob 2: spreading tile edge (tiled path only)
+  // knob 2: spreading tile edge, or no cell sort (plans that can tile)
   if (P->tile > 0) {
     const int base = best.tile;
     for (int T : {4, 8, 16, 32})
       if (T != base && kpme::tile_ok(P->p.K, P->p.order, T)) trial(Config{T, best.fused, best.split});
+    if (base != -1) trial(Config{-1, best.fused, best.split});
   }
   // knob 3: split-K multiplier
   const int base_split = best.split;

@@ -30,16 +30,20 @@ def test_autotune_keeps_results_and_caches(torch, tmp_path, K, order, n, L):
     cache = str(tmp_path / "tune.txt")
     t = plan.autotune(x, q, cache=cache)
     assert t["from_cache"] == 0 and t["ms_per_eval"] > 0
-    assert t["split"] in (1, 2, 4) and t["fused"] in (0, 1) and t["tile"] in (4, 8, 16, 32)
+    assert t["split"] in (1, 2, 4) and t["fused"] in (0, 1) and t["tile"] in (-1, 4, 8, 16, 32)
     out = plan.energy_forces(x, q)
     assert rel(host(out["dEdq"]), ref["phi"]) < 1e-6 and rel(host(out["forces"]), ref["F"]) < 1e-5
     # every knob setting evaluates the same operator
-    for tile, fused, split in [(8, 1, 1), (16, 0, 4), (4, 1, 2)]:
-        if K % tile or (K not in (32, 64) and fused):
+    # (tile -1: no cell sort, float64-atomic spreading and untiled gathering)
+    for tile, fused, split in [(8, 1, 1), (16, 0, 4), (4, 1, 2), (-1, 1, 2), (-1, 0, 1)]:
+        if (tile > 0 and K % tile) or (K not in (32, 64) and fused):
             continue
         plan.set_tune(tile, fused, split)
-        o2 = plan.energy_forces(x, q)
+        o2 = plan.energy_forces(x, q, virial=True)
         assert rel(host(o2["dEdq"]), ref["phi"]) < 1e-6
+        assert rel(host(o2["forces"]), ref["F"]) < 1e-5
+        assert abs(host(o2["energy"])[0] - ref["E"]) < 1e-6 * abs(ref["E"])
+        assert abs(host(o2["virial"])[0] - ref["W"]) < 1e-5 * abs(ref["W"])
     # a second plan with the same problem key takes the cached choice without timing
     p2 = Plan(s.box, K, order, s.beta, precision="bf16x10", skp_tol=s.skp_tol, max_n=n)
     p2.set_skp(*skp.generators(o))
