@@ -190,7 +190,7 @@ def run_batched(args):
         offsets = np.cumsum([0] + [s.n for s in mine])
         x = torch.tensor(np.concatenate([s.x for s in mine]), device=dev)
         q = torch.tensor(np.concatenate([s.q for s in mine]), device=dev)
-        tuned = batch.autotune(x, q, offsets)   # per class of systems, before any timed step
+        tuned = batch.autotune(x, q, offsets, cache=args.tune_cache)   # per class, before any timed step
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         stream = torch.cuda.current_stream()
         for _ in range(args.warmup):
@@ -249,6 +249,9 @@ def main(argv=None):
     ap.add_argument("--precision", default="bf16x10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file: a matching entry is applied without timing, a new choice is "
+                         "appended (a profiling run then repeats the configuration of the plain run)")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
@@ -276,7 +279,7 @@ def main(argv=None):
     info = plan.info()
     x = torch.tensor(s.x, device=dev)
     q = torch.tensor(s.q, device=dev)
-    tune = plan.autotune(x, q)   # launch configuration picked by timing (before any timed step)
+    tune = plan.autotune(x, q, cache=args.tune_cache)   # launch configuration picked by timing (before any timed step)
     out = {"energy": torch.empty(1, dtype=torch.float64, device=dev),
            "forces": torch.empty((s.n, 3), dtype=torch.float64, device=dev),
            "dEdq": torch.empty(s.n, dtype=torch.float64, device=dev),
@@ -357,8 +360,11 @@ def main(argv=None):
         part[kname] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs,
                       "frac_hbm": (gbs / hbm) if gbs else None}
     part["hbm_peak_gbs"] = hbm
-    part["note"] = ("spread includes the cell sort (count, scan, scatter) and the mesh clear; "
-                    "the kernels are bound by shared-memory atomics and latency at these sizes")
+    part["note"] = ("no cell sort (autotuned): spread = mesh clear + lane-group spreading with float32 atomics "
+                    "into the L2-resident mesh, gather = one thread per particle; bound by atomics and latency"
+                    if tune.get("tile") == -1 else
+                    "spread includes the cell sort (count, scan, scatter) and the mesh clear; the kernels are "
+                    "bound by shared-memory atomics and latency at these sizes")
 
     # end to end through the public API with host buffers
     xh = torch.tensor(s.x).pin_memory()

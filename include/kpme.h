@@ -259,8 +259,9 @@ typedef struct {
 } kpme_tune_t;
 
 /* Time kpme_energy_forces for the n particles x, q (DEVICE, as in kpme_energy_forces) by
- * coordinate descent over the knobs (each candidate: 2 warm-up and 5 timed evaluations,
- * CUDA events on the plan's stream), leave the plan configured with the fastest and
+ * coordinate descent over the knobs (each candidate: 2 warm-up evaluations, a 3-evaluation
+ * probe, then 5 to 100 timed evaluations, about 20 ms of work; CUDA events on the plan's
+ * stream), leave the plan configured with the fastest and
  * report it in *out.  cache_path (may be NULL): a text file with one line per problem key
  * (K, order, precision, log2 n, SM count, compute capability); a matching entry is applied
  * without timing, a new result is appended.  Needs a built SKP (else KPME_ERR_NOT_BUILT).

@@ -642,20 +642,21 @@ kpme_status_t virial_finish(kpme_plan_t P, const double* energy, double* out) {
 
 bool tiled(kpme_plan_t P) { return !P->prec.fp64 && P->tile > 0 && !P->no_sort; }
 
-// Charge mesh of n particles: cell sort + tile-staged float32 spreading, or float64 atomics
-// for the FP64 form (and meshes the tiling does not divide).
+// Charge mesh of n particles: cell sort + tile-staged float32 spreading, float32 spreading
+// with no sort (lane groups, float32 atomics), or float64 atomics for the FP64 form.
 kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, MeshRef& out) {
   const int64_t k3 = K3(P);
   KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-  if (!tiled(P)) {
+  if (P->prec.fp64) {
     KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
     KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
     out = {P->d_Q, true};
-    if (!P->prec.fp64) {
-      // one float32 copy, made before the virial branch forks, read by both branches
-      KPME_CUDA_TRY(P, launch_convert(P->d_Q, true, P->d_Qf, false, k3, P->stream));
-      out = {P->d_Qf, false};
-    }
+    return KPME_OK;
+  }
+  if (!tiled(P)) {
+    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Qf, 0, (size_t)k3 * sizeof(float), P->stream));
+    KPME_CUDA_TRY(P, launch_spread_nosort(P, n, x, q, P->d_Qf));
+    out = {P->d_Qf, false};
     return KPME_OK;
   }
   KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Qf, 0, (size_t)k3 * sizeof(float), P->stream));
@@ -922,7 +923,6 @@ kpme_status_t kpme_spread(kpme_plan_t P, int64_t n, const double* x, const doubl
   const int64_t k3 = K3(P);
   MeshRef m;
   if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
-  if (!tiled(P)) m = {P->d_Q, true};   // the float64 mesh, not its float32 copy
   KPME_CUDA_TRY(P, launch_convert(m.p, m.dbl, Q, true, k3, P->stream));
   return KPME_OK;
 }
@@ -966,7 +966,7 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
   KPME_CUDA_TRY(P, cudaMemsetAsync(energy, 0, sizeof(double), P->stream));
   MeshRef m;
   {
-    StepScope sc(P, STEP_SPREAD, n > 0 ? (tiled(P) ? 4 : P->prec.fp64 ? 1 : 2) : 0);
+    StepScope sc(P, STEP_SPREAD, n > 0 ? (tiled(P) ? 4 : 1) : 0);
     if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
   }
   // the virial's mesh part only reads Q: outside profiling it runs on a forked branch,

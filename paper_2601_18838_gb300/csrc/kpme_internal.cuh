@@ -178,6 +178,7 @@ kpme_status_t install_skp(kpme_plan_t P);
 constexpr int kTileCounters = 8;   // counters per tile of the cell sort (sub-ranges per tile)
 cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double* q, double* sumq);
 cudaError_t launch_spread_tiled(kpme_plan_t P, int64_t n, const double* q, float* Q);
+cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q);
 cudaError_t launch_gather_tiled(kpme_plan_t P, int64_t n, const double* q, const float* Phi, double* phi, double* F,
                                 double* energy, bool correct);
 

@@ -243,9 +243,7 @@ cudaError_t gather_t(kpme_plan_t P, int64_t n, const double* x, const double* q,
 }  // namespace
 
 cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, double* Q) {
-  // The charge mesh is accumulated in float64 for every arithmetic: each mesh value is a sum
-  // of many contributions of both signs (neutral molecules), and float32 accumulation of it
-  // dominates the potential error of the float32-class paths.
+  // The FP64 form's charge mesh: float64 weights and float64 atomics.
   if (n <= 0) return cudaSuccess;
   return spread_t<double>(P, n, x, q, Q);
 }
@@ -691,6 +689,77 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
   }
 }
 
+// ---- spreading with no cell sort ----
+// A group of LG lanes per particle: lanes 0..2 take the float64 mesh coordinate of one axis
+// each and its double-float B-spline weights, shared with the group by shuffles; lane l then
+// adds the n^2 stencil values of column j2 = l, so at every (j0, j1) the lanes of a group
+// write n consecutive mesh points of one row (n^2 short coalesced segments per particle
+// instead of n^3 scattered words).  Products are rounded once to float32 and added by
+// float32 atomics: the arithmetic of the tile-staged kernel.  (Gathering with no sort is
+// gather_kernel<float>: one thread per particle measured faster than lane groups.)
+template <int N>
+__global__ void __launch_bounds__(kThreads) spread_nosort_kernel(MeshGeom G, int64_t n, const double* __restrict__ x,
+                                                                 const double* __restrict__ q, float* __restrict__ Q,
+                                                                 double* __restrict__ sumq) {
+  constexpr int LG = Lanes<N>::value;
+  constexpr int PB = kThreads / LG;   // particles per block and pass
+  const int K = G.K;
+  const int gl = threadIdx.x % LG;
+  const int base = (threadIdx.x & 31) - gl;
+  double qs = 0.0;
+  for (int64_t pb = blockIdx.x * (int64_t)PB; pb < n; pb += (int64_t)gridDim.x * PB) {
+    const int64_t i = pb + threadIdx.x / LG;
+    const bool active = i < n;
+    const unsigned mask = __ballot_sync(0xffffffffu, active);
+    if (!active) continue;
+    int myg = 0;
+    df mine[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) mine[j] = {0.0f, 0.0f};
+    if (gl < 3) {
+      double f;
+      mesh_coord(x[3 * i + gl], gl == 0 ? G.c0 : (gl == 1 ? G.c1 : G.c2), G.L, K, myg, f);
+      bspline_df<N>(df_from(f), mine);
+    }
+    int g[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) g[a] = __shfl_sync(mask, myg, base + a);
+    df w[3][N];
+    share_axes<N>(mine, w, base, mask);
+    if (gl >= N) continue;
+    const double qi = q[i];
+    if (gl == 0) qs += qi;
+    const df c2 = df_mul(df_from(qi), pick<N>(w[2], gl));
+    int k2 = g[2] - gl;
+    k2 += k2 < 0 ? K : 0;
+#pragma unroll
+    for (int j0 = 0; j0 < N; ++j0) {
+      int k0 = g[0] - j0;
+      k0 += k0 < 0 ? K : 0;
+      const df c02 = df_mul(c2, w[0][j0]);
+#pragma unroll
+      for (int j1 = 0; j1 < N; ++j1) {
+        int k1 = g[1] - j1;
+        k1 += k1 < 0 ? K : 0;
+        const df v = df_mul(c02, w[1][j1]);   // rounded once to float32 below
+        atomicAdd(Q + ((int64_t)k0 * K + k1) * K + k2, v.hi + v.lo);
+      }
+    }
+  }
+  if (sumq) {
+    const double sq = block_sum_to_thread0<double>(qs);
+    if (threadIdx.x == 0 && sq != 0.0) atomicAdd(sumq, sq);
+  }
+}
+
+int grid_groups(kpme_plan_t P, int64_t n, int lg) {
+  const int64_t pb = kThreads / lg;
+  int64_t want = (n + pb - 1) / pb;
+  const int64_t cap = (int64_t)P->sm_count * 8;
+  if (want > cap) want = cap;
+  return (int)(want < 1 ? 1 : want);
+}
+
 Tiling tiling_of(kpme_plan_t P) {
   Tiling t;
   t.K = P->p.K;
@@ -746,6 +815,19 @@ cudaError_t launch_spread_tiled(kpme_plan_t P, int64_t n, const double* q, float
     case 4: spread_tiled<4>(P, tl, nt, smem, q, Q); break;
     case 6: spread_tiled<6>(P, tl, nt, smem, q, Q); break;
     case 8: spread_tiled<8>(P, tl, nt, smem, q, Q); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q) {
+  if (n <= 0) return cudaSuccess;
+  const MeshGeom G = geom(P);
+  const int grid = grid_groups(P, n, P->p.order <= 4 ? 4 : 8);
+  switch (P->p.order) {
+    case 4: spread_nosort_kernel<4><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq); break;
+    case 6: spread_nosort_kernel<6><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq); break;
+    case 8: spread_nosort_kernel<8><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

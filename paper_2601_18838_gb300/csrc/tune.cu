@@ -11,6 +11,7 @@
 // text cache (one line per problem key) stores the choice for later plans.
 #include "kpme_internal.cuh"
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -54,17 +55,27 @@ kpme_status_t time_config(kpme_plan_t P, int64_t n, const double* x, const doubl
     cudaEventDestroy(e0);
     return KPME_ERR_CUDA;
   }
-  constexpr int kReps = 5;
-  cudaEventRecord(e0, P->stream);
-  st = KPME_OK;
-  for (int i = 0; i < kReps && st == KPME_OK; ++i) st = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, b.W);
-  cudaEventRecord(e1, P->stream);
-  float t = 0.0f;
-  if (st == KPME_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
-    st = KPME_ERR_CUDA;
+  // a probe of 3 evaluations sizes the timed run to ~20 ms of work (5 to 100 evaluations),
+  // so that short evaluations are not judged on a few microseconds of launch noise
+  auto run = [&](int reps, double* out) {
+    cudaEventRecord(e0, P->stream);
+    kpme_status_t r = KPME_OK;
+    for (int i = 0; i < reps && r == KPME_OK; ++i) r = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, b.W);
+    cudaEventRecord(e1, P->stream);
+    float t = 0.0f;
+    if (r == KPME_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+      r = KPME_ERR_CUDA;
+    *out = (double)t / reps;
+    return r;
+  };
+  double probe = 0.0;
+  st = run(3, &probe);
+  if (st == KPME_OK) {
+    const int reps = probe > 0.0 ? (int)std::min(100.0, std::max(5.0, std::ceil(20.0 / probe))) : 100;
+    st = run(reps, ms);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  *ms = (double)t / kReps;
   return st;
 }
 

@@ -56,10 +56,14 @@ def test_sinc_skp_build_matches_oracle(torch, prec):
     assert rel(host(out["dEdq"]), sv["phi"]) < 1e-6
 
 
-@pytest.mark.parametrize("prec,order,n", [("fp64", 4, 999), ("fp32", 4, 999), ("fp64", 6, 1001), ("fp32", 8, 257)])
-def test_spread(torch, prec, order, n):
+@pytest.mark.parametrize("prec,order,n,sort", [("fp64", 4, 999, True), ("fp32", 4, 999, True), ("fp64", 6, 1001, True),
+                                               ("fp32", 8, 257, True), ("fp32", 4, 999, False),
+                                               ("bf16x10", 6, 1001, False), ("fp32", 8, 257, False)])
+def test_spread(torch, prec, order, n, sort):
     s = wl.random_system(n, 17.0, 32, order, seed=n)
     plan = _plan(s, prec)
+    if not sort:
+        plan.set_tune(-1, 1, 2)   # no cell sort: lane-group spreading with float32 atomics
     Q = host(plan.spread(dev(torch, s.x), dev(torch, s.q)))
     ref = spme.spread(s.x, s.q, s.box, s.K, s.order)
     tol = 1e-13 if prec == "fp64" else 2e-6
@@ -113,14 +117,17 @@ def test_apply_with_oracle_factors(torch, prec):
     assert e < TOL[prec][0] * (10 if prec in ("fp32", "tf32x3", "bf16x6") else 1)
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32"])
-def test_gather(torch, prec):
-    s = wl.random_system(1531, 23.0, 48, 6, seed=3)
+@pytest.mark.parametrize("prec,order,sort", [("fp64", 6, True), ("fp32", 6, True), ("fp32", 6, False),
+                                             ("fp32", 4, False), ("bf16x10", 8, False)])
+def test_gather(torch, prec, order, sort):
+    s = wl.random_system(1531, 23.0, 48, order, seed=3)
     rng = np.random.default_rng(0)
     Phi = rng.standard_normal((48, 48, 48))
     plan = _plan(s, prec)
+    if not sort:
+        plan.set_tune(-1, 1, 2)   # no cell sort: one thread per particle, untiled mesh reads
     phi, F = plan.gather(dev(torch, s.x), dev(torch, s.q), dev(torch, Phi))
-    phi_r, F_r = spme.gather(s.x, s.q, s.box, 48, 6, Phi)
+    phi_r, F_r = spme.gather(s.x, s.q, s.box, 48, order, Phi)
     tol = 1e-13 if prec == "fp64" else 2e-6
     assert rel(host(phi), phi_r) < tol and rel(host(F), F_r) < tol
 
