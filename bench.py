@@ -190,7 +190,7 @@ def run_batched(args):
         offsets = np.cumsum([0] + [s.n for s in mine])
         x = torch.tensor(np.concatenate([s.x for s in mine]), device=dev)
         q = torch.tensor(np.concatenate([s.q for s in mine]), device=dev)
-        tuned = batch.autotune(x, q, offsets, cache=args.tune_cache)   # per class, before any timed step
+        tuned = 0 if args.no_autotune else batch.autotune(x, q, offsets, cache=args.tune_cache)   # per class
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
         stream = torch.cuda.current_stream()
         for _ in range(args.warmup):
@@ -249,6 +249,7 @@ def main(argv=None):
     ap.add_argument("--precision", default="bf16x10")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--fp64-steps", type=int, default=5)
+    ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch configuration")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file: a matching entry is applied without timing, a new choice is "
                          "appended (a profiling run then repeats the configuration of the plain run)")
@@ -279,7 +280,8 @@ def main(argv=None):
     info = plan.info()
     x = torch.tensor(s.x, device=dev)
     q = torch.tensor(s.q, device=dev)
-    tune = plan.autotune(x, q, cache=args.tune_cache)   # launch configuration picked by timing (before any timed step)
+    # launch configuration picked by timing (before any timed step)
+    tune = {"tile": None, "autotune": "off"} if args.no_autotune else plan.autotune(x, q, cache=args.tune_cache)
     out = {"energy": torch.empty(1, dtype=torch.float64, device=dev),
            "forces": torch.empty((s.n, 3), dtype=torch.float64, device=dev),
            "dEdq": torch.empty(s.n, dtype=torch.float64, device=dev),
@@ -426,7 +428,7 @@ def main(argv=None):
             "vs_baseline": None, "dtype": DTYPE.get(args.precision, args.precision), "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": args.precision,
                        "skp_rank": R, "skp_r0": info["r0"], "skp_rel_err": skp_err,
-                       "autotune": {k: tune[k] for k in ("tile", "fused", "split", "ms_per_eval")},
+                       "autotune": ({k: tune[k] for k in ("tile", "fused", "split", "ms_per_eval")} if not args.no_autotune else "off"),
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "tflops_useful": useful / (ms_step * 1e-3) / 1e12,

@@ -251,7 +251,8 @@ const char* kpme_batch_last_error(kpme_batch_t batch);
  *   fused    - 1: SKP stages 2 and 3 fused on the SM where the kernel exists (error-free
  *              split, K = 32 or 64), 0: separate stages;
  *   split    - split-K multiplier of the term ranges: 1 (half), 2 (the cost model's
- *              choice), 4 (double). */
+ *              choice), 4 (double); for the fused stages the number of CTAs of their
+ *              static schedule: half, one or two per SM. */
 typedef struct {
   int tile, fused, split;
   int from_cache;        /* 1: taken from the cache file, not timed                   */
@@ -274,8 +275,11 @@ kpme_status_t kpme_set_tune(kpme_plan_t plan, const kpme_tune_t* t);
 
 /* Autotune a batch: the first system of each class (K, order, precision, log2 n) is tuned
  * with kpme_autotune on its own particles (offsets, x, q as in kpme_batch_energy_forces);
- * the others of the class take its configuration.  n_tuned (may be NULL): number of
- * systems timed.  The batch's graph is captured again at the next evaluation. */
+ * the others of the class take its configuration.  The whole batch (graph replay, forces,
+ * dE/dq and virials) is then timed with the tuned configurations and with those it had
+ * before, and the faster set is kept (systems timed alone do not see the concurrency of
+ * the batch).  n_tuned (may be NULL): number of systems timed.  The batch's graph is
+ * captured again at the next evaluation. */
 kpme_status_t kpme_batch_autotune(kpme_batch_t batch, const int64_t* offsets, const double* x, const double* q,
                                   const char* cache_path, int* n_tuned);
 

@@ -63,6 +63,8 @@ kpme_status_t dalloc(kpme_plan_t P, void** p, size_t bytes) {
 void free_joblist(JobList& j) {
   dfree(j.d_start);
   dfree(j.d_pairs);
+  dfree(j.d_items);
+  dfree(j.d_cta);
   j = JobList();
 }
 
@@ -79,6 +81,14 @@ kpme_status_t upload_joblist(kpme_plan_t P, JobList& j) {
   if (!j.h_pairs.empty())
     KPME_CUDA_TRY(P, cudaMemcpyAsync(j.d_pairs, j.h_pairs.data(), j.h_pairs.size() * sizeof(int2),
                                      cudaMemcpyHostToDevice, P->stream));
+  if (!j.h_items.empty()) {
+    if ((st = dalloc(P, (void**)&j.d_items, j.h_items.size() * sizeof(int4))) != KPME_OK) return st;
+    if ((st = dalloc(P, (void**)&j.d_cta, j.h_cta.size() * sizeof(int))) != KPME_OK) return st;
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(j.d_items, j.h_items.data(), j.h_items.size() * sizeof(int4),
+                                     cudaMemcpyHostToDevice, P->stream));
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(j.d_cta, j.h_cta.data(), j.h_cta.size() * sizeof(int),
+                                     cudaMemcpyHostToDevice, P->stream));
+  }
   return KPME_OK;
 }
 
@@ -388,25 +398,29 @@ kpme_status_t install_skp(kpme_plan_t P) {
     if ((st = upload_joblist(P, P->stage1_res)) != KPME_OK) return st;
   }
   if (P->ozf) {
-    // fused stages 2 and 3: contiguous term ranges; makespan = rounds x (terms per range +
-    // 2 for the range's cuts of Y_i tiles and its atomic Phi update)
-    int splits = 1;
-    int64_t best = INT64_MAX;
-    for (int sp = 1; sp <= R; ++sp) {
-      const int64_t rounds = ((int64_t)m_tiles * sp + P->sm_count - 1) / P->sm_count;
-      const int64_t cost = rounds * ((R + sp - 1) / sp + 2);
-      if (cost < best) {
-        best = cost;
-        splits = sp;
-      }
-    }
-    splits = std::max(1, std::min(R, splits * P->tune_split / 2));
-    P->stage23.h_start.assign(1, 0);
+    // fused stages 2 and 3: a static schedule.  The m_tiles x R (tile, term) steps, tile-major,
+    // are cut into one contiguous range per CTA (equal step counts);
+    // a range that crosses a tile boundary becomes two items.  Within an item the terms run
+    // in order, so the consecutive terms of one outer index share a cut of Y_i.
     P->stage23.h_pairs.clear();
-    for (int k = 0; k < splits; ++k) {
-      const int a = (int)((int64_t)R * k / splits), b = (int)((int64_t)R * (k + 1) / splits);
-      for (int t = a; t < b; ++t) P->stage23.h_pairs.push_back(make_int2(S.outer_of[t], t));
-      P->stage23.h_start.push_back((int)P->stage23.h_pairs.size());
+    for (int t = 0; t < R; ++t) P->stage23.h_pairs.push_back(make_int2(S.outer_of[t], t));
+    P->stage23.h_start = {0, R};
+    // (the split knob scales the grid: x1/2, x1, x2 of the SM count; a batch of concurrent
+    // systems may prefer fewer, longer CTAs)
+    const int64_t steps = (int64_t)m_tiles * R;
+    const int grid = (int)std::min<int64_t>(std::max(1, P->sm_count * P->tune_split / 2), steps);
+    P->stage23.h_items.clear();
+    P->stage23.h_cta.assign(1, 0);
+    for (int c = 0; c < grid; ++c) {
+      int64_t a = steps * c / grid;
+      const int64_t b = steps * (c + 1) / grid;
+      while (a < b) {
+        const int tile = (int)(a / R), t0 = (int)(a % R);
+        const int t1 = (int)std::min<int64_t>(R, t0 + (b - a));
+        P->stage23.h_items.push_back(make_int4(tile, t0, t1, 0));
+        a += t1 - t0;
+      }
+      P->stage23.h_cta.push_back((int)P->stage23.h_items.size());
     }
     if ((st = upload_joblist(P, P->stage23)) != KPME_OK) return st;
   }

@@ -19,8 +19,12 @@
 // The tensor pipe alternates step 2 of term j + 1 and step 3 of term j; the transposed Z
 // tile is double-buffered, so cutting term j + 1's digits overlaps the MMAs of step 2 of
 // term j + 2.
+// Each CTA runs its own list of items (a tile and a range of terms) from a static schedule
+// that gives every CTA of the persistent grid the same number of (tile, term) steps.
 // All waits are bounded; a wait that runs out raises the device status word.
 #include "kpme_internal.cuh"
+
+#include <algorithm>
 #include "tc_common.cuh"
 
 namespace kpme {
@@ -38,9 +42,10 @@ constexpr int kThreads = 10 * 32;       // TMA, MMA, 4 converters, 4 epilogue wa
 struct OzfParams {
   int K, M, sb;
   float* phi;
-  const int* start;
   const int2* pairs;   // (outer index, term)
-  int n_jobs, n_pairs;
+  const int4* items;   // (m tile, first pair, end pair, 0)
+  const int* cta;      // CTA c runs items [cta[c], cta[c + 1])
+  int n_pairs, max_items;
   int* status;
 };
 
@@ -111,13 +116,13 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty_a3 + 2);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
   int2* s_pairs = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
-  int* s_start = reinterpret_cast<int*>(s_pairs + prm.n_pairs);
+  int4* s_items = reinterpret_cast<int4*>(s_pairs + ((prm.n_pairs + 1) & ~1));   // 16-byte aligned
+  const int i_first = prm.cta[blockIdx.x];
+  const int n_items = prm.cta[blockIdx.x + 1] - i_first;   // this CTA's items (<= max_items)
   for (int i = threadIdx.x; i < prm.n_pairs; i += blockDim.x) s_pairs[i] = prm.pairs[i];
-  for (int i = threadIdx.x; i <= prm.n_jobs; i += blockDim.x) s_start[i] = prm.start[i];
+  for (int i = threadIdx.x; i < n_items; i += blockDim.x) s_items[i] = prm.items[i_first + i];
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m_tiles = prm.M / kBM;
-  const int n_items = m_tiles * prm.n_jobs;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < prm.sb; ++s) {
@@ -184,9 +189,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       // ---------------- TMA: Y_i rows (at every change of outer index) and factor digits ----------------
       int ib = 0, jf = 0;
       bool ok = true;
-      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
-        const int job = w / m_tiles, m0 = (w % m_tiles) * kBM;
-        const int p0 = s_start[job], n = s_start[job + 1] - p0;
+      for (int w = 0; w < n_items && ok; ++w) {
+        const int4 itm = s_items[w];
+        const int m0 = itm.x * kBM, p0 = itm.y, n = itm.z - itm.y;
         for (int o = 0; o < 2 * n && ok; ++o) {
           bool s2;
           int j;
@@ -225,9 +230,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id = idesc_bf16(kBM, BN);
       int ib = 0, ia2 = 0, ja3 = 0, jd = 0;
       bool ok = true;
-      for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
-        const int job = w / m_tiles;
-        const int p0 = s_start[job], n = s_start[job + 1] - p0;
+      for (int w = 0; w < n_items && ok; ++w) {
+        const int4 itm = s_items[w];
+        const int p0 = itm.y, n = itm.z - itm.y;
         // bit j: term j starts a new outer index (read once per item, not between MMAs)
         uint64_t nmask = 0;
         if (n <= 64) {
@@ -295,9 +300,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
     int jf = 0, ia2 = 0, jz = 0, ja3 = 0;
     bool ok = true;
-    for (int w = blockIdx.x; w < n_items && ok; w += gridDim.x) {
-      const int job = w / m_tiles;
-      const int p0 = s_start[job], n = s_start[job + 1] - p0;
+    for (int w = 0; w < n_items && ok; ++w) {
+      const int4 itm = s_items[w];
+      const int p0 = itm.y, n = itm.z - itm.y;
       // digits in the order the tensor pipe consumes them: Y_i of term t (when its outer index
       // changes) before Z of term t - 1, since step 2 of term t precedes step 3 of term t - 1
       for (int t = 0; t <= n && ok; ++t) {
@@ -352,9 +357,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int c = 0; c < 8; ++c) zoff[c] = tile_off(sub * K + c, k1) - c * 32;
     int jd = 0, jz = 0;
     bool ok = true;
-    for (int w = blockIdx.x; w < n_items; w += gridDim.x) {
-      const int job = w / m_tiles, m0 = (w % m_tiles) * kBM;
-      const int n = s_start[job + 1] - s_start[job];
+    for (int w = 0; w < n_items; ++w) {
+      const int4 itm = s_items[w];
+      const int m0 = itm.x * kBM, n = itm.z - itm.y;
       float acc[BN];
 #pragma unroll
       for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
@@ -425,14 +430,13 @@ template <int K>
 cudaError_t launch_k(kpme_plan_t P, const OzfArgs& a, OzfParams prm) {
   const int bstage = kSlices * K * 128;
   prm.sb = (K == 64) ? 3 : 6;
-  const int smem = prm.sb * bstage + 3 * kTile + kBarBytes + prm.n_pairs * (int)sizeof(int2) +
-                   (prm.n_jobs + 1) * (int)sizeof(int) + 1024;
+  const int smem = prm.sb * bstage + 3 * kTile + kBarBytes + ((prm.n_pairs + 1) & ~1) * (int)sizeof(int2) +
+                   prm.max_items * (int)sizeof(int4) + 1024;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   auto kern = mp_ozf_kernel<K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
-  const int items = (prm.M / kBM) * prm.n_jobs;
-  dim3 grid(items < P->sm_count ? items : P->sm_count);
+  const dim3 grid((unsigned)a.jobs->h_cta.size() - 1);   // one CTA per range of the static schedule
   kern<<<grid, kThreads, smem, P->stream>>>(*a.tmY, *a.tmB2, *a.tmB1, prm);
   return cudaGetLastError();
 }
@@ -446,10 +450,14 @@ cudaError_t launch_mp_ozf(kpme_plan_t P, const OzfArgs& a) {
   prm.K = a.K;
   prm.M = a.K * a.K;
   prm.phi = a.phi;
-  prm.start = a.jobs->d_start;
+  if (a.jobs->h_cta.size() < 2 || !a.jobs->d_items || !a.jobs->d_cta) return cudaErrorInvalidValue;
   prm.pairs = a.jobs->d_pairs;
-  prm.n_jobs = a.jobs->n_jobs;
+  prm.items = a.jobs->d_items;
+  prm.cta = a.jobs->d_cta;
   prm.n_pairs = (int)a.jobs->h_pairs.size();
+  prm.max_items = 0;
+  for (size_t c = 0; c + 1 < a.jobs->h_cta.size(); ++c)
+    prm.max_items = std::max(prm.max_items, a.jobs->h_cta[c + 1] - a.jobs->h_cta[c]);
   prm.status = P->d_status;
   if (a.K == 64) return launch_k<64>(P, a, prm);
   if (a.K == 32) return launch_k<32>(P, a, prm);

@@ -34,6 +34,12 @@ struct JobList {
   std::vector<int> h_start;
   std::vector<int2> h_pairs;
   int max_pairs = 0;
+  // optional static schedule (fused stages): items (m tile, first pair, end pair, 0) and
+  // for every CTA c its items [cta[c], cta[c + 1])
+  std::vector<int4> h_items;
+  std::vector<int> h_cta;
+  int4* d_items = nullptr;
+  int* d_cta = nullptr;
 };
 
 // One group of consecutive Kronecker terms processed by stages 2 and 3 together.

@@ -5,7 +5,8 @@
 //   tile   - edge T of the cell-sort tiles of spreading and gathering (T^3 cells per CTA),
 //            or -1: no cell sort (float64 atomics on the mesh, untiled gathering);
 //   fused  - stages 2 and 3 of the SKP fused on the SM (K = 32, 64) or run separately;
-//   split  - split-K multiplier of the term ranges (x split / 2 of the cost-model choice).
+//   split  - split-K multiplier of the term ranges (x split / 2 of the cost-model choice);
+//            for the fused stages, the grid of the static schedule (x split / 2 of the SMs).
 // kpme_autotune times kpme_energy_forces (graph replay, CUDA events on the plan's stream,
 // after warm-ups) by coordinate descent over the knobs and keeps the fastest; an optional
 // text cache (one line per problem key) stores the choice for later plans.
