@@ -399,28 +399,52 @@ kpme_status_t install_skp(kpme_plan_t P) {
   }
   if (P->ozf) {
     // fused stages 2 and 3: a static schedule.  The m_tiles x R (tile, term) steps, tile-major,
-    // are cut into one contiguous range per CTA (equal step counts);
-    // a range that crosses a tile boundary becomes two items.  Within an item the terms run
-    // in order, so the consecutive terms of one outer index share a cut of Y_i.
+    // are cut into one contiguous range per CTA of equal cost: a step costs 1, plus 0.4 where
+    // its term starts a run of a new outer index (the cut of the Y_i digits stalls step 2 for
+    // about 0.4 of a term).  A range that crosses a tile boundary becomes two items.  Within
+    // an item the terms run in order, so the consecutive terms of one outer index share a
+    // cut of Y_i.  (The split knob scales the grid: x1/2, x1, x2 of the SM count; a batch of
+    // concurrent systems may prefer fewer, longer CTAs.)
     P->stage23.h_pairs.clear();
     for (int t = 0; t < R; ++t) P->stage23.h_pairs.push_back(make_int2(S.outer_of[t], t));
     P->stage23.h_start = {0, R};
-    // (the split knob scales the grid: x1/2, x1, x2 of the SM count; a batch of concurrent
-    // systems may prefer fewer, longer CTAs)
     const int64_t steps = (int64_t)m_tiles * R;
     const int grid = (int)std::min<int64_t>(std::max(1, P->sm_count * P->tune_split / 2), steps);
+    constexpr double kCutCost = 0.4;
+    std::vector<double> term_cost(R);
+    double tile_cost = 0.0;
+    for (int t = 0; t < R; ++t) {
+      term_cost[t] = 1.0 + ((t == 0 || S.outer_of[t] != S.outer_of[t - 1]) ? kCutCost : 0.0);
+      tile_cost += term_cost[t];
+    }
+    const double total = tile_cost * m_tiles;
     P->stage23.h_items.clear();
     P->stage23.h_cta.assign(1, 0);
+    int64_t pos = 0;   // next step (tile-major)
+    double done = 0.0;
     for (int c = 0; c < grid; ++c) {
-      int64_t a = steps * c / grid;
-      const int64_t b = steps * (c + 1) / grid;
-      while (a < b) {
+      const double target = total * (c + 1) / grid;
+      int64_t end = pos;
+      double acc = done;
+      // take steps while the cost stays at or below the target (the last CTA takes the rest)
+      while (end < steps && (c == grid - 1 || acc + term_cost[end % R] * 0.5 <= target)) {
+        acc += term_cost[end % R];
+        ++end;
+      }
+      if (end == pos && end < steps && steps - end > grid - 1 - c) {   // every CTA gets a step if it can
+        acc += term_cost[end % R];
+        ++end;
+      }
+      int64_t a = pos;
+      while (a < end) {
         const int tile = (int)(a / R), t0 = (int)(a % R);
-        const int t1 = (int)std::min<int64_t>(R, t0 + (b - a));
+        const int t1 = (int)std::min<int64_t>(R, t0 + (end - a));
         P->stage23.h_items.push_back(make_int4(tile, t0, t1, 0));
         a += t1 - t0;
       }
       P->stage23.h_cta.push_back((int)P->stage23.h_items.size());
+      pos = end;
+      done = acc;
     }
     if ((st = upload_joblist(P, P->stage23)) != KPME_OK) return st;
   }
@@ -555,7 +579,7 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       }
       KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
       StepScope sc(P, STEP_SKP2, 1);
-      OzfArgs a{&P->tmF_Y, &P->tm_f2, &P->tm_f1, (float*)Phi, K, &P->stage23};
+      OzfArgs a{(const float*)P->d_Y, &P->tm_f2, &P->tm_f1, (float*)Phi, K, &P->stage23};
       KPME_CUDA_TRY(P, launch_mp_ozf(P, a));
       return KPME_OK;
     }

@@ -7,20 +7,22 @@
 // Z_t never leaves the SM: the epilogue warps drain the first product's accumulators and
 // write Z_t transposed (rows (k3', k2'), k1 fastest) into a shared-memory tile; converter
 // warps cut each row into four fixed-point bf16 digits with the power of two above the row's
-// own maximum (a full row is one thread's 64 values) and store them into tensor memory as
-// the A operand of the second product.  Both products use the error-free split of
+// own maximum (a full row is one thread's 64 values) as the A operand of the second
+// product.  Both products use the error-free split of
 // gemm_oz.cu / gemm_ozt.cu (ten digit products, exact leading accumulator D0, cross terms
 // D1; Ozaki, Ogita, Oishi and Rump, Numer. Algorithms 59, 2012), drained per term.  The
 // Phi tile is summed over the item's terms in registers and added to the mesh atomically.
 //
-// Tensor memory (512 columns): two accumulators (2 BN each) taken by the steps in turn, so
-// the epilogue drains one while the tensor pipe fills the other, A of step 2 (Y_i digits,
-// 128) and the slots of A of step 3 (Z_t digits, 128 each: one for K = 64, two for K = 32).
-// The tensor pipe alternates step 2 of term j + 1 and step 3 of term j; the transposed Z
-// tile is double-buffered, so cutting term j + 1's digits overlaps the MMAs of step 2 of
-// term j + 2.
+// Operands: the Y_i digits (A of step 2) are cut by the converter warps from rows read in
+// one go from global memory into a 64 KB shared-memory tile in the MMA's swizzled K-major
+// layout; the Z_t digits (A of step 3) go to tensor memory, whose 512 columns hold two
+// accumulators (2 BN each, taken by the ops in turn, so the epilogue drains one while the
+// tensor pipe fills the other) and two Z_t digit slots (128 each).  The factor digits come
+// by TMA.  The tensor pipe alternates step 2 of term j + 1 and step 3 of term j; two MMA
+// threads issue the ops of one accumulator each, so one thread's waits overlap the other's
+// MMAs; the transposed Z tile is double-buffered.
 // Each CTA runs its own list of items (a tile and a range of terms) from a static schedule
-// that gives every CTA of the persistent grid the same number of (tile, term) steps.
+// that balances the CTAs' costs (terms and cuts of Y_i).
 // All waits are bounded; a wait that runs out raises the device status word.
 #include "kpme_internal.cuh"
 
@@ -36,11 +38,13 @@ constexpr int kBM = 128;
 constexpr int kFBox = kBM * 128;        // 128 rows x 32 floats, 128-byte swizzle: 16 KB
 constexpr int kTile = 2 * kFBox;        // 128 rows x 64 floats: 32 KB
 constexpr int kACols = kSlices * 32;    // tensor-memory columns of one 64-wide A row's digits
+constexpr int kA2Slice = kBM * 128;     // one digit plane of the Y_i tile in shared memory: 16 KB
 constexpr int kBarBytes = 512;
-constexpr int kThreads = 10 * 32;       // TMA, MMA, 4 converters, 4 epilogue warps
+constexpr int kThreads = 11 * 32;       // TMA, MMA, 4 converters, 4 epilogue warps, second MMA
 
 struct OzfParams {
   int K, M, sb;
+  const float* Y;      // stage-1 output: r0 planes of K^2 rows x K floats
   float* phi;
   const int2* pairs;   // (outer index, term)
   const int4* items;   // (m tile, first pair, end pair, 0)
@@ -84,28 +88,50 @@ __device__ __forceinline__ void cut_row(const float* tile, int row, uint32_t tad
   }
 }
 
+// Digits of one Y_i row (held in registers: its K floats are loaded from global memory in one
+// go, before the wait for the digit buffer) into the shared-memory A operand of step 2: four
+// planes of 128 rows x 128 bytes (64 bf16), 16-byte chunks XOR-swizzled by row % 8, the
+// K-major layout of the MMA's shared-memory descriptors (as TMA writes the factor tiles).
+template <int K>
+__device__ __forceinline__ void cut_row_smem(const float4 (&y)[K / 4], int r, uint8_t* a2s) {
+  float m = 0.0f;
+#pragma unroll
+  for (int j = 0; j < K / 4; ++j)
+    m = fmaxf(m, fmaxf(fmaxf(fabsf(y[j].x), fabsf(y[j].y)), fmaxf(fabsf(y[j].z), fabsf(y[j].w))));
+  int e = 0;
+  frexpf(m, &e);
+  uint8_t* rb = a2s + (r >> 3) * 1024 + (r & 7) * 128;
+#pragma unroll
+  for (int g = 0; g < K / 8; ++g) {
+    const float v[8] = {y[2 * g].x, y[2 * g].y, y[2 * g].z, y[2 * g].w,
+                        y[2 * g + 1].x, y[2 * g + 1].y, y[2 * g + 1].z, y[2 * g + 1].w};
+    uint4 o[kSlices];
+    slice8(v, e, o);
+#pragma unroll
+    for (int sl = 0; sl < kSlices; ++sl) *reinterpret_cast<uint4*>(rb + sl * kA2Slice + ((g ^ (r & 7)) << 4)) = o[sl];
+  }
+}
+
 template <int K>
 __global__ void __launch_bounds__(kThreads, 1)
-    mp_ozf_kernel(const __grid_constant__ CUtensorMap tmY, const __grid_constant__ CUtensorMap tmB2,
+    mp_ozf_kernel(const __grid_constant__ CUtensorMap tmB2,
                   const __grid_constant__ CUtensorMap tmB1, OzfParams prm) {
   constexpr int BN = K;                 // both products have N = K
   constexpr int kBSlice = BN * 128;
   constexpr int kKSteps = K / 16;
   constexpr int kSub = kBM / K;         // k3' values per tile
-  constexpr int kA3 = (512 - 4 * BN - kACols) / kACols;   // Z_t digit slots after 2 accumulators
-  static_assert(kA3 >= 1 && 4 * BN + (1 + kA3) * kACols <= 512, "tensor memory layout");
+  constexpr int kA3 = (512 - 4 * BN) / kACols >= 2 ? 2 : 1;   // Z_t digit slots after 2 accumulators
+  static_assert(4 * BN + kA3 * kACols <= 512, "tensor memory layout");
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const int bstage = kSlices * kBSlice;
   uint8_t* ring_b = smem;
-  float* ftile = reinterpret_cast<float*>(ring_b + prm.sb * bstage);   // Y_i rows (TMA)
-  float* ztile = ftile + kTile / 4;                                      // Z_t transposed, 2 buffers
+  uint8_t* a2s = ring_b + prm.sb * bstage;                               // Y_i digits (A of step 2)
+  float* ztile = reinterpret_cast<float*>(a2s + kSlices * kA2Slice);    // Z_t transposed, 2 buffers
   uint64_t* bars = reinterpret_cast<uint64_t*>(ztile + 2 * (kTile / 4));
   uint64_t* full_b = bars;
   uint64_t* empty_b = full_b + prm.sb;
-  uint64_t* full_f = empty_b + prm.sb;
-  uint64_t* empty_f = full_f + 1;
-  uint64_t* full_a2 = empty_f + 1;
+  uint64_t* full_a2 = empty_b + prm.sb;
   uint64_t* empty_a2 = full_a2 + 1;
   uint64_t* d_full = empty_a2 + 1;     // [2] accumulators, taken by the ops in turn
   uint64_t* d_empty = d_full + 2;      // [2]
@@ -127,12 +153,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (threadIdx.x == 0) {
     for (int s = 0; s < prm.sb; ++s) {
       mbar_init(&full_b[s], 1);
-      mbar_init(&empty_b[s], 1);
+      mbar_init(&empty_b[s], 2);   // the op's owner (commit) and the other MMA thread
     }
-    mbar_init(full_f, 1);
-    mbar_init(empty_f, 4);
     mbar_init(full_a2, 4);
-    mbar_init(empty_a2, 1);
+    mbar_init(empty_a2, 2);   // one commit from each MMA thread
     for (int b = 0; b < 2; ++b) {
       mbar_init(&d_full[b], 1);
       mbar_init(&d_empty[b], 4);
@@ -143,7 +167,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(&full_a3[b], 4);
-      mbar_init(&empty_a3[b], 1);
+      mbar_init(&empty_a3[b], 2);  // the op's owner (commit) and the other MMA thread
     }
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -159,10 +183,9 @@ __global__ void __launch_bounds__(kThreads, 1)
   __syncthreads();
   fence_after();
   const uint32_t tmem = *taddr_slot;
-  // two accumulators (ops in turn), Y_i digits, kA3 slots of Z_t digits
+  // tensor memory: two accumulators (ops in turn), kA3 slots of Z_t digits
   auto c_d = [](int b) { return (uint32_t)(b * 2 * BN); };
-  const uint32_t c_a2 = 4 * BN;
-  auto c_a3 = [&](int slot) { return (uint32_t)(4 * BN + kACols + slot * kACols); };
+  auto c_a3 = [&](int slot) { return (uint32_t)(4 * BN + slot * kACols); };
 
   // step order of one item with n terms: S2(0), then S2(j), S3(j - 1) for j = 1..n-1, then
   // S3(n - 1); op o in [0, 2n): o = 0 -> S2(0), o = 2n - 1 -> S3(n - 1), else odd o -> S2((o+1)/2),
@@ -186,27 +209,17 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   if (warp == 0) {
     if (lane == 0) {
-      // ---------------- TMA: Y_i rows (at every change of outer index) and factor digits ----------------
-      int ib = 0, jf = 0;
+      // ---------------- TMA: factor digits, in op order ----------------
+      int ib = 0;
       bool ok = true;
       for (int w = 0; w < n_items && ok; ++w) {
         const int4 itm = s_items[w];
-        const int m0 = itm.x * kBM, p0 = itm.y, n = itm.z - itm.y;
+        const int p0 = itm.y, n = itm.z - itm.y;
         for (int o = 0; o < 2 * n && ok; ++o) {
           bool s2;
           int j;
           op_of(o, n, s2, j);
           const int2 pr = s_pairs[p0 + j];
-          if (s2 && new_outer(p0, j)) {
-            if (jf >= 1 && !mbar_wait(empty_f, ((uint32_t)jf & 1u) ^ 1u, abort_flag, prm.status)) {
-              ok = false;
-              break;
-            }
-            mbar_expect_tx(full_f, (uint32_t)((K / 32) * kFBox));
-            for (int h = 0; h < K / 32; ++h)
-              tma_load_3d(reinterpret_cast<uint8_t*>(ftile) + h * kFBox, &tmY, full_f, 32 * h, m0, pr.x);
-            ++jf;
-          }
           const int s = ib % prm.sb;
           if (ib >= prm.sb &&
               !mbar_wait(&empty_b[s], ((uint32_t)(ib / prm.sb) & 1u) ^ 1u, abort_flag, prm.status)) {
@@ -222,11 +235,20 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
       }
     }
-  } else if (warp == 1) {
+  } else if (warp == 1 || warp == 10) {
     if (lane == 0) {
-      // ---------------- MMA issue ----------------
-      // The Y_i digits are released right after the last step 2 that reads them, so the
+      // ---------------- MMA issue: two threads, one per accumulator ----------------
+      // An issuing thread is held while the tensor pipe's queue is full, i.e. until its op is
+      // nearly done, so one thread's waits for the next op would leave the pipe idle.  Thread
+      // `mine` issues the ops of accumulator `mine` (every other op) and does its waits while
+      // the other thread's op runs.  A parity wait is only unambiguous while the waiter is at
+      // most one phase behind, so both threads walk the whole op sequence and wait for every
+      // phase of the shared barriers (factor stages, Y_i and Z_t digits) in order, own op or
+      // not, and those resources are released to their producers only when both threads have
+      // passed them: the owner's commit (its MMAs done) plus the other thread's arrive.  The
+      // Y_i digits are released right after the last step 2 that reads them, so the
       // converters cut the next Y_i while step 3 of the previous term runs.
+      const int mine = warp == 1 ? 0 : 1;
       const uint32_t id = idesc_bf16(kBM, BN);
       int ib = 0, ia2 = 0, ja3 = 0, jd = 0;
       bool ok = true;
@@ -244,7 +266,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           bool s2;
           int j;
           op_of(o, n, s2, j);
-          const int slot = ja3 % kA3;
+          const int slot = ja3 % kA3, db = jd & 1, s = ib % prm.sb;
+          const bool own = db == mine;
+          // the op's operands, observed by both threads in sequence order
           if (s2) {
             if (newo(j)) {
               if (!mbar_wait(full_a2, (uint32_t)ia2 & 1u, abort_flag, prm.status)) {
@@ -257,36 +281,56 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const int db = jd & 1;
-          if (jd >= 2 && !mbar_wait(&d_empty[db], ((uint32_t)(jd >> 1) & 1u) ^ 1u, abort_flag, prm.status)) {
-            ok = false;
-            break;
-          }
-          const int s = ib % prm.sb;
           if (!mbar_wait(&full_b[s], (uint32_t)(ib / prm.sb) & 1u, abort_flag, prm.status)) {
             ok = false;
             break;
           }
+          const bool last_s2 = s2 && (j + 1 == n || newo(j + 1));
+          if (!own) {   // the other thread's op: release what this thread has passed
+            mbar_arrive(&empty_b[s]);
+            if (!s2) mbar_arrive(&empty_a3[slot]);
+            if (last_s2) mma_commit(empty_a2);   // this thread's earlier MMAs on the Y_i digits
+            if (!s2) ++ja3;
+            ++jd;
+            ++ib;
+            continue;
+          }
+          if (jd >= 2 && !mbar_wait(&d_empty[db], ((uint32_t)(jd >> 1) & 1u) ^ 1u, abort_flag, prm.status)) {
+            ok = false;
+            break;
+          }
           fence_after();
-          const uint32_t a = tmem + (s2 ? c_a2 : c_a3(slot));
           const uint32_t d = tmem + c_d(db);
           const uint64_t db0 = sdesc(smem_u32(ring_b + s * bstage));
+          if (s2) {   // A: Y_i digits in shared memory
+            const uint64_t da0 = sdesc(smem_u32(a2s));
 #pragma unroll
-          for (int kk = 0; kk < kKSteps; ++kk)
+            for (int kk = 0; kk < kKSteps; ++kk)
 #pragma unroll
-            for (int p = 0; p < kProducts; ++p) {
-              const uint32_t at = a + (uint32_t)(pa(p) * 32 + kk * 8);
-              const uint64_t dbp = db0 + (uint64_t)((pb(p) * kBSlice + kk * 32) >> 4);
-              const uint32_t acc = (kk == 0 && p <= 1) ? 0u : 1u;
-              mma_bf16_ta(p == 0 ? d : d + BN, at, dbp, id, acc);
-            }
+              for (int p = 0; p < kProducts; ++p) {
+                const uint64_t dap = da0 + (uint64_t)((pa(p) * kA2Slice + kk * 32) >> 4);
+                const uint64_t dbp = db0 + (uint64_t)((pb(p) * kBSlice + kk * 32) >> 4);
+                const uint32_t acc = (kk == 0 && p <= 1) ? 0u : 1u;
+                mma_bf16(p == 0 ? d : d + BN, dap, dbp, id, acc);
+              }
+          } else {    // A: Z_t digits in tensor memory
+            const uint32_t a = tmem + c_a3(slot);
+#pragma unroll
+            for (int kk = 0; kk < kKSteps; ++kk)
+#pragma unroll
+              for (int p = 0; p < kProducts; ++p) {
+                const uint32_t at = a + (uint32_t)(pa(p) * 32 + kk * 8);
+                const uint64_t dbp = db0 + (uint64_t)((pb(p) * kBSlice + kk * 32) >> 4);
+                const uint32_t acc = (kk == 0 && p <= 1) ? 0u : 1u;
+                mma_bf16_ta(p == 0 ? d : d + BN, at, dbp, id, acc);
+              }
+          }
           mma_commit(&empty_b[s]);
-          if (s2) {
-            if (j + 1 == n || newo(j + 1)) mma_commit(empty_a2);
-          } else {
+          if (!s2) {
             mma_commit(&empty_a3[slot]);
             ++ja3;
           }
+          if (last_s2) mma_commit(empty_a2);
           mma_commit(&d_full[db]);
           ++jd;
           ++ib;
@@ -294,31 +338,33 @@ __global__ void __launch_bounds__(kThreads, 1)
       }
     }
   } else if (warp < 6) {
-    // ---------------- converters: digits of Y_i rows and of Z_t rows into tensor memory ----------------
+    // ---------- converters: digits of Y_i rows (shared memory) and of Z_t rows (tensor memory) ----------
     const int qd = warp & 3;
     const int r = 32 * qd + lane;
     const uint32_t lane_base = tmem + ((uint32_t)(32 * qd) << 16);
-    int jf = 0, ia2 = 0, jz = 0, ja3 = 0;
+    const int64_t kk2 = (int64_t)K * K;
+    int ia2 = 0, jz = 0, ja3 = 0;
     bool ok = true;
     for (int w = 0; w < n_items && ok; ++w) {
       const int4 itm = s_items[w];
-      const int p0 = itm.y, n = itm.z - itm.y;
+      const int m0 = itm.x * kBM, p0 = itm.y, n = itm.z - itm.y;
       // digits in the order the tensor pipe consumes them: Y_i of term t (when its outer index
       // changes) before Z of term t - 1, since step 2 of term t precedes step 3 of term t - 1
       for (int t = 0; t <= n && ok; ++t) {
         if (t < n && new_outer(p0, t)) {
-          if (!__all_sync(0xffffffffu, mbar_wait(full_f, (uint32_t)jf & 1u, abort_flag, prm.status)) ||
-              (ia2 >= 1 &&
-               !__all_sync(0xffffffffu, mbar_wait(empty_a2, ((uint32_t)ia2 & 1u) ^ 1u, abort_flag, prm.status)))) {
+          // the row's loads are in flight while this warp waits for the digit buffer
+          const float4* y4 = reinterpret_cast<const float4*>(prm.Y + ((int64_t)s_pairs[p0 + t].x * kk2 + m0 + r) * K);
+          float4 y[K / 4];
+#pragma unroll
+          for (int q = 0; q < K / 4; ++q) y[q] = __ldg(y4 + q);
+          if (ia2 >= 1 &&
+              !__all_sync(0xffffffffu, mbar_wait(empty_a2, ((uint32_t)ia2 & 1u) ^ 1u, abort_flag, prm.status))) {
             ok = false;
             break;
           }
-          fence_after();
-          cut_row<K>(ftile, r, lane_base + c_a2);
-          mbar_arrive_warp(empty_f);
-          ++jf;
-          tmem_wait_st();
-          fence_before();
+          cut_row_smem<K>(y, r, a2s);
+          // generic-proxy writes, read by the tensor pipe (async proxy)
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_arrive_warp(full_a2);
           ++ia2;
         }
@@ -430,14 +476,16 @@ template <int K>
 cudaError_t launch_k(kpme_plan_t P, const OzfArgs& a, OzfParams prm) {
   const int bstage = kSlices * K * 128;
   prm.sb = (K == 64) ? 3 : 6;
-  const int smem = prm.sb * bstage + 3 * kTile + kBarBytes + ((prm.n_pairs + 1) & ~1) * (int)sizeof(int2) +
-                   prm.max_items * (int)sizeof(int4) + 1024;
+  const int fixed = kSlices * kA2Slice + 2 * kTile + kBarBytes + ((prm.n_pairs + 1) & ~1) * (int)sizeof(int2) +
+                    prm.max_items * (int)sizeof(int4) + 1024;
+  while (prm.sb > 2 && prm.sb * bstage + fixed > 227 * 1024) --prm.sb;   // long pair tables
+  const int smem = prm.sb * bstage + fixed;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   auto kern = mp_ozf_kernel<K>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)a.jobs->h_cta.size() - 1);   // one CTA per range of the static schedule
-  kern<<<grid, kThreads, smem, P->stream>>>(*a.tmY, *a.tmB2, *a.tmB1, prm);
+  kern<<<grid, kThreads, smem, P->stream>>>(*a.tmB2, *a.tmB1, prm);
   return cudaGetLastError();
 }
 
@@ -450,6 +498,7 @@ cudaError_t launch_mp_ozf(kpme_plan_t P, const OzfArgs& a) {
   prm.K = a.K;
   prm.M = a.K * a.K;
   prm.phi = a.phi;
+  prm.Y = a.Y;
   if (a.jobs->h_cta.size() < 2 || !a.jobs->d_items || !a.jobs->d_cta) return cudaErrorInvalidValue;
   prm.pairs = a.jobs->d_pairs;
   prm.items = a.jobs->d_items;

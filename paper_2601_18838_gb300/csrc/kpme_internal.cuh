@@ -247,7 +247,7 @@ struct OztArgs {
   const JobList* jobs;
 };
 struct OzfArgs {
-  const CUtensorMap* tmY;    // float32 Y (r0 planes x K^2 rows x K), 128 x 32 boxes
+  const float* Y;            // float32 Y (r0 planes x K^2 rows x K), device
   const CUtensorMap* tmB2;   // digits of the axis-1 factors B_t
   const CUtensorMap* tmB1;   // digits of the axis-0 factors A_t
   float* phi;
