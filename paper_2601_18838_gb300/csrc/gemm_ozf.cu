@@ -187,9 +187,11 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto c_d = [](int b) { return (uint32_t)(b * 2 * BN); };
   auto c_a3 = [&](int slot) { return (uint32_t)(4 * BN + slot * kACols); };
 
-  // step order of one item with n terms: S2(0), then S2(j), S3(j - 1) for j = 1..n-1, then
-  // S3(n - 1); op o in [0, 2n): o = 0 -> S2(0), o = 2n - 1 -> S3(n - 1), else odd o -> S2((o+1)/2),
-  // even o -> S3(o/2 - 1)
+  // The CTA's items form one stream of NT terms (items in order, each item's terms in order),
+  // and the ops run over the stream, across item boundaries: S2(0), then S2(u), S3(u - 1) for
+  // u = 1..NT-1, then S3(NT - 1); op o in [0, 2 NT): o = 0 -> S2(0), o = 2 NT - 1 -> S3(NT - 1),
+  // else odd o -> S2((o+1)/2), even o -> S3(o/2 - 1).  Step 2 of an item's first term thus
+  // runs while the previous item's last step 3 waits for its digits.
   auto op_of = [](int o, int n, bool& s2, int& j) {
     if (o == 0) {
       s2 = true;
@@ -206,20 +208,39 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
   };
   auto new_outer = [&](int p0, int j) { return j == 0 || s_pairs[p0 + j].x != s_pairs[p0 + j - 1].x; };
+  // a cursor (item w, term j of the item) walks the stream in order
+  struct Cur {
+    int w, j;
+  };
+  auto n_of = [&](int w) { return s_items[w].z - s_items[w].y; };
+  auto step = [&](Cur& c) {
+    if (++c.j == n_of(c.w)) {
+      ++c.w;
+      c.j = 0;
+    }
+  };
+  auto pidx = [&](const Cur& c) { return s_items[c.w].y + c.j; };
+  auto c_newo = [&](const Cur& c) { return new_outer(s_items[c.w].y, c.j); };
+  auto c_last_item = [&](const Cur& c) { return c.j + 1 == n_of(c.w); };
+  // the next term of the stream needs a new cut of Y_i (its outer index or its tile changes)
+  auto c_last_s2 = [&](const Cur& c) { return c_last_item(c) || new_outer(s_items[c.w].y, c.j + 1); };
+  int NT = 0;
+  for (int w = 0; w < n_items; ++w) NT += n_of(w);
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA: factor digits, in op order ----------------
       int ib = 0;
       bool ok = true;
-      for (int w = 0; w < n_items && ok; ++w) {
-        const int4 itm = s_items[w];
-        const int p0 = itm.y, n = itm.z - itm.y;
-        for (int o = 0; o < 2 * n && ok; ++o) {
+      Cur c2{0, 0}, c3{0, 0};
+      {
+        for (int o = 0; o < 2 * NT && ok; ++o) {
           bool s2;
-          int j;
-          op_of(o, n, s2, j);
-          const int2 pr = s_pairs[p0 + j];
+          int u;
+          op_of(o, NT, s2, u);
+          Cur& c = s2 ? c2 : c3;
+          const int2 pr = s_pairs[pidx(c)];
+          step(c);
           const int s = ib % prm.sb;
           if (ib >= prm.sb &&
               !mbar_wait(&empty_b[s], ((uint32_t)(ib / prm.sb) & 1u) ^ 1u, abort_flag, prm.status)) {
@@ -252,25 +273,34 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t id = idesc_bf16(kBM, BN);
       int ib = 0, ia2 = 0, ja3 = 0, jd = 0;
       bool ok = true;
-      for (int w = 0; w < n_items && ok; ++w) {
-        const int4 itm = s_items[w];
-        const int p0 = itm.y, n = itm.z - itm.y;
-        // bit j: term j starts a new outer index (read once per item, not between MMAs)
-        uint64_t nmask = 0;
-        if (n <= 64) {
-#pragma unroll 8
-          for (int j = 0; j < n; ++j) nmask |= (uint64_t)new_outer(p0, j) << j;
+      // per stream term u (first 64): bit u of nmask = a new cut of Y_i starts at u, of lmask =
+      // u is the last step 2 on its cut (read from shared memory once, not between MMAs)
+      uint64_t nmask = 0, lmask = 0;
+      if (NT <= 64) {
+        Cur c{0, 0};
+        for (int u = 0; u < NT; ++u) {
+          nmask |= (uint64_t)c_newo(c) << u;
+          lmask |= (uint64_t)c_last_s2(c) << u;
+          step(c);
         }
-        auto newo = [&](int j) { return n <= 64 ? ((nmask >> j) & 1u) != 0 : new_outer(p0, j); };
-        for (int o = 0; o < 2 * n && ok; ++o) {
+      }
+      Cur c2{0, 0};   // the next step 2's term (steps 3 need no term data here)
+      {
+        for (int o = 0; o < 2 * NT && ok; ++o) {
           bool s2;
-          int j;
-          op_of(o, n, s2, j);
+          int u;
+          op_of(o, NT, s2, u);
+          bool newo_u = false, last_s2 = false;
+          if (s2) {
+            newo_u = NT <= 64 ? ((nmask >> u) & 1u) != 0 : c_newo(c2);
+            last_s2 = NT <= 64 ? ((lmask >> u) & 1u) != 0 : c_last_s2(c2);
+            step(c2);
+          }
           const int slot = ja3 % kA3, db = jd & 1, s = ib % prm.sb;
           const bool own = db == mine;
           // the op's operands, observed by both threads in sequence order
           if (s2) {
-            if (newo(j)) {
+            if (newo_u) {
               if (!mbar_wait(full_a2, (uint32_t)ia2 & 1u, abort_flag, prm.status)) {
                 ok = false;
                 break;
@@ -285,7 +315,6 @@ __global__ void __launch_bounds__(kThreads, 1)
             ok = false;
             break;
           }
-          const bool last_s2 = s2 && (j + 1 == n || newo(j + 1));
           if (!own) {   // the other thread's op: release what this thread has passed
             mbar_arrive(&empty_b[s]);
             if (!s2) mbar_arrive(&empty_a3[slot]);
@@ -345,15 +374,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     const int64_t kk2 = (int64_t)K * K;
     int ia2 = 0, jz = 0, ja3 = 0;
     bool ok = true;
-    for (int w = 0; w < n_items && ok; ++w) {
-      const int4 itm = s_items[w];
-      const int m0 = itm.x * kBM, p0 = itm.y, n = itm.z - itm.y;
-      // digits in the order the tensor pipe consumes them: Y_i of term t (when its outer index
-      // changes) before Z of term t - 1, since step 2 of term t precedes step 3 of term t - 1
-      for (int t = 0; t <= n && ok; ++t) {
-        if (t < n && new_outer(p0, t)) {
+    Cur cy{0, 0};
+    {
+      // digits in the order the tensor pipe consumes them: Y_i of stream term t (when a new cut
+      // starts there) before Z of term t - 1, since step 2 of term t precedes step 3 of t - 1
+      for (int t = 0; t <= NT && ok; ++t) {
+        const bool cut_y = t < NT && c_newo(cy);
+        const int m0 = t < NT ? s_items[cy.w].x * kBM : 0;
+        const int outer = t < NT ? s_pairs[pidx(cy)].x : 0;
+        if (t < NT) step(cy);
+        if (cut_y) {
           // the row's loads are in flight while this warp waits for the digit buffer
-          const float4* y4 = reinterpret_cast<const float4*>(prm.Y + ((int64_t)s_pairs[p0 + t].x * kk2 + m0 + r) * K);
+          const float4* y4 = reinterpret_cast<const float4*>(prm.Y + ((int64_t)outer * kk2 + m0 + r) * K);
           float4 y[K / 4];
 #pragma unroll
           for (int q = 0; q < K / 4; ++q) y[q] = __ldg(y4 + q);
@@ -403,16 +435,15 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int c = 0; c < 8; ++c) zoff[c] = tile_off(sub * K + c, k1) - c * 32;
     int jd = 0, jz = 0;
     bool ok = true;
-    for (int w = 0; w < n_items; ++w) {
-      const int4 itm = s_items[w];
-      const int m0 = itm.x * kBM, n = itm.z - itm.y;
-      float acc[BN];
+    Cur c3{0, 0};   // the next step 3's term
+    float acc[BN];
 #pragma unroll
-      for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
-      for (int o = 0; o < 2 * n; ++o) {
+    for (int c = 0; c < BN; ++c) acc[c] = 0.0f;
+    {
+      for (int o = 0; o < 2 * NT; ++o) {
         bool s2;
-        int j;
-        op_of(o, n, s2, j);
+        int u;
+        op_of(o, NT, s2, u);
         if (!ok) continue;
         const int zb = jz & 1;
         if ((s2 && jz >= 2 &&
@@ -453,14 +484,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (s2) {
           mbar_arrive_warp(&full_z[zb]);
           ++jz;
+          continue;
+        }
+        // step 3: at the last term of an item its Phi tile is complete
+        const bool flush = c_last_item(c3);
+        const int m0 = s_items[c3.w].x * kBM;
+        step(c3);
+        if (!flush || *abort_flag) continue;
+        // Phi[k1'][k2'][k3'] for this thread's row rho = m: k3' = m0 / K + m / K, k2' = m % K
+        const int k3 = m0 / K + sub, k2 = k1;
+        float* out = prm.phi + (int64_t)k2 * K + k3;
+#pragma unroll
+        for (int c = 0; c < BN; ++c) {
+          atomicAdd(out + (int64_t)c * K * K, acc[c]);
+          acc[c] = 0.0f;
         }
       }
-      if (!ok || *abort_flag) continue;
-      // Phi[k1'][k2'][k3'] for this thread's row rho = m: k3' = m0 / K + m / K, k2' = m % K
-      const int k3 = m0 / K + sub, k2 = k1;
-      float* out = prm.phi + (int64_t)k2 * K + k3;
-#pragma unroll
-      for (int c = 0; c < BN; ++c) atomicAdd(out + (int64_t)c * K * K, acc[c]);
     }
   }
   fence_before();
