@@ -38,6 +38,35 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16":
          "bf16x6": "bf16", "bf16x10": "bf16"}
 
 
+# DRAM bytes (read + write) per launch of the SKP mode-product kernels, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, averaged over the launches of one evaluation),
+# with the digest of the kernel sources the counters were taken on: a changed kernel reports
+# null until it is captured again.
+SKP_TRAFFIC = {
+    # profiles/dram_traffic_water_k64_bf16x10.md: mp_ozt_kernel 1,515,008 B + mp_ozf_kernel
+    # 19,320,064 B (reads; 0 B written: Y and Phi stay in L2), 2 launches per evaluation
+    ("water", "bf16x10"): {"digest": "71ec9ddf3dd12bac", "bytes_per_launch": (1515008 + 19320064) / 2},
+}
+SKP_SOURCES = ("gemm_ozf.cu", "gemm_ozt.cu", "tc_common.cuh")
+
+
+def _skp_digest():
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2601_18838_gb300", "csrc")
+    for name in SKP_SOURCES:
+        with open(os.path.join(csrc, name), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _skp_traffic(workload, precision):
+    rec = SKP_TRAFFIC.get((workload, precision))
+    if not rec or rec["digest"] != _skp_digest():
+        return None
+    return rec["bytes_per_launch"]
+
+
 def _peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -343,9 +372,10 @@ def main(argv=None):
     kname = ("SKP mode products, error-free split on tcgen05 (mp_ozt_kernel stage 1, mp_ozf_kernel fused "
              "stages 2-3 for K = 32/64; mp_ozt/mp_oz_kernel otherwise)" if args.precision == "bf16x10"
              else "mp_tc_kernel (SKP mode products, tcgen05)")
+    traffic = _skp_traffic(args.workload, args.precision)
     roof = {"bound": "tensor", "kernel": kname,
             "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": None,
+            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
             "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 1/2 (tf32 nominal ratio)" if args.precision.startswith("tf32") else ""),
             "flops_per_step": mp_flops, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
             "ms_per_launch": per_launch_ms}
