@@ -65,6 +65,58 @@ def reciprocal_exact(x, q, box: float, beta: float, eps: float = 1e-18, center=N
     return dict(E=E, phi=phi, F=F)
 
 
+def reciprocal_energy_cell(x, q, h, beta: float, mmax: int) -> float:
+    """Exact reciprocal energy for a general (triclinic) periodic cell with cell vectors the
+    columns of h: E = 1/(2 pi V) sum_{m != 0, |m|_inf <= mmax} exp(-pi^2|k|^2/beta^2)/|k|^2 |S(k)|^2
+    with k = h^-T m, V = |det h| and S(k) = sum_j q_j exp(2 i pi k.x_j).  Used to pin the
+    virial tensor by finite differences of a strained cell (a cubic box is h = L I)."""
+    x = np.asarray(x, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    h = np.asarray(h, dtype=np.float64)
+    V = abs(float(np.linalg.det(h)))
+    r = np.arange(-mmax, mmax + 1, dtype=np.float64)
+    m = np.stack(np.meshgrid(r, r, r, indexing="ij"), axis=-1).reshape(-1, 3)
+    m = m[np.any(m != 0, axis=1)]
+    k = m @ np.linalg.inv(h)                      # rows: k = h^-T m
+    ksq = np.sum(k * k, axis=1)
+    S = np.exp(2j * np.pi * (k @ x.T)) @ q        # (n_modes,)
+    return float(np.sum(np.exp(-np.pi ** 2 * ksq / beta ** 2) / ksq * np.abs(S) ** 2)) / (2 * np.pi * V)
+
+
+def reciprocal_virial_exact(x, q, box: float, beta: float, eps: float = 1e-18, center=None) -> np.ndarray:
+    """Exact reciprocal virial tensor of a cubic box (modes truncated as in reciprocal_exact):
+    Pi_ab = sum_{m != 0} E(m) [delta_ab - 2 (1 + pi^2|k|^2/beta^2) k_a k_b/|k|^2] with
+    E(m) = exp(-pi^2|k|^2/beta^2)/|k|^2 |S(k)|^2 / (2 pi V)."""
+    x = np.asarray(x, dtype=np.float64)
+    q = np.asarray(q, dtype=np.float64)
+    c = np.full(3, 0.5 * box) if center is None else np.asarray(center, dtype=np.float64)
+    s = (x - c) / box + 0.5
+    mmax = _mode_cutoff(box, beta, eps)
+    r = np.arange(-mmax, mmax + 1, dtype=np.float64)
+    e = [np.exp(2j * np.pi * np.outer(s[:, a], r)) for a in range(3)]
+    k1 = r / box
+    V = box ** 3
+    Pi = np.zeros((3, 3))
+    E = 0.0
+    for i0 in range(r.size):
+        ka = [np.full((r.size, r.size), k1[i0]), np.broadcast_to(k1[:, None], (r.size, r.size)),
+              np.broadcast_to(k1[None, :], (r.size, r.size))]
+        ksq = ka[0] ** 2 + ka[1] ** 2 + ka[2] ** 2
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g = np.exp(-np.pi ** 2 * ksq / beta ** 2) / ksq
+            fac = 2.0 * (1.0 + np.pi ** 2 * ksq / beta ** 2) / ksq
+        if r[i0] == 0:
+            g[mmax, mmax] = 0.0
+            fac[mmax, mmax] = 0.0
+        S = ((q * e[0][:, i0])[:, None] * e[1]).T @ e[2]
+        Em = g * np.abs(S) ** 2 / (2 * np.pi * V)
+        E += float(np.sum(Em))
+        for a in range(3):
+            for b in range(3):
+                Pi[a, b] -= float(np.sum(Em * fac * ka[a] * ka[b]))
+    return Pi + E * np.eye(3)
+
+
 def real_space(x, q, box: float, beta: float, rcut: float) -> float:
     """E_real over all image pairs with |r| < rcut (the i = j, n = 0 term excluded)."""
     x = np.asarray(x, dtype=np.float64)

@@ -123,6 +123,31 @@ def virial_influence(K: int, n: int, box: float, beta: float) -> np.ndarray:
     return e[:, None, None] * e[None, :, None] * e[None, None, :] / (np.pi * box ** 3)
 
 
+def virial_tensor(Q, K: int, n: int, box: float, beta: float) -> np.ndarray:
+    """Full reciprocal virial tensor of SPME (not given in the paper; the standard analytic
+    derivative of the mesh energy, reading Z8):
+
+      Pi_ab = sum_{m != 0} E(m) [delta_ab - 2 (1 + pi^2 |k|^2/beta^2) k_a k_b / |k|^2],
+      E(m)  = 1/2 T(m) |S(m)|^2,  S = DFT of the charge mesh,  sum_m E(m) = E,
+
+    i.e. Pi_ab = -dE/d eps_ab under the affine strain x -> (1 + eps) x of positions and cell.
+    Its trace is virial_trace()."""
+    T = influence(K, n, box, beta)
+    Em = 0.5 * T * np.abs(np.fft.fftn(Q)) ** 2
+    k = wrapped_modes(K).astype(np.float64) / box
+    ka = [k[:, None, None], k[None, :, None], k[None, None, :]]
+    ksq = ka[0] ** 2 + ka[1] ** 2 + ka[2] ** 2
+    with np.errstate(divide="ignore", invalid="ignore"):
+        fac = 2.0 * (1.0 + np.pi ** 2 * ksq / beta ** 2) / ksq
+    fac[0, 0, 0] = 0.0
+    E = float(np.sum(Em))
+    Pi = np.empty((3, 3))
+    for a in range(3):
+        for c in range(3):
+            Pi[a, c] = (E if a == c else 0.0) - float(np.sum(Em * fac * ka[a] * ka[c]))
+    return Pi
+
+
 def pme(x, q, box: float, K: int, n: int, beta: float, center=None) -> dict:
     """Classical smooth PME reciprocal result (FFT route).
 
