@@ -435,6 +435,22 @@ def main(argv=None):
     e2e = {"value": ws * args.steps / (e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": s.n * 32,
            "d2h_bytes_per_step": s.n * 32 + 16}
 
+    # full virial tensor (mode space; an extra call, outside the timed step)
+    vt = None
+    if rank == 0:
+        for _ in range(3):
+            plan.virial_tensor(x, q)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            plan.virial_tensor(x, q)
+        b.record(stream)
+        b.synchronize()
+        Pi, _ = plan.virial_tensor(x, q)
+        vt = {"ms_per_call": a.elapsed_time(b) / 10, "trace": float(Pi.trace().item()),
+              "note": "kpme_virial_tensor: spread, three real-DFT mode products, float64 mode-space reduction"}
+
     # FP64 GPU form at the same SKP (the baseline the tensor path must beat)
     fp64 = None
     if args.fp64_steps > 0:
@@ -462,7 +478,7 @@ def main(argv=None):
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
             "tflops_useful": useful / (ms_step * 1e-3) / 1e12,
-            "roofline": roof, "particle_kernels": part, "e2e": e2e,
+            "roofline": roof, "particle_kernels": part, "virial_tensor": vt, "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
             "fp64_form": fp64, "clocks": clocks, "cpu_baseline": cb,
             "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},

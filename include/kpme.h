@@ -161,6 +161,21 @@ kpme_status_t kpme_get_skp(kpme_plan_t plan, int* r0_out, int* R_out, int* r1, d
                            double* gen2, double* gen1, double* sigma_outer,
                            double* sigma_inner, double* c_out);
 
+/* Full reciprocal virial tensor of smooth PME for the n charges x, q (DEVICE, as in
+ * kpme_energy_forces).  The paper gives no virial; the standard analytic strain derivative
+ * of the mesh energy is used:
+ *   Pi_ab = sum_{m != 0} E(m) [delta_ab - 2 (1 + pi^2 |k|^2/beta^2) k_a k_b / |k|^2],
+ *   E(m) = 1/2 coulomb_k T(m) |S(m)|^2,  T(m) = B(m) exp(-pi^2 |k|^2/beta^2) / (pi V |k|^2),
+ * k = m / L, S the discrete Fourier transform of the charge mesh, so Pi_ab = -dE/d eps_ab
+ * under the affine strain x -> (1 + eps) x of positions and box.  It is evaluated in mode
+ * space (three real-DFT mode products of the mesh and one float64 reduction), with the exact
+ * mesh kernel T rather than its SKP, so its trace equals the scalar virial of
+ * kpme_energy_forces up to the SKP approximation.  tensor: DEVICE, 9 doubles, row-major,
+ * symmetric (overwritten).  energy (DEVICE, 1 double, may be NULL): sum_m E(m), the mesh
+ * energy.  The plan's arithmetic (FP64 form or float32) is used for the mode products. */
+kpme_status_t kpme_virial_tensor(kpme_plan_t plan, int64_t n, const double* x, const double* q, double* tensor,
+                                 double* energy);
+
 /* Reciprocal potentials at the targets X from the charges on the sources Y
  * (Algorithm 4: spread, SKP products, gather, correction).  y: n_y x 3,
  * q: n_y, x: n_x x 3, p: n_x (output, overwritten).  n_y, n_x <= max_n. */

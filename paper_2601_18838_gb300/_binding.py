@@ -19,7 +19,7 @@ STEP_NAMES = ["spread", "split", "skp_stage1", "skp_stage2", "skp_stage3", "gath
 
 EXPORTS = [
     "kpme_default_params", "kpme_plan", "kpme_destroy", "kpme_set_stream", "kpme_set_precision",
-    "kpme_build_skp", "kpme_set_skp", "kpme_get_skp", "kpme_potential", "kpme_energy_forces",
+    "kpme_build_skp", "kpme_set_skp", "kpme_get_skp", "kpme_potential", "kpme_virial_tensor", "kpme_energy_forces",
     "kpme_spread", "kpme_apply", "kpme_gather", "kpme_set_profiling", "kpme_get_profile",
     "kpme_get_info", "kpme_status_string", "kpme_last_error", "kpme_spread_noalloc",
     "kpme_batch_create", "kpme_batch_destroy", "kpme_batch_set_stream", "kpme_batch_build_skp",
@@ -86,6 +86,7 @@ def lib():
         "kpme_set_skp": (st, [_vp, C.c_int, _ip, _dp, _dp, _dp, C.c_double]),
         "kpme_get_skp": (st, [_vp, _ip, _ip, _ip, _dp, _dp, _dp, _dp, _dp, C.POINTER(C.c_double)]),
         "kpme_potential": (st, [_vp, _i64, _vp, _vp, _i64, _vp, _vp]),
+        "kpme_virial_tensor": (st, [_vp, _i64, _vp, _vp, _vp, _vp]),
         "kpme_energy_forces": (st, [_vp, _i64, _vp, _vp, _vp, _vp, _vp, _vp]),
         "kpme_spread": (st, [_vp, _i64, _vp, _vp, _vp]),
         "kpme_apply": (st, [_vp, _vp, _vp]),
@@ -278,6 +279,16 @@ class Plan:
         p = torch.empty(x.shape[0], dtype=torch.float64, device=x.device)
         self._call("kpme_potential", C.c_int64(y.shape[0]), _ptr(y), _ptr(q), C.c_int64(x.shape[0]), _ptr(x), _ptr(p))
         return p
+
+    def virial_tensor(self, x, q):
+        """kpme_virial_tensor: the full reciprocal virial tensor (3, 3) and the mesh energy."""
+        import torch
+        n = x.shape[0]
+        _check_dev(x, "x", torch.float64, (n, 3))
+        _check_dev(q, "q", torch.float64, (n,))
+        out = torch.empty(10, dtype=torch.float64, device=x.device)
+        self._call("kpme_virial_tensor", C.c_int64(n), _ptr(x), _ptr(q), _ptr(out), C.c_void_p(out.data_ptr() + 72))
+        return out[:9].reshape(3, 3), out[9]
 
     def spread(self, x, q):
         import torch

@@ -126,6 +126,9 @@ void release_mesh_buffers(kpme_plan_t P) {
   dfree(P->d_tmp1);
   dfree(P->d_tmp2);
   dfree(P->d_facv);
+  dfree(P->d_facW);
+  dfree(P->d_bmod);
+  dfree(P->d_vt);
 }
 
 void drop_graph(kpme_plan_t P) {
@@ -184,6 +187,17 @@ kpme_status_t alloc_meshes(kpme_plan_t P) {
   P->scratch_bytes -= P->p.K * sizeof(double);
   if (e != cudaSuccess) {
     P->last_error = std::string("virial operator: ") + cudaGetErrorString(e);
+    return KPME_ERR_CUDA;
+  }
+  // mode-space virial tensor: real DFT matrix, B-spline moduli, float64 sums
+  if ((st = dalloc(P, &P->d_facW, (size_t)P->p.K * P->p.K * mesh_elem(P))) != KPME_OK) return st;
+  if ((st = dalloc(P, (void**)&P->d_bmod, (size_t)(P->p.K / 2 + 1) * sizeof(double))) != KPME_OK) return st;
+  if ((st = dalloc(P, (void**)&P->d_vt, 8 * sizeof(double))) != KPME_OK) return st;
+  e = launch_dft_matrix(P, P->d_facW);
+  if (e == cudaSuccess) e = launch_bmod(P, P->d_bmod);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+  if (e != cudaSuccess) {
+    P->last_error = std::string("virial tensor operator: ") + cudaGetErrorString(e);
     return KPME_ERR_CUDA;
   }
   return KPME_OK;
@@ -1072,6 +1086,28 @@ kpme_status_t kpme_energy_forces(kpme_plan_t P, int64_t n, const double* x, cons
     memcpy(P->graph_key, key, sizeof(key));
   }
   KPME_CUDA_TRY(P, cudaGraphLaunch(P->graph_exec, P->stream));
+  return KPME_OK;
+}
+
+kpme_status_t kpme_virial_tensor(kpme_plan_t P, int64_t n, const double* x, const double* q, double* tensor,
+                                 double* energy) {
+  kpme_status_t st = common_checks(P, n);
+  if (st != KPME_OK) return st;
+  if (!tensor || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
+  MeshRef m;
+  if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
+  const bool dbl = P->prec.fp64;
+  const int K = P->p.K, M = K * K;
+  const void* in = m.p;
+  if (!dbl && m.dbl) {
+    KPME_CUDA_TRY(P, launch_convert(m.p, true, P->d_Qf, false, K3(P), P->stream));
+    in = P->d_Qf;
+  }
+  // Q^ = Q x1 W x2 W x3 W (the mode products rotate the axes back to [m1][m2][m3])
+  KPME_CUDA_TRY(P, launch_mp_simt(dbl, in, 0, P->d_facW, P->d_tmp1, 0, M, K, K, P->single, 0, P->stream));
+  KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp1, 0, P->d_facW, P->d_tmp2, 0, M, K, K, P->single, 0, P->stream));
+  KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp2, 0, P->d_facW, P->d_Psi, 0, M, K, K, P->single, 0, P->stream));
+  KPME_CUDA_TRY(P, launch_virial_tensor(P, P->d_Psi, P->d_vt, tensor, energy));
   return KPME_OK;
 }
 

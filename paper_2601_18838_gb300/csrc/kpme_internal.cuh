@@ -114,6 +114,9 @@ struct kpme_plan_s {
   void* d_fac2 = nullptr;
   void* d_fac1 = nullptr;
   void* d_facv = nullptr;          // virial circulant (float/double), K x K
+  void* d_facW = nullptr;          // real DFT matrix (cosine / sine rows), K x K, plan's mesh format
+  double* d_bmod = nullptr;        // B-spline moduli |b(m)|^2, m = 0..K/2
+  double* d_vt = nullptr;          // virial-tensor sums (E and six components)
   void* d_Qs = nullptr;            // tensor path: sliced Q
   void* d_Y = nullptr;             // stage-1 output (r0 tensors)
   void* d_Z = nullptr;             // stage-2 output (one term group)
@@ -194,6 +197,9 @@ kpme_status_t build_skp_sinc(kpme_plan_t P, SkpHost& out);
 cudaError_t launch_materialize(kpme_plan_t P, const double* d_gen, int count, void* dst, int fmt_slices,
                                int fmt_kind);
 cudaError_t launch_virial_generator(kpme_plan_t P, double* d_gen);
+cudaError_t launch_bmod(kpme_plan_t P, double* d_out);   // K/2 + 1 moduli
+cudaError_t launch_dft_matrix(kpme_plan_t P, void* W);
+cudaError_t launch_virial_tensor(kpme_plan_t P, const void* Qhat, double* acc, double* out9, double* energy);
 
 // gemm_simt.cu: out[job][n][m] (+)= sum_pairs sum_k fac[f][n][k] in[a][m][k]
 cudaError_t launch_mp_simt(bool dbl, const void* in, int64_t in_bs, const void* fac, void* out,

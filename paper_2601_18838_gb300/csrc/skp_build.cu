@@ -631,6 +631,12 @@ cudaError_t launch_materialize(kpme_plan_t P, const double* d_gen, int count, vo
   return cudaGetLastError();
 }
 
+cudaError_t launch_bmod(kpme_plan_t P, double* d_out) {
+  const int Kh = P->p.K / 2 + 1;
+  bmod_kernel<<<(Kh + 127) / 128, 128, 0, P->stream>>>(P->p.K, P->p.order, Kh, d_out);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_virial_generator(kpme_plan_t P, double* d_gen) {
   const int K = P->p.K, Kh = K / 2 + 1;
   double* bm = nullptr;

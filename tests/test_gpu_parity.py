@@ -221,3 +221,27 @@ def test_empty_and_errors(torch):
     big = dev(torch, np.zeros((65, 3)))
     with pytest.raises(KpmeError, match="capacity"):
         plan.energy_forces(big, dev(torch, np.zeros(65)))
+
+
+@pytest.mark.parametrize("prec,box", [("fp64", "small"), ("fp32", "small"), ("bf16x10", "small"),
+                                      ("bf16x10", "water")])
+def test_virial_tensor_matches_oracle(torch, prec, box):
+    # full reciprocal virial tensor (mode space, exact mesh kernel) against the oracle's FFT
+    # evaluation on the same mesh; its trace is the scalar virial of energy_forces up to the
+    # SKP approximation of the mesh kernel
+    s = wl.small() if box == "small" else wl.water()
+    x, q = dev(torch, s.x), dev(torch, s.q)
+    plan = _plan(s, prec)
+    Pi, E = plan.virial_tensor(x, q)
+    Q = spme.spread(s.x, s.q, s.box, s.K, s.order)
+    ref = spme.virial_tensor(Q, s.K, s.order, s.box, s.beta)
+    Eref = 0.5 * float(np.sum(spme.influence(s.K, s.order, s.box, s.beta) * np.abs(np.fft.fftn(Q)) ** 2))
+    Pi = host(Pi)
+    tol = 1e-12 if prec == "fp64" else 5e-6
+    e_pi = np.linalg.norm(Pi - ref) / np.linalg.norm(ref)
+    print(f"{prec} {box}: tensor {e_pi:.2e}")
+    assert e_pi < tol and abs(float(E) - Eref) < tol * abs(Eref)
+    np.testing.assert_array_equal(Pi, Pi.T)
+    plan.set_skp(*skp.generators(_oracle_skp(s)))
+    W = plan.energy_forces(x, q, virial=True)["virial"].item()
+    assert abs(np.trace(Pi) - W) < 1e-6 * abs(W)
