@@ -577,7 +577,8 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       // float32 charge mesh and its row maxima (rows of stage 1)
       StepScope sc(P, STEP_SPLIT, Q.dbl ? 2 : 1);
       if (Q.dbl) KPME_CUDA_TRY(P, launch_convert(Q.p, true, P->d_Qf, false, k3, P->stream));
-      KPME_CUDA_TRY(P, launch_rowmax_rows(P, P->d_Qf, k2, K, P->d_rmQ));
+      // (the same launch clears Phi, which the following stages accumulate into)
+      KPME_CUDA_TRY(P, launch_rowmax_rows(P, P->d_Qf, k2, K, P->d_rmQ, (float*)Phi, k3));
     } else {
       StepScope sc(P, STEP_SPLIT, 1);
       KPME_CUDA_TRY(P, launch_slice_rows(P, Q.p, Q.dbl, k2, 1, K, P->d_Qsl));
@@ -591,7 +592,6 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
                   &P->stage1_res};
         KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
       }
-      KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
       StepScope sc(P, STEP_SKP2, 1);
       OzfArgs a{(const float*)P->d_Y, &P->tm_f2, &P->tm_f1, (float*)Phi, K, &P->stage23};
       KPME_CUDA_TRY(P, launch_mp_ozf(P, a));
@@ -613,7 +613,7 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       StepScope sc(P, STEP_SPLIT, 1);
       KPME_CUDA_TRY(P, launch_slice_rows(P, P->d_Y, false, k2, S.r0, K, P->d_Ysl));
     }
-    KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));
+    if (!res) KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));   // else cleared above
     for (const auto& g : P->groups) {
       KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
       {
@@ -696,22 +696,25 @@ bool tiled(kpme_plan_t P) { return !P->prec.fp64 && P->tile > 0 && !P->no_sort; 
 
 // Charge mesh of n particles: cell sort + tile-staged float32 spreading, float32 spreading
 // with no sort (lane groups, float32 atomics), or float64 atomics for the FP64 form.
-kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, MeshRef& out) {
+// also_zero (may be NULL): a float64 accumulator of the caller cleared in the same launch.
+kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, MeshRef& out,
+                          double* also_zero = nullptr) {
   const int64_t k3 = K3(P);
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
   if (P->prec.fp64) {
+    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+    if (also_zero) KPME_CUDA_TRY(P, cudaMemsetAsync(also_zero, 0, sizeof(double), P->stream));
     KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
     KPME_CUDA_TRY(P, launch_spread(P, n, x, q, P->d_Q));
     out = {P->d_Q, true};
     return KPME_OK;
   }
+  // the float32 mesh, the charge sum and the caller's accumulator in one launch
+  KPME_CUDA_TRY(P, launch_clear(P, P->d_Qf, k3, P->d_sumq, also_zero));
   if (!tiled(P)) {
-    KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Qf, 0, (size_t)k3 * sizeof(float), P->stream));
     KPME_CUDA_TRY(P, launch_spread_nosort(P, n, x, q, P->d_Qf));
     out = {P->d_Qf, false};
     return KPME_OK;
   }
-  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Qf, 0, (size_t)k3 * sizeof(float), P->stream));
   KPME_CUDA_TRY(P, launch_sort(P, n, x, q, P->d_sumq));
   KPME_CUDA_TRY(P, launch_spread_tiled(P, n, q, P->d_Qf));
   out = {P->d_Qf, false};
@@ -1015,11 +1018,11 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
   P->launches = 0;
   const int64_t k3 = K3(P);
   (void)k3;
-  KPME_CUDA_TRY(P, cudaMemsetAsync(energy, 0, sizeof(double), P->stream));
   MeshRef m;
   {
-    StepScope sc(P, STEP_SPREAD, n > 0 ? (tiled(P) ? 4 : 1) : 0);
-    if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
+    const int spread_launches = P->prec.fp64 ? (n > 0 ? 1 : 0) : (n > 0 ? (tiled(P) ? 5 : 2) : 1);
+    StepScope sc(P, STEP_SPREAD, spread_launches);
+    if ((st = spread_mesh(P, n, x, q, m, energy)) != KPME_OK) return st;   // also clears energy
   }
   // the virial's mesh part only reads Q: outside profiling it runs on a forked branch,
   // concurrently with the SKP stages, and joins before the finalisation

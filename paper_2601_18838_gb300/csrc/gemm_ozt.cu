@@ -478,7 +478,13 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
 }
 
 // Row maxima of a float32 tensor of rows x K values (one warp per row): max |x| per row.
-__global__ void rowmax_rows_kernel(const float* __restrict__ in, int64_t rows, int K, float* __restrict__ out) {
+// Optionally zeroes nz floats of `zero` (the potential mesh the following stages accumulate
+// into), which saves a separate clearing node on the path.
+__global__ void rowmax_rows_kernel(const float* __restrict__ in, int64_t rows, int K, float* __restrict__ out,
+                                   float* __restrict__ zero, int64_t nz) {
+  if (zero)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nz; i += (int64_t)gridDim.x * blockDim.x)
+      zero[i] = 0.0f;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (w >= rows) return;
@@ -581,11 +587,12 @@ cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
   }
 }
 
-cudaError_t launch_rowmax_rows(kpme_plan_t P, const float* in, int64_t rows, int K, float* out) {
-  if (rows <= 0) return cudaSuccess;
+cudaError_t launch_rowmax_rows(kpme_plan_t P, const float* in, int64_t rows, int K, float* out, float* zero,
+                               int64_t nz) {
+  if (rows <= 0) return zero && nz > 0 ? cudaMemsetAsync(zero, 0, (size_t)nz * sizeof(float), P->stream) : cudaSuccess;
   const int threads = 256;
   const int64_t blocks = (rows * 32 + threads - 1) / threads;
-  rowmax_rows_kernel<<<(unsigned)blocks, threads, 0, P->stream>>>(in, rows, K, out);
+  rowmax_rows_kernel<<<(unsigned)blocks, threads, 0, P->stream>>>(in, rows, K, out, zero, nz);
   return cudaGetLastError();
 }
 

@@ -266,7 +266,9 @@ bool ozt_supported(int K, int bn, bool a_res);
 cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a);
 cudaError_t launch_mesh_correction(kpme_plan_t P, const double* Q, double* Phi, int64_t count, double c,
                                    double* scratch);
-cudaError_t launch_rowmax_rows(kpme_plan_t P, const float* in, int64_t rows, int K, float* out);
+cudaError_t launch_rowmax_rows(kpme_plan_t P, const float* in, int64_t rows, int K, float* out,
+                               float* zero = nullptr, int64_t nz = 0);
+cudaError_t launch_clear(kpme_plan_t P, float* a, int64_t n, double* s0, double* s1);
 cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a);
 cudaError_t launch_slice_rows(kpme_plan_t P, const void* in, bool in_double, int64_t rows_per_batch, int nbatch,
                               int K, void* out);

@@ -820,6 +820,32 @@ cudaError_t launch_spread_tiled(kpme_plan_t P, int64_t n, const double* q, float
   return cudaGetLastError();
 }
 
+// One launch clears a float32 mesh and up to two float64 accumulators (instead of three
+// memset nodes on the evaluation's path).
+__global__ void clear_kernel(float4* __restrict__ a4, int64_t n4, float* __restrict__ tail, int ntail,
+                             double* __restrict__ s0, double* __restrict__ s1) {
+  const int64_t i0 = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  for (int64_t i = i0; i < n4; i += (int64_t)gridDim.x * blockDim.x) a4[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (i0 < ntail) tail[i0] = 0.0f;
+  if (i0 == 0) {
+    if (s0) *s0 = 0.0;
+    if (s1) *s1 = 0.0;
+  }
+}
+
+cudaError_t launch_clear(kpme_plan_t P, float* a, int64_t n, double* s0, double* s1) {
+  const int64_t n4 = (reinterpret_cast<uintptr_t>(a) % 16 == 0) ? n / 4 : 0;
+  const int ntail = (int)(n - 4 * n4);
+  if (ntail > 4096) return cudaErrorInvalidValue;
+  int64_t blocks = (n4 + kThreads - 1) / kThreads;
+  if (blocks > (int64_t)P->sm_count * 8) blocks = (int64_t)P->sm_count * 8;
+  if (blocks < 1) blocks = 1;
+  if (blocks * kThreads < ntail) blocks = (ntail + kThreads - 1) / kThreads;
+  clear_kernel<<<(unsigned)blocks, kThreads, 0, P->stream>>>(reinterpret_cast<float4*>(a), n4, a + 4 * n4, ntail, s0,
+                                                              s1);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q) {
   if (n <= 0) return cudaSuccess;
   const MeshGeom G = geom(P);
