@@ -26,15 +26,17 @@ def _mode_cutoff(box: float, beta: float, eps: float) -> int:
     return int(math.ceil(beta * box * math.sqrt(-math.log(eps)) / math.pi))
 
 
-def reciprocal_exact(x, q, box: float, beta: float, eps: float = 1e-18, center=None) -> dict:
-    """Exact (mode-truncated at exp(-pi^2|k|^2/beta^2) < eps) reciprocal Ewald sum.
+def reciprocal_exact(x, q, box: float, beta: float, eps: float = 1e-18, center=None, mmax: int | None = None) -> dict:
+    """Exact (mode-truncated at exp(-pi^2|k|^2/beta^2) < eps, or on the cube |m|_inf <= mmax
+    when given) reciprocal Ewald sum.
 
     Returns E, potentials phi_i = dE/dq_i and forces F_i = -dE/dx_i."""
     x = np.asarray(x, dtype=np.float64)
     q = np.asarray(q, dtype=np.float64)
     c = np.full(3, 0.5 * box) if center is None else np.asarray(center, dtype=np.float64)
     s = (x - c) / box + 0.5
-    mmax = _mode_cutoff(box, beta, eps)
+    if mmax is None:
+        mmax = _mode_cutoff(box, beta, eps)
     m = np.arange(-mmax, mmax + 1, dtype=np.float64)
     e = [np.exp(2j * np.pi * np.outer(s[:, a], m)) for a in range(3)]   # (N, M)
     k2 = (m / box) ** 2
