@@ -95,6 +95,16 @@ typedef enum {
   KPME_SKP_SINC = 1   /* sinc quadrature of 1/|m|^2, §2.1.2 (m = 0 correction c)     */
 } kpme_skp_method_t;
 
+/* Particle <-> node interpolation. */
+typedef enum {
+  KPME_INTERP_BSPLINE = 0,    /* cardinal B-splines of order `order` on one periodic K^3 mesh
+                                 (smooth PME; the path of the benchmarks)                    */
+  KPME_INTERP_LAGRANGE = 1    /* the paper's per-cell form (§2.2, §4.1, Algorithm 4):
+                                 K / order cells per axis, `order` equispaced Lagrange nodes
+                                 per cell and axis (K nodes per axis), modes |m|_inf <= modes,
+                                 quadrature SKP of alpha_M with dense axis factors           */
+} kpme_interp_t;
+
 typedef struct {
   double center[3];   /* c_B                                                          */
   double radius;      /* r_B > 0; the box side is 2 r_B                               */
@@ -106,10 +116,21 @@ typedef struct {
   int precision;      /* kpme_precision_t                                             */
   int64_t max_n;      /* largest particle count of any call (scratch capacity)        */
   double coulomb_k;   /* scale of potentials, energies and forces (1 = Gaussian)      */
+  int interp;         /* interpolation, a kpme_interp_t; 0 = B-spline                 */
+  int modes;          /* KPME_INTERP_LAGRANGE: largest mode M per axis (|m|_inf <= M) */
 } kpme_params_t;
 
 /* Fill *p with defaults (centre 0, radius 1, beta 0.35, order 4, K 32, tol 1e-8,
- * SVD, KPME_FP32, max_n 1<<20, coulomb_k 1).  Never fails for p != NULL. */
+ * SVD, KPME_FP32, max_n 1<<20, coulomb_k 1, B-spline interpolation).  Never fails for
+ * p != NULL.
+ *
+ * KPME_INTERP_LAGRANGE plans: order = Ln nodes per cell (4, 6, 8, 12 or 16), K = Kc Ln with
+ * Kc >= 1 cells per axis, 1 <= modes <= 64, skp_method = KPME_SKP_SINC (the quadrature SKP of
+ * Eq. quaddecompalpham over the mode cube, built by kpme_build_skp; kpme_set_skp / kpme_get_skp,
+ * the virial and kpme_virial_tensor are not available for them).  The potential is
+ * (1/(pi L)) sum_{0 != m, |m|_inf <= M} alpha(|m|) ... interpolated per cell (Thm. 3 bounds the
+ * interpolation error by (pi M r / Ln)^Ln (2 Ln)! / Ln!^2 with the cell radius r = 1/(2 Kc) in
+ * fractional coordinates). */
 kpme_status_t kpme_default_params(kpme_params_t* p);
 
 /* Create a plan on the current CUDA device.  stream: a cudaStream_t (NULL =

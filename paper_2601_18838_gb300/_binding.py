@@ -33,7 +33,11 @@ class Params(C.Structure):
         ("center", C.c_double * 3), ("radius", C.c_double), ("beta", C.c_double),
         ("order", C.c_int), ("K", C.c_int), ("skp_tol", C.c_double), ("skp_method", C.c_int),
         ("precision", C.c_int), ("max_n", C.c_int64), ("coulomb_k", C.c_double),
+        ("interp", C.c_int), ("modes", C.c_int),
     ]
+
+
+INTERP = {"bspline": 0, "lagrange": 1}
 
 
 class Tune(C.Structure):
@@ -146,7 +150,10 @@ class Plan:
 
     def __init__(self, box: float, K: int, order: int, beta: float = 0.35, center=None,
                  precision: str = "bf16x10", skp_tol: float = 1e-8, skp_method: str = "svd",
-                 max_n: int = 1 << 20, coulomb_k: float = 1.0, stream=None):
+                 max_n: int = 1 << 20, coulomb_k: float = 1.0, stream=None, interp: str = "bspline",
+                 modes: int = 0):
+        """interp="lagrange": the per-cell form (K / order cells per axis, `order` Lagrange nodes
+        per cell, modes |m|_inf <= `modes`); it needs skp_method="sinc"."""
         import torch
         L = lib()
         p = Params()
@@ -162,7 +169,10 @@ class Plan:
         p.precision = PRECISIONS[precision]
         p.max_n = max_n
         p.coulomb_k = coulomb_k
+        p.interp = INTERP[interp]
+        p.modes = modes
         self.params = p
+        self.interp, self.modes = interp, modes
         self.box, self.K, self.order, self.beta = box, K, order, beta
         self.precision = precision
         self._stream = stream
@@ -249,6 +259,10 @@ class Plan:
 
     def skp_c(self) -> float:
         """The m = 0 correction constant c of the installed SKP (0 for the SVD form)."""
+        if getattr(self, "interp", "bspline") == "lagrange":   # dense factors: sizes and c only
+            r0, R, c = C.c_int(), C.c_int(), C.c_double()
+            self._call("kpme_get_skp", C.byref(r0), C.byref(R), None, None, None, None, None, None, C.byref(c))
+            return float(c.value)
         return float(self.get_skp()["c"])
 
     def set_precision(self, precision: str):

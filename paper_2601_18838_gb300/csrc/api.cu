@@ -171,6 +171,7 @@ kpme_status_t alloc_meshes(kpme_plan_t P) {
   if ((st = dalloc(P, &P->d_Psi, b)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_tmp1, b)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_tmp2, b)) != KPME_OK) return st;
+  if (kpme::lagrange(P)) return KPME_OK;   // the virial operators are B-spline mesh operators
   // rank-one virial operator (CUDA-core format of the plan's mesh)
   double* dg = nullptr;
   if ((st = dalloc(P, (void**)&dg, P->p.K * sizeof(double))) != KPME_OK) return st;
@@ -302,6 +303,22 @@ kpme_status_t install_skp(kpme_plan_t P) {
     double* dg = nullptr;
     KPME_CUDA_TRY(P, cudaMalloc((void**)&dg, gen.size() * sizeof(double)));
     cudaError_t e = cudaMemcpyAsync(dg, gen.data(), gen.size() * sizeof(double), cudaMemcpyHostToDevice, P->stream);
+    double* dmax = nullptr;
+    if (S.dense) {   // dense factor matrices: one power of two per factor from its largest entry
+      std::vector<double> gmax(count, 0.0);
+      const size_t KK = (size_t)K * K;
+      for (int t = 0; t < count; ++t)
+        for (size_t i = 0; i < KK; ++i) gmax[t] = std::max(gmax[t], std::fabs(gen[(size_t)t * KK + i]));
+      if (e == cudaSuccess) e = cudaMalloc((void**)&dmax, count * sizeof(double));
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(dmax, gmax.data(), count * sizeof(double), cudaMemcpyHostToDevice, P->stream);
+      if (e == cudaSuccess) e = launch_materialize_dense(P, dg, dmax, count, *dst, slices, kind);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+      cudaFree(dmax);
+      cudaFree(dg);
+      KPME_CUDA_TRY(P, e);
+      return KPME_OK;
+    }
     if (e == cudaSuccess) e = launch_materialize(P, dg, count, *dst, slices, kind);
     if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
     cudaFree(dg);
@@ -692,7 +709,8 @@ kpme_status_t virial_finish(kpme_plan_t P, const double* energy, double* out) {
   return KPME_OK;
 }
 
-bool tiled(kpme_plan_t P) { return !P->prec.fp64 && P->tile > 0 && !P->no_sort; }
+bool tiled(kpme_plan_t P) { return !P->prec.fp64 && P->tile > 0 && !P->no_sort && !lagrange(P); }
+bool lagrange(kpme_plan_t P) { return P->p.interp == KPME_INTERP_LAGRANGE; }
 
 // Charge mesh of n particles: cell sort + tile-staged float32 spreading, float32 spreading
 // with no sort (lane groups, float32 atomics), or float64 atomics for the FP64 form.
@@ -700,6 +718,19 @@ bool tiled(kpme_plan_t P) { return !P->prec.fp64 && P->tile > 0 && !P->no_sort; 
 kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, MeshRef& out,
                           double* also_zero = nullptr) {
   const int64_t k3 = K3(P);
+  if (lagrange(P)) {   // node charges Q = S_Y q of the per-cell form
+    if (P->prec.fp64) {
+      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+      if (also_zero) KPME_CUDA_TRY(P, cudaMemsetAsync(also_zero, 0, sizeof(double), P->stream));
+      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
+    } else {
+      KPME_CUDA_TRY(P, launch_clear(P, P->d_Qf, k3, P->d_sumq, also_zero));
+    }
+    void* Qm = P->prec.fp64 ? (void*)P->d_Q : (void*)P->d_Qf;
+    KPME_CUDA_TRY(P, launch_lagrange_spread(P, n, x, q, Qm, P->prec.fp64));
+    out = {Qm, P->prec.fp64};
+    return KPME_OK;
+  }
   if (P->prec.fp64) {
     KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
     if (also_zero) KPME_CUDA_TRY(P, cudaMemsetAsync(also_zero, 0, sizeof(double), P->stream));
@@ -725,6 +756,11 @@ kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const doubl
 // the cell sort of these positions is already in place (same call).
 kpme_status_t gather_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, double* phi, double* F,
                           double* energy, bool correct, bool sorted) {
+  if (lagrange(P)) {   // S_X^* of the per-cell form
+    if (!correct) KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
+    KPME_CUDA_TRY(P, launch_lagrange_gather(P, n, x, q, P->d_Phi, P->prec.fp64, phi, F, energy, correct));
+    return KPME_OK;
+  }
   if (!tiled(P)) {
     if (!correct) KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
     KPME_CUDA_TRY(P, launch_gather(P, n, x, q, P->d_Phi, phi, F, energy, 1.0));
@@ -792,12 +828,16 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   if (!params || !out) return KPME_ERR_INVALID_ARG;
   *out = nullptr;
   const kpme_params_t& p = *params;
-  const bool ok = std::isfinite(p.radius) && p.radius > 0 && std::isfinite(p.beta) && p.beta > 0 &&
-                  (p.order == 4 || p.order == 6 || p.order == 8) && p.K % 2 == 0 && p.K >= 2 * p.order &&
-                  p.K <= 512 && std::isfinite(p.skp_tol) && p.skp_tol >= 0 &&
-                  (p.skp_method == KPME_SKP_SVD || p.skp_method == KPME_SKP_SINC) && valid_precision(p.precision) &&
-                  p.max_n >= 0 && std::isfinite(p.coulomb_k) && std::isfinite(p.center[0]) &&
-                  std::isfinite(p.center[1]) && std::isfinite(p.center[2]);
+  const bool lag = p.interp == KPME_INTERP_LAGRANGE;
+  const bool geometry =
+      lag ? ((p.order == 4 || p.order == 6 || p.order == 8 || p.order == 12 || p.order == 16) && p.K % p.order == 0 &&
+             p.K >= p.order && p.K <= 512 && p.modes >= 1 && p.modes <= 64 && p.skp_method == KPME_SKP_SINC)
+          : (p.interp == KPME_INTERP_BSPLINE && (p.order == 4 || p.order == 6 || p.order == 8) && p.K % 2 == 0 &&
+             p.K >= 2 * p.order && p.K <= 512 && (p.skp_method == KPME_SKP_SVD || p.skp_method == KPME_SKP_SINC));
+  const bool ok = geometry && std::isfinite(p.radius) && p.radius > 0 && std::isfinite(p.beta) && p.beta > 0 &&
+                  std::isfinite(p.skp_tol) && p.skp_tol >= 0 && valid_precision(p.precision) && p.max_n >= 0 &&
+                  std::isfinite(p.coulomb_k) && std::isfinite(p.center[0]) && std::isfinite(p.center[1]) &&
+                  std::isfinite(p.center[2]);
   if (!ok) return KPME_ERR_INVALID_ARG;
   kpme_plan_t P = new (std::nothrow) kpme_plan_s();
   if (!P) return KPME_ERR_OOM;
@@ -849,7 +889,7 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->d_qpsi = acc + 2;
   P->allow_fused = getenv_flag("KPME_FUSED", true);
   P->tile = 0;
-  if (choose_tile(p.K, p.order) > 0) {
+  if (!lag && choose_tile(p.K, p.order) > 0) {
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
     if ((st = set_tile(P, choose_tile(p.K, p.order))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);
@@ -921,7 +961,8 @@ kpme_status_t kpme_build_skp(kpme_plan_t P, int* rank_out, double* err_out) {
   if (!P) return KPME_ERR_INVALID_ARG;
   KPME_CUDA_TRY(P, cudaSetDevice(P->device));
   SkpHost S;
-  kpme_status_t st = P->p.skp_method == KPME_SKP_SVD ? build_skp_svd(P, S) : build_skp_sinc(P, S);
+  kpme_status_t st = lagrange(P) ? build_skp_lagrange(P, S)
+                     : P->p.skp_method == KPME_SKP_SVD ? build_skp_svd(P, S) : build_skp_sinc(P, S);
   if (st != KPME_OK) return st;
   P->skp = S;
   if ((st = install_skp(P)) != KPME_OK) return st;
@@ -933,6 +974,7 @@ kpme_status_t kpme_build_skp(kpme_plan_t P, int* rank_out, double* err_out) {
 kpme_status_t kpme_set_skp(kpme_plan_t P, int r0, const int* r1, const double* gen3, const double* gen2,
                            const double* gen1, double c) {
   if (!P || r0 <= 0 || !r1 || !gen3 || !gen2 || !gen1 || !std::isfinite(c)) return KPME_ERR_INVALID_ARG;
+  if (lagrange(P)) return KPME_ERR_UNSUPPORTED;   // its factors are dense, built by kpme_build_skp
   KPME_CUDA_TRY(P, cudaSetDevice(P->device));
   const int K = P->p.K;
   SkpHost S;
@@ -959,6 +1001,7 @@ kpme_status_t kpme_get_skp(kpme_plan_t P, int* r0_out, int* R_out, int* r1, doub
   if (!P) return KPME_ERR_INVALID_ARG;
   const SkpHost& S = P->skp;
   if (!S.valid) return KPME_ERR_NOT_BUILT;
+  if (S.dense && (gen3 || gen2 || gen1)) return KPME_ERR_UNSUPPORTED;   // dense factors: sizes and c only
   if (r0_out) *r0_out = S.r0;
   if (R_out) *R_out = S.R;
   if (r1) std::copy(S.r1.begin(), S.r1.end(), r1);
@@ -1015,6 +1058,7 @@ kpme_status_t kpme_gather(kpme_plan_t P, int64_t n, const double* x, const doubl
 kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x, const double* q, double* energy,
                                        double* forces, double* dEdq, double* vir) {
   kpme_status_t st;
+  if (vir && lagrange(P)) return KPME_ERR_UNSUPPORTED;   // the virial is a B-spline mesh operator here
   P->launches = 0;
   const int64_t k3 = K3(P);
   (void)k3;
@@ -1097,6 +1141,7 @@ kpme_status_t kpme_virial_tensor(kpme_plan_t P, int64_t n, const double* x, cons
   kpme_status_t st = common_checks(P, n);
   if (st != KPME_OK) return st;
   if (!tensor || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
+  if (lagrange(P)) return KPME_ERR_UNSUPPORTED;
   MeshRef m;
   if ((st = spread_mesh(P, n, x, q, m)) != KPME_OK) return st;
   const bool dbl = P->prec.fp64;

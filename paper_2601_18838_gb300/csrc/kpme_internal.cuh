@@ -55,7 +55,8 @@ struct SkpHost {
   int r0 = 0, R = 0;
   std::vector<int> r1;
   std::vector<int> outer_of;               // term -> outer index
-  std::vector<double> gen3, gen2, gen1;    // r0 x K, R x K, R x K
+  std::vector<double> gen3, gen2, gen1;    // r0 x K, R x K, R x K (dense: r0, R, R x K x K)
+  bool dense = false;                      // full factor matrices instead of circulant generators
   std::vector<double> sig_outer, sig_inner;
   double c = 0.0;
   double rel_err = 0.0;
@@ -194,6 +195,15 @@ cudaError_t launch_gather_tiled(kpme_plan_t P, int64_t n, const double* q, const
 // skp_build.cu
 kpme_status_t build_skp_svd(kpme_plan_t P, SkpHost& out);
 kpme_status_t build_skp_sinc(kpme_plan_t P, SkpHost& out);
+kpme_status_t build_skp_lagrange(kpme_plan_t P, SkpHost& out);
+kpme_status_t sinc_search(kpme_plan_t P, const std::vector<double>& args, double tol, int& nq, double& h,
+                          double& best);
+cudaError_t launch_materialize_dense(kpme_plan_t P, const double* d_dense, const double* d_gmax, int count, void* dst,
+                                     int slices, int kind);
+bool lagrange(kpme_plan_t P);   // per-cell Lagrange interpolation (KPME_INTERP_LAGRANGE)
+cudaError_t launch_lagrange_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, void* Q, bool dbl);
+cudaError_t launch_lagrange_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
+                                   bool dbl, double* phi, double* F, double* energy, bool correct);
 cudaError_t launch_materialize(kpme_plan_t P, const double* d_gen, int count, void* dst, int fmt_slices,
                                int fmt_kind);
 cudaError_t launch_virial_generator(kpme_plan_t P, double* d_gen);

@@ -59,6 +59,7 @@ extern "C" kpme_status_t kpme_spread_noalloc(const kpme_params_t* params, void* 
                                              const double* q, double* Q) {
   if (!params || !Q || n < 0 || (n > 0 && (!x || !q))) return KPME_ERR_INVALID_ARG;
   const kpme_params_t& p = *params;
+  if (p.interp != KPME_INTERP_BSPLINE) return KPME_ERR_UNSUPPORTED;   // B-spline spreading only
   const bool ok = std::isfinite(p.radius) && p.radius > 0 && (p.order == 4 || p.order == 6 || p.order == 8) &&
                   p.K % 2 == 0 && p.K >= 2 * p.order && std::isfinite(p.center[0]) && std::isfinite(p.center[1]) &&
                   std::isfinite(p.center[2]);

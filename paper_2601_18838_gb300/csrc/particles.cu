@@ -752,6 +752,175 @@ __global__ void __launch_bounds__(kThreads) spread_nosort_kernel(MeshGeom G, int
   }
 }
 
+// ---- per-cell Lagrange interpolation: S_Y and S_X^* of §2.2 and §4.1 ----
+// Kc^3 cells, Ln equispaced nodes per axis and cell (t_l = -1 + 2l/(Ln - 1) in the cell's local
+// coordinate t in [-1, 1], Eq. interp1d); node l of cell i of an axis has index i Ln + l (K = Kc Ln
+// nodes per axis, not periodic: the periodicity lives in the node operator).  One warp per
+// particle: lanes 0..2 take the float64 cell coordinate of one axis and its Ln weights (and
+// derivatives) from the product formula into the warp's shared-memory slot; the Ln^2 (l0, l1)
+// rows of the stencil are then spread over the lanes, each visiting its row's Ln consecutive nodes.
+
+// cell index and local coordinate of one axis (the float64 operations of the oracle, rounded alike)
+__device__ __forceinline__ void lagrange_cell(double x, double c, double L, int Kc, int& i, double& t) {
+  double s = __dadd_rn(__ddiv_rn(__dsub_rn(x, c), L), 0.5);
+  s = __dsub_rn(s, floor(s));
+  if (s >= 1.0) s = 0.0;
+  const double u = __dmul_rn((double)Kc, s);
+  int ii = (int)floor(u);
+  ii = ii > Kc - 1 ? Kc - 1 : (ii < 0 ? 0 : ii);
+  i = ii;
+  t = __dsub_rn(__dmul_rn(2.0, __dsub_rn(u, (double)ii)), 1.0);
+}
+
+// S_l(t) = prod_{k != l} (t - t_k)/(t_l - t_k) and, when dw != nullptr, dS_l/dt = sum_{k != l}
+// prod_{j != l, k} (t - t_j)/(t_l - t_j) / (t_l - t_k) through prefix and suffix products
+template <int LN>
+__device__ __forceinline__ void lagrange_weights(double t, double* w, double* dw) {
+#pragma unroll
+  for (int l = 0; l < LN; ++l) {
+    const double tl = -1.0 + 2.0 * l / (LN - 1);
+    double f[LN];
+    double S = 1.0;
+#pragma unroll
+    for (int j = 0; j < LN; ++j) {
+      const double tj = -1.0 + 2.0 * j / (LN - 1);
+      f[j] = (j == l) ? 1.0 : (t - tj) / (tl - tj);
+      S *= f[j];
+    }
+    w[l] = S;
+    if (dw) {
+      double pre[LN + 1];
+      pre[0] = 1.0;
+#pragma unroll
+      for (int j = 0; j < LN; ++j) pre[j + 1] = pre[j] * f[j];
+      double suf = 1.0, d = 0.0;
+#pragma unroll
+      for (int k = LN - 1; k >= 0; --k) {
+        if (k != l) d += pre[k] * suf / (tl - (-1.0 + 2.0 * k / (LN - 1)));
+        suf *= f[k];
+      }
+      dw[l] = d;
+    }
+  }
+}
+
+template <typename T, int LN>
+__global__ void __launch_bounds__(kThreads) lagrange_spread_kernel(MeshGeom G, int Kc, int64_t n,
+                                                                   const double* __restrict__ x,
+                                                                   const double* __restrict__ q, T* __restrict__ Q,
+                                                                   double* __restrict__ sumq) {
+  constexpr int W = kThreads / 32;
+  __shared__ double sw[W][3][LN];
+  __shared__ int sc[W][3];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int K = G.K;
+  double qs = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)W + wib; p < n; p += (int64_t)gridDim.x * W) {
+    if (lane < 3) {
+      int i;
+      double t, w[LN];
+      lagrange_cell(x[3 * p + lane], lane == 0 ? G.c0 : (lane == 1 ? G.c1 : G.c2), G.L, Kc, i, t);
+      lagrange_weights<LN>(t, w, nullptr);
+#pragma unroll
+      for (int l = 0; l < LN; ++l) sw[wib][lane][l] = w[l];
+      sc[wib][lane] = i * LN;
+    }
+    __syncwarp();
+    const double qi = q[p];
+    if (lane == 0) qs += qi;
+    const int b0 = sc[wib][0], b1 = sc[wib][1], b2 = sc[wib][2];
+    for (int r = lane; r < LN * LN; r += 32) {
+      const int l0 = r / LN, l1 = r % LN;
+      const double w01 = qi * sw[wib][0][l0] * sw[wib][1][l1];
+      T* row = Q + ((int64_t)(b0 + l0) * K + (b1 + l1)) * K + b2;
+#pragma unroll
+      for (int l2 = 0; l2 < LN; ++l2) atomicAdd(row + l2, (T)(w01 * sw[wib][2][l2]));
+    }
+    __syncwarp();
+  }
+  if (sumq) {
+    const double sq = block_sum_to_thread0<double>(qs);
+    if (threadIdx.x == 0 && sq != 0.0) atomicAdd(sumq, sq);
+  }
+}
+
+template <typename T, int LN>
+__global__ void __launch_bounds__(kThreads) lagrange_gather_kernel(MeshGeom G, int Kc, int64_t n,
+                                                                   const double* __restrict__ x,
+                                                                   const double* __restrict__ q,
+                                                                   const T* __restrict__ Phi,
+                                                                   double* __restrict__ phi_out,
+                                                                   double* __restrict__ F_out,
+                                                                   double* __restrict__ energy,
+                                                                   const double* __restrict__ sumq, double corr_c,
+                                                                   double ke) {
+  constexpr int W = kThreads / 32;
+  __shared__ double sw[W][3][LN], sd[W][3][LN];
+  __shared__ int sc[W][3];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int K = G.K;
+  const double shift = corr_c * (sumq ? *sumq : 0.0);
+  const double gscale = 2.0 * Kc / G.L;   // dt/dx
+  double e = 0.0;
+  for (int64_t p = blockIdx.x * (int64_t)W + wib; p < n; p += (int64_t)gridDim.x * W) {
+    if (lane < 3) {
+      int i;
+      double t, w[LN], dw[LN];
+      lagrange_cell(x[3 * p + lane], lane == 0 ? G.c0 : (lane == 1 ? G.c1 : G.c2), G.L, Kc, i, t);
+      lagrange_weights<LN>(t, w, dw);
+#pragma unroll
+      for (int l = 0; l < LN; ++l) {
+        sw[wib][lane][l] = w[l];
+        sd[wib][lane][l] = dw[l];
+      }
+      sc[wib][lane] = i * LN;
+    }
+    __syncwarp();
+    const int b0 = sc[wib][0], b1 = sc[wib][1], b2 = sc[wib][2];
+    double a = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
+    for (int r = lane; r < LN * LN; r += 32) {
+      const int l0 = r / LN, l1 = r % LN;
+      const T* row = Phi + ((int64_t)(b0 + l0) * K + (b1 + l1)) * K + b2;
+      double sv = 0.0, dv = 0.0;
+#pragma unroll
+      for (int l2 = 0; l2 < LN; ++l2) {
+        const double v = (double)row[l2];
+        sv = fma(sw[wib][2][l2], v, sv);
+        dv = fma(sd[wib][2][l2], v, dv);
+      }
+      const double w0 = sw[wib][0][l0], w1 = sw[wib][1][l1];
+      a = fma(w0 * w1, sv, a);
+      g0 = fma(sd[wib][0][l0] * w1, sv, g0);
+      g1 = fma(w0 * sd[wib][1][l1], sv, g1);
+      g2 = fma(w0 * w1, dv, g2);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      a += __shfl_xor_sync(0xffffffffu, a, o);
+      g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+      g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+      g2 += __shfl_xor_sync(0xffffffffu, g2, o);
+    }
+    if (lane == 0) {
+      const double phi = (a - shift) * ke;
+      const double qi = q ? q[p] : 0.0;
+      if (phi_out) phi_out[p] = phi;
+      if (F_out) {
+        const double sc2 = -qi * ke * gscale;
+        F_out[3 * p + 0] = sc2 * g0;
+        F_out[3 * p + 1] = sc2 * g1;
+        F_out[3 * p + 2] = sc2 * g2;
+      }
+      e += 0.5 * qi * phi;
+    }
+    __syncwarp();
+  }
+  if (energy) {
+    const double sum = block_sum_to_thread0<double>(e);
+    if (threadIdx.x == 0 && sum != 0.0) atomicAdd(energy, sum);
+  }
+}
+
 int grid_groups(kpme_plan_t P, int64_t n, int lg) {
   const int64_t pb = kThreads / lg;
   int64_t want = (n + pb - 1) / pb;
@@ -844,6 +1013,61 @@ cudaError_t launch_clear(kpme_plan_t P, float* a, int64_t n, double* s0, double*
   clear_kernel<<<(unsigned)blocks, kThreads, 0, P->stream>>>(reinterpret_cast<float4*>(a), n4, a + 4 * n4, ntail, s0,
                                                               s1);
   return cudaGetLastError();
+}
+
+namespace {
+
+template <typename T>
+cudaError_t lagrange_spread_t(kpme_plan_t P, int64_t n, const double* x, const double* q, T* Q) {
+  const MeshGeom G = geom(P);
+  const int Ln = P->p.order, Kc = P->p.K / Ln;
+  const int grid = grid_groups(P, n, 32);
+  switch (Ln) {
+    case 4: lagrange_spread_kernel<T, 4><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
+    case 6: lagrange_spread_kernel<T, 6><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
+    case 8: lagrange_spread_kernel<T, 8><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
+    case 12: lagrange_spread_kernel<T, 12><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
+    case 16: lagrange_spread_kernel<T, 16><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t lagrange_gather_t(kpme_plan_t P, int64_t n, const double* x, const double* q, const T* Phi, double* phi,
+                              double* F, double* energy, double c) {
+  const MeshGeom G = geom(P);
+  const int Ln = P->p.order, Kc = P->p.K / Ln;
+  const int grid = grid_groups(P, n, 32);
+  const double ke = P->p.coulomb_k;
+#define KPME_LG(LN)                                                                                              \
+  lagrange_gather_kernel<T, LN><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Phi, phi, F, energy, P->d_sumq, \
+                                                                  c, ke)
+  switch (Ln) {
+    case 4: KPME_LG(4); break;
+    case 6: KPME_LG(6); break;
+    case 8: KPME_LG(8); break;
+    case 12: KPME_LG(12); break;
+    case 16: KPME_LG(16); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef KPME_LG
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_lagrange_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, void* Q, bool dbl) {
+  if (n <= 0) return cudaSuccess;
+  return dbl ? lagrange_spread_t<double>(P, n, x, q, (double*)Q) : lagrange_spread_t<float>(P, n, x, q, (float*)Q);
+}
+
+cudaError_t launch_lagrange_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
+                                   bool dbl, double* phi, double* F, double* energy, bool correct) {
+  if (n <= 0) return cudaSuccess;
+  const double c = correct ? P->skp.c : 0.0;
+  return dbl ? lagrange_gather_t<double>(P, n, x, q, (const double*)Phi, phi, F, energy, c)
+             : lagrange_gather_t<float>(P, n, x, q, (const float*)Phi, phi, F, energy, c);
 }
 
 cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q) {

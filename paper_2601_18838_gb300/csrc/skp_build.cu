@@ -508,40 +508,21 @@ __global__ void sinc_err_kernel(const double* __restrict__ args, int nargs, cons
   if (threadIdx.x == 0) maxerr[blockIdx.x] = __double_as_longlong(red[0]);
 }
 
-// Quadrature-based SKP (§2.1.2, Eq. quaddecompalpham) with the B-spline factor:
-// T(m) = (1/(pi L)) B(m) exp(-pi^2 |m|^2 / (beta L)^2) / |m|^2, and 1/|m|^2 ~ sum_l w_l exp(-lambda_l |m|^2)
-// gives rank-one terms with the same factor a_l(m) = |b(m)|^2 exp(-(lambda_l + pi^2/(beta L)^2) m^2) on
-// every axis, weight w_l / (pi L), minus c delta_0 with c = |b(0)|^6 sum_l w_l / (pi L).  The node
-// count is the smallest whose best h (64 candidates in [0.5, 2] pi / sqrt(2 nq + 1)) keeps the
-// max relative error of the 1/R rule over the actual arguments R = |m|^2 > 0 within tol; that
-// error is returned as rel_err.  Terms are laid out in the two-level form with one inner term per
-// outer term.
-kpme_status_t build_skp_sinc(kpme_plan_t P, SkpHost& out) {
-  const int K = P->p.K, n = P->p.order, Kh = K / 2 + 1;
-  const double L = 2.0 * P->p.radius, beta = P->p.beta, tol = P->p.skp_tol;
-  if (!(tol > 0.0)) {
-    P->last_error = "the sinc-quadrature SKP needs a positive tolerance";
-    return KPME_ERR_INVALID_ARG;
-  }
+// Smallest node count per side N (<= 400) whose cardinal-sine rule of 1/R has a max relative
+// error <= tol over the arguments, with its best step h among 64 candidates around
+// pi / sqrt(2N + 1) (the brute-force search of §2.1.2); the errors are evaluated on the GPU.
+kpme_status_t sinc_search(kpme_plan_t P, const std::vector<double>& args, double tol, int& nq, double& h,
+                          double& best) {
   cudaStream_t s = P->stream;
-  cudaError_t err = cudaSuccess;
-  // arguments: distinct m1^2 + m2^2 + m3^2 > 0 over the wrapped modes (|m| <= K/2)
-  const int h2 = (K / 2) * (K / 2);
-  std::vector<char> seen(3 * h2 + 1, 0);
-  for (int a = 0; a <= K / 2; ++a)
-    for (int b = a; b <= K / 2; ++b)
-      for (int c = b; c <= K / 2; ++c) seen[a * a + b * b + c * c] = 1;
-  std::vector<double> args;
-  for (int r = 1; r <= 3 * h2; ++r)
-    if (seen[r]) args.push_back((double)r);
   constexpr int kH = 64;
-  DevBuf dargs, dhs, derr, bmod, vecs, scales, gen;
+  DevBuf dargs, dhs, derr;
   KPME_CUDA_TRY(P, cudaMalloc(&dargs.p, args.size() * sizeof(double)));
   KPME_CUDA_TRY(P, cudaMalloc(&dhs.p, kH * sizeof(double)));
   KPME_CUDA_TRY(P, cudaMalloc(&derr.p, kH * sizeof(unsigned long long)));
   KPME_CUDA_TRY(P, cudaMemcpyAsync(dargs.p, args.data(), args.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-  int nq = 0;
-  double h = 0.0, best = 0.0;
+  nq = 0;
+  h = 0.0;
+  best = 0.0;
   for (int q = 1; q <= 400 && nq == 0; ++q) {
     const double h0 = M_PI / std::sqrt(2.0 * q + 1.0);
     std::vector<double> hs(kH);
@@ -573,6 +554,42 @@ kpme_status_t build_skp_sinc(kpme_plan_t P, SkpHost& out) {
     P->last_error = "sinc quadrature did not reach the tolerance with 400 nodes per side";
     return KPME_ERR_TOLERANCE;
   }
+  return KPME_OK;
+}
+
+// Quadrature-based SKP (§2.1.2, Eq. quaddecompalpham) with the B-spline factor:
+// T(m) = (1/(pi L)) B(m) exp(-pi^2 |m|^2 / (beta L)^2) / |m|^2, and 1/|m|^2 ~ sum_l w_l exp(-lambda_l |m|^2)
+// gives rank-one terms with the same factor a_l(m) = |b(m)|^2 exp(-(lambda_l + pi^2/(beta L)^2) m^2) on
+// every axis, weight w_l / (pi L), minus c delta_0 with c = |b(0)|^6 sum_l w_l / (pi L).  The node
+// count is the smallest whose best h (64 candidates in [0.5, 2] pi / sqrt(2 nq + 1)) keeps the
+// max relative error of the 1/R rule over the actual arguments R = |m|^2 > 0 within tol; that
+// error is returned as rel_err.  Terms are laid out in the two-level form with one inner term per
+// outer term.
+kpme_status_t build_skp_sinc(kpme_plan_t P, SkpHost& out) {
+  const int K = P->p.K, n = P->p.order, Kh = K / 2 + 1;
+  const double L = 2.0 * P->p.radius, beta = P->p.beta, tol = P->p.skp_tol;
+  if (!(tol > 0.0)) {
+    P->last_error = "the sinc-quadrature SKP needs a positive tolerance";
+    return KPME_ERR_INVALID_ARG;
+  }
+  cudaStream_t s = P->stream;
+  cudaError_t err = cudaSuccess;
+  // arguments: distinct m1^2 + m2^2 + m3^2 > 0 over the wrapped modes (|m| <= K/2)
+  const int h2 = (K / 2) * (K / 2);
+  std::vector<char> seen(3 * h2 + 1, 0);
+  for (int a = 0; a <= K / 2; ++a)
+    for (int b = a; b <= K / 2; ++b)
+      for (int c = b; c <= K / 2; ++c) seen[a * a + b * b + c * c] = 1;
+  std::vector<double> args;
+  for (int r = 1; r <= 3 * h2; ++r)
+    if (seen[r]) args.push_back((double)r);
+  int nq = 0;
+  double h = 0.0, best = 0.0;
+  {
+    const kpme_status_t sst = sinc_search(P, args, tol, nq, h, best);
+    if (sst != KPME_OK) return sst;
+  }
+  DevBuf bmod, vecs, scales, gen;
   // factors
   KPME_CUDA_TRY(P, cudaMalloc(&bmod.p, Kh * sizeof(double)));
   bmod_kernel<<<(Kh + 127) / 128, 128, 0, s>>>(K, n, Kh, (double*)bmod.p);
@@ -624,6 +641,123 @@ kpme_status_t build_skp_sinc(kpme_plan_t P, SkpHost& out) {
   out.rel_err = best;
   out.valid = true;
   return KPME_OK;
+}
+
+// Quadrature SKP of the per-cell Lagrange form (§2.1.2, §2.2, §4.1): alpha_M on the mode cube
+// |m|_inf <= M by the sinc rule of 1/|m|^2 searched over the cube's arguments, and dense axis
+// factors on the K node positions y (cell i, node l at (i + (1 + t_l)/2) / Kc, t_l = -1 + 2l/(Ln-1)):
+//   A_l(g, h) = sum_{m=-M}^{M} exp(-(lambda_l + pi^2/xi^2) m^2) cos(2 pi m (y_g - y_h)),
+// the real cosine form of §2.3 summed over the modes.  Term l is (w_l/(pi L)) A_l x A_l x A_l (its
+// weight on the axis-3 factor) and the m = 0 correction is c = sum_l w_l / (pi L).  The factors
+// are formed here, at plan time, in float64.
+kpme_status_t build_skp_lagrange(kpme_plan_t P, SkpHost& out) {
+  const int K = P->p.K, Ln = P->p.order, Kc = K / Ln, M = P->p.modes;
+  const double L = 2.0 * P->p.radius, beta = P->p.beta, tol = P->p.skp_tol;
+  if (!(tol > 0.0)) {
+    P->last_error = "the sinc-quadrature SKP needs a positive tolerance";
+    return KPME_ERR_INVALID_ARG;
+  }
+  std::vector<char> seen(3 * M * M + 1, 0);
+  for (int a = 0; a <= M; ++a)
+    for (int b = a; b <= M; ++b)
+      for (int c = b; c <= M; ++c) seen[a * a + b * b + c * c] = 1;
+  std::vector<double> args;
+  for (int r = 1; r <= 3 * M * M; ++r)
+    if (seen[r]) args.push_back((double)r);
+  int nq = 0;
+  double h = 0.0, best = 0.0;
+  {
+    const kpme_status_t sst = sinc_search(P, args, tol, nq, h, best);
+    if (sst != KPME_OK) return sst;
+  }
+  const int R = 2 * nq + 1;
+  const double pre = 1.0 / (M_PI * L), xi2 = (beta * L) * (beta * L);
+  std::vector<double> y(K);
+  for (int i = 0; i < Kc; ++i)
+    for (int l = 0; l < Ln; ++l) {
+      const double t = -1.0 + 2.0 * l / (Ln - 1);
+      y[i * Ln + l] = (i + 0.5 * (1.0 + t)) / Kc;
+    }
+  const size_t KK = (size_t)K * K;
+  std::vector<double> cs((size_t)M * KK);   // cos(2 pi m (y_g - y_h)), m = 1..M
+  for (int m = 1; m <= M; ++m)
+    for (int g = 0; g < K; ++g)
+      for (int hh = 0; hh < K; ++hh) cs[(m - 1) * KK + (size_t)g * K + hh] = std::cos(2.0 * M_PI * m * (y[g] - y[hh]));
+  out = SkpHost();
+  out.dense = true;
+  out.gen3.resize((size_t)R * KK);
+  out.gen2.resize((size_t)R * KK);
+  double wsum = 0.0;
+  std::vector<double> am(M + 1), w3(R);
+  for (int t = 0; t < R; ++t) {
+    const int l = t - nq;
+    const double wl = h / (1.0 + std::exp(-l * h));
+    const double lam = std::log1p(std::exp(l * h));
+    wsum += wl;
+    w3[t] = pre * wl;
+    for (int m = 0; m <= M; ++m) am[m] = std::exp(-(lam + M_PI * M_PI / xi2) * (double)m * m);
+    for (size_t gh = 0; gh < KK; ++gh) {
+      double A = am[0];
+      for (int m = 1; m <= M; ++m) A += 2.0 * am[m] * cs[(m - 1) * KK + gh];
+      out.gen2[(size_t)t * KK + gh] = A;
+      out.gen3[(size_t)t * KK + gh] = w3[t] * A;
+    }
+  }
+  out.gen1 = out.gen2;
+  out.r0 = R;
+  out.R = R;
+  out.r1.assign(R, 1);
+  out.outer_of.resize(R);
+  std::iota(out.outer_of.begin(), out.outer_of.end(), 0);
+  out.sig_outer = w3;
+  out.sig_inner.assign(R, 1.0);
+  out.c = pre * wsum;
+  out.rel_err = best;
+  out.valid = true;
+  return KPME_OK;
+}
+
+// Dense factors F[s][t][n][k] = slice s of D_t[n][k] in the requested format (the formats of
+// materialize_kernel; the fixed-point digits use one power of two per factor, gmax[t]).
+__global__ void materialize_dense_kernel(const double* __restrict__ D, const double* __restrict__ gmax, int count,
+                                         int K, int slices, int kind, void* __restrict__ dst) {
+  const int64_t per = (int64_t)K * K;
+  const int64_t total = per * count;
+  for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (int64_t)gridDim.x * blockDim.x) {
+    const double v = D[idx];
+    if (kind == 0) {
+      ((double*)dst)[idx] = v;
+    } else if (kind == 1) {
+      ((float*)dst)[idx] = (float)v;
+    } else if (kind == 2) {
+      double r = v;
+      for (int s = 0; s < slices; ++s) {
+        const __nv_bfloat16 h = __double2bfloat16(r);
+        ((__nv_bfloat16*)dst)[s * total + idx] = h;
+        r -= (double)__bfloat162float(h);
+      }
+    } else if (kind == 4) {
+      int e = 0;
+      frexp(gmax[idx / per], &e);
+      double u = ldexp(v, 7 - e);
+      for (int s = 0; s < slices; ++s) {
+        const double dg = rint(u);
+        u = (u - dg) * 256.0;
+        ((__nv_bfloat16*)dst)[s * total + idx] = __double2bfloat16(ldexp(dg, e - 7 - 8 * s));
+      }
+    } else {
+      const float hi = tf32_rn((float)v);
+      ((float*)dst)[idx] = hi;
+      if (slices > 1) ((float*)dst)[total + idx] = (float)(v - (double)hi);
+    }
+  }
+}
+
+cudaError_t launch_materialize_dense(kpme_plan_t P, const double* d_dense, const double* d_gmax, int count, void* dst,
+                                     int slices, int kind) {
+  materialize_dense_kernel<<<1024, kT, 0, P->stream>>>(d_dense, d_gmax, count, P->p.K, slices, kind, dst);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_materialize(kpme_plan_t P, const double* d_gen, int count, void* dst, int slices, int kind) {

@@ -1,0 +1,95 @@
+"""The per-cell Lagrange form of KPME on the GPU (KPME_INTERP_LAGRANGE) against the oracle:
+node charges and gathering, the quadrature SKP over the mode cube, and energies / potentials /
+forces, against the oracle's exact node operator and the direct sum on the same modes."""
+import numpy as np
+import pytest
+
+from oracle import lagrange as lg
+from tests._gpu_util import cuda_or_skip, dev, host, rel
+
+pytestmark = pytest.mark.gpu
+
+L_BOX, BETA, M = 20.0, 0.15, 4
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = cuda_or_skip()
+    import __graft_entry__ as g
+    g.build()
+    return t
+
+
+def _cloud(n, seed):
+    rng = np.random.default_rng(seed)
+    x = rng.uniform(0.0, L_BOX, (n, 3))
+    q = rng.choice([-1.0, 1.0], n)
+    return x, q - q.mean()
+
+
+def _plan(prec, Kc, Ln, max_n, tol=1e-12):
+    from paper_2601_18838_gb300 import Plan
+    return Plan(L_BOX, Kc * Ln, Ln, BETA, precision=prec, skp_tol=tol, skp_method="sinc", max_n=max_n,
+                interp="lagrange", modes=M)
+
+
+@pytest.mark.parametrize("Kc,Ln", [(4, 16), (8, 8), (16, 4), (6, 12)])
+def test_lagrange_spread_and_gather_match_oracle(torch, Kc, Ln):
+    x, q = _cloud(301, Kc)
+    plan = _plan("fp64", Kc, Ln, 301)
+    Q = host(plan.spread(dev(torch, x), dev(torch, q)))
+    Qr = lg.spread(x, q, L_BOX, Kc, Ln)
+    assert np.abs(Q - Qr).max() <= 1e-12 * np.abs(Qr).max()
+    rng = np.random.default_rng(1)
+    Phi = rng.standard_normal(Q.shape)
+    phi, F = plan.gather(dev(torch, x), dev(torch, q), dev(torch, Phi))
+    phi_r, F_r = lg.gather(x, q, L_BOX, Kc, Ln, Phi)
+    assert rel(host(phi), phi_r) < 1e-12 and rel(host(F), F_r) < 1e-12
+
+
+# Equispaced nodes: at Ln = 16 the weights reach ~1e3 with cancelling signs (the Lebesgue
+# constant), which float32 node charges do not survive; the float forms are used with Ln <= 8
+# and the FP64 form carries the high orders (the paper's "relatively small orders" in double).
+@pytest.mark.parametrize("prec,Kc,Ln,tol,tol_f", [("fp64", 4, 16, 3e-9, 1e-7), ("fp64", 8, 8, 1e-12, 1e-11),
+                                                 ("fp32", 8, 8, 5e-5, 2e-4), ("fp32", 16, 4, 2e-5, 1e-4),
+                                                 ("bf16x10", 8, 8, 2e-5, 1e-4), ("bf16x10", 16, 4, 2e-5, 1e-4)])
+def test_lagrange_energy_forces_match_oracle(torch, prec, Kc, Ln, tol, tol_f):
+    x, q = _cloud(500, 7)
+    plan = _plan(prec, Kc, Ln, 500)
+    R, err = plan.build_skp()
+    assert R > 0 and err <= 1e-12
+    out = plan.energy_forces(dev(torch, x), dev(torch, q))
+    ref = lg.reciprocal(x, q, L_BOX, BETA, Kc, Ln, M)            # exact node operator
+    e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
+    e_E = abs(out["energy"].item() - ref["E"]) / abs(ref["E"])
+    print(f"lagrange {prec} Kc={Kc} Ln={Ln}: R={R} phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e}")
+    assert e_phi < tol and e_f < tol_f and e_E < tol
+    if prec == "fp64":
+        # and the interpolation error against the direct sum on the same modes (Thm. 3)
+        d = lg.direct(x, q, L_BOX, BETA, M)
+        assert rel(host(out["dEdq"]), d["phi"]) < (1e-8 if Ln >= 12 else 1e-6)
+
+
+def test_lagrange_non_neutral_charges_use_the_correction(torch):
+    x, q = _cloud(200, 3)
+    q = q + 0.25
+    plan = _plan("fp64", 4, 16, 200)
+    plan.build_skp()
+    out = plan.energy_forces(dev(torch, x), dev(torch, q))
+    ref = lg.reciprocal(x, q, L_BOX, BETA, 4, 16, M)
+    assert rel(host(out["dEdq"]), ref["phi"]) < 1e-9
+    assert plan.skp_c() > 0
+
+
+def test_lagrange_rejects_what_it_does_not_support(torch):
+    from paper_2601_18838_gb300._binding import KpmeError
+    x, q = _cloud(50, 5)
+    plan = _plan("fp64", 4, 16, 50)
+    plan.build_skp()
+    with pytest.raises(KpmeError):
+        plan.energy_forces(dev(torch, x), dev(torch, q), virial=True)
+    with pytest.raises(KpmeError):
+        plan.virial_tensor(dev(torch, x), dev(torch, q))
+    with pytest.raises(KpmeError):   # the B-spline form's parameters are checked as before
+        from paper_2601_18838_gb300 import Plan
+        Plan(L_BOX, 64, 16, BETA, precision="fp64", skp_method="svd", interp="lagrange", modes=M)
