@@ -33,6 +33,8 @@ WORKLOAD_TEXT = {
     "large": "1e6 charges +-1, L=220 A, order 6, K=256, beta=0.35/A, SKP tol 1e-7",
     "batched": "64 independent neutral +-1 systems, N log-uniform in [2000, 50000], box 30-80 A, "
                "K in {32, 48, 64} (box/K <= 1.25 A), order 4, one graph launch per evaluation",
+    "lagrange": "per-cell Lagrange form: 2e4 charges +-1, L=30 A, beta=0.1/A, modes |m|_inf <= 4, "
+                "8^3 cells of 8^3 equispaced nodes (64 per axis), quadrature SKP 1e-12, no virial",
 }
 DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16": "bf16", "bf16x3": "bf16",
          "bf16x6": "bf16", "bf16x10": "bf16"}
@@ -44,8 +46,8 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16":
 # null until it is captured again.
 SKP_TRAFFIC = {
     # profiles/dram_traffic_water_k64_bf16x10.md: mp_ozt_kernel 1,515,008 B + mp_ozf_kernel
-    # 19,320,064 B (reads; 0 B written: Y and Phi stay in L2), 2 launches per evaluation
-    ("water", "bf16x10"): {"digest": "71ec9ddf3dd12bac", "bytes_per_launch": (1515008 + 19320064) / 2},
+    # 19,324,160 B (reads; 0 B written: Y and Phi stay in L2), 2 launches per evaluation
+    ("water", "bf16x10"): {"digest": "15ac4d609920d908", "bytes_per_launch": (1515008 + 19324160) / 2},
 }
 SKP_SOURCES = ("gemm_ozf.cu", "gemm_ozt.cu", "tc_common.cuh")
 
@@ -127,17 +129,33 @@ def _system(name):
     return getattr(workloads, name)()
 
 
+def _oracle_eval(s):
+    """The oracle's evaluation of workload s and its plan-time build (returns (build_s, eval))."""
+    t0 = time.perf_counter()
+    if s.meta.get("interp") == "lagrange":
+        from oracle import lagrange as lg
+        Kc, M = s.meta["cells"], s.meta["modes"]
+        fac = lg.sinc_factors(Kc, s.order, s.box, s.beta, M, s.skp_tol)
+
+        def ev():
+            Qn = lg.spread(s.x, s.q, s.box, Kc, s.order)
+            Phi = lg.apply_skp(Qn, *fac, s.box)
+            phi, F = lg.gather(s.x, s.q, s.box, Kc, s.order, Phi)
+            return {"phi": phi, "F": F}
+        return time.perf_counter() - t0, ev
+    from oracle import skp
+    o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol)
+    return time.perf_counter() - t0, lambda: skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+
+
 def cpu_baseline(s, budget_s: float = 20.0, max_evals: int = 5, gpu_out=None) -> dict:
     """The float64 oracle (as it stands) on the host cores: full reciprocal evaluations of
     the same workload, as many as fit in the budget (at least one)."""
-    from oracle import skp
-    t0 = time.perf_counter()
-    o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol)
-    t_build = time.perf_counter() - t0
+    t_build, ev = _oracle_eval(s)
     n, t, ref = 0, 0.0, None
     while n < max_evals and (n == 0 or t < budget_s):
         a = time.perf_counter()
-        ref = skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+        ref = ev()
         t += time.perf_counter() - a
         n += 1
     res = {"value": n / t, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
@@ -158,13 +176,12 @@ def run_reference(args):
     if rank != 0:
         return 0
     s = _system(args.workload)
-    from oracle import skp
-    o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol)
+    _, ev = _oracle_eval(s)
     for _ in range(args.warmup):
-        skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+        ev()
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+        ev()
     dt = time.perf_counter() - t0
     v = args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
@@ -304,7 +321,10 @@ def main(argv=None):
 
     s = _system(args.workload)
     stream = torch.cuda.current_stream()
-    plan = Plan(s.box, s.K, s.order, s.beta, precision=args.precision, skp_tol=s.skp_tol, max_n=s.n)
+    lag = s.meta.get("interp") == "lagrange"
+    extra = dict(interp="lagrange", modes=s.meta["modes"], skp_method="sinc") if lag else {}
+    plan = Plan(s.box, s.K, s.order, s.beta, precision=args.precision, skp_tol=s.skp_tol, max_n=s.n, **extra)
+    vir = not lag   # the per-cell form has no virial
     R, skp_err = plan.build_skp()
     info = plan.info()
     x = torch.tensor(s.x, device=dev)
@@ -318,7 +338,7 @@ def main(argv=None):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)   # > L2 (129 MB)
 
     def step():
-        plan.energy_forces(x, q, forces=True, dEdq=True, virial=True, out=out)
+        plan.energy_forces(x, q, forces=True, dEdq=True, virial=vir, out=out)
 
     def timed(nsteps, profile=False):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nsteps)]
@@ -392,7 +412,10 @@ def main(argv=None):
         part[kname] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs,
                       "frac_hbm": (gbs / hbm) if gbs else None}
     part["hbm_peak_gbs"] = hbm
-    part["note"] = ("no cell sort (autotuned): spread = mesh clear + lane-group spreading with float32 atomics "
+    part["note"] = ("per-cell Lagrange: spread = mesh clear + one warp per particle (Ln^3 equispaced-node "
+                    "weights, float32 atomics into the L2-resident node mesh), gather = one warp per particle"
+                    if lag else
+                    "no cell sort (autotuned): spread = mesh clear + lane-group spreading with float32 atomics "
                     "into the L2-resident mesh, gather = one thread per particle; bound by atomics and latency"
                     if tune.get("tile") == -1 else
                     "spread includes the cell sort (count, scan, scatter) and the mesh clear; the kernels are "
@@ -410,11 +433,12 @@ def main(argv=None):
     def e2e_step():
         xd.copy_(xh, non_blocking=True)
         qd.copy_(qh, non_blocking=True)
-        plan.energy_forces(xd, qd, forces=True, dEdq=True, virial=True, out=out)
+        plan.energy_forces(xd, qd, forces=True, dEdq=True, virial=vir, out=out)
         Fh.copy_(out["forces"], non_blocking=True)
         ph.copy_(out["dEdq"], non_blocking=True)
         Eh[0:1].copy_(out["energy"], non_blocking=True)
-        Eh[1:2].copy_(out["virial"], non_blocking=True)
+        if vir:
+            Eh[1:2].copy_(out["virial"], non_blocking=True)
 
     for _ in range(3):
         e2e_step()
@@ -433,11 +457,11 @@ def main(argv=None):
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
         e_ms = t.item()
     e2e = {"value": ws * args.steps / (e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": s.n * 32,
-           "d2h_bytes_per_step": s.n * 32 + 16}
+           "d2h_bytes_per_step": s.n * 32 + (16 if vir else 8)}
 
     # full virial tensor (mode space; an extra call, outside the timed step)
     vt = None
-    if rank == 0:
+    if rank == 0 and vir:
         for _ in range(3):
             plan.virial_tensor(x, q)
         torch.cuda.synchronize()

@@ -48,8 +48,9 @@ struct Buffers {
 
 kpme_status_t time_config(kpme_plan_t P, int64_t n, const double* x, const double* q, const Buffers& b, double* ms) {
   kpme_status_t st;
+  double* W = kpme::lagrange(P) ? nullptr : b.W;   // the per-cell form has no virial
   for (int i = 0; i < 2; ++i)   // the first call captures the evaluation graph
-    if ((st = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, b.W)) != KPME_OK) return st;
+    if ((st = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, W)) != KPME_OK) return st;
   cudaEvent_t e0, e1;
   if (cudaEventCreate(&e0) != cudaSuccess) return KPME_ERR_CUDA;
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -61,7 +62,7 @@ kpme_status_t time_config(kpme_plan_t P, int64_t n, const double* x, const doubl
   auto run = [&](int reps, double* out) {
     cudaEventRecord(e0, P->stream);
     kpme_status_t r = KPME_OK;
-    for (int i = 0; i < reps && r == KPME_OK; ++i) r = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, b.W);
+    for (int i = 0; i < reps && r == KPME_OK; ++i) r = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, W);
     cudaEventRecord(e1, P->stream);
     float t = 0.0f;
     if (r == KPME_OK && (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
@@ -83,7 +84,7 @@ kpme_status_t time_config(kpme_plan_t P, int64_t n, const double* x, const doubl
 std::string key_of(kpme_plan_t P, int64_t n) {
   char buf[160];
   const int nb = n > 0 ? (int)std::floor(std::log2((double)n)) : 0;
-  snprintf(buf, sizeof(buf), "K%d_order%d_prec%d_n2^%d_sm%d_cc%d%d", P->p.K, P->p.order, P->p.precision, nb,
+  snprintf(buf, sizeof(buf), "K%d_order%d_prec%d_interp%d_n2^%d_sm%d_cc%d%d", P->p.K, P->p.order, P->p.precision, P->p.interp, nb,
            P->sm_count, P->cc_major, P->cc_minor);
   return buf;
 }

@@ -93,3 +93,16 @@ def test_lagrange_rejects_what_it_does_not_support(torch):
     with pytest.raises(KpmeError):   # the B-spline form's parameters are checked as before
         from paper_2601_18838_gb300 import Plan
         Plan(L_BOX, 64, 16, BETA, precision="fp64", skp_method="svd", interp="lagrange", modes=M)
+
+
+def test_lagrange_autotune_keeps_results(torch):
+    """The autotuner times Lagrange plans without a virial and keeps the results unchanged."""
+    x, q = _cloud(2000, 9)
+    plan = _plan("bf16x10", 8, 8, 2000)
+    plan.build_skp()
+    xd, qd = dev(torch, x), dev(torch, q)
+    t = plan.autotune(xd, qd)
+    assert t["ms_per_eval"] > 0
+    out = plan.energy_forces(xd, qd)
+    ref = lg.reciprocal(x, q, L_BOX, BETA, 8, 8, M)
+    assert rel(host(out["dEdq"]), ref["phi"]) < 2e-5 and rel(host(out["forces"]), ref["F"]) < 1e-4
