@@ -412,8 +412,9 @@ def main(argv=None):
         part[kname] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs,
                       "frac_hbm": (gbs / hbm) if gbs else None}
     part["hbm_peak_gbs"] = hbm
-    part["note"] = ("per-cell Lagrange: spread = mesh clear + one warp per particle (Ln^3 equispaced-node "
-                    "weights, float32 atomics into the L2-resident node mesh), gather = one warp per particle"
+    part["note"] = ("per-cell Lagrange: spread = counting sort by cell (clear, count, scan, scatter) + one CTA "
+                    "per cell writing its Ln^3 node block once (no atomics), gather = one CTA per cell with the "
+                    "block in shared memory, one warp per particle"
                     if lag else
                     "no cell sort (autotuned): spread = mesh clear + lane-group spreading with float32 atomics "
                     "into the L2-resident mesh, gather = one thread per particle; bound by atomics and latency"

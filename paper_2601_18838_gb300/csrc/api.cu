@@ -718,16 +718,10 @@ bool lagrange(kpme_plan_t P) { return P->p.interp == KPME_INTERP_LAGRANGE; }
 kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, MeshRef& out,
                           double* also_zero = nullptr) {
   const int64_t k3 = K3(P);
-  if (lagrange(P)) {   // node charges Q = S_Y q of the per-cell form
-    if (P->prec.fp64) {
-      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-      if (also_zero) KPME_CUDA_TRY(P, cudaMemsetAsync(also_zero, 0, sizeof(double), P->stream));
-      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Q, 0, (size_t)k3 * sizeof(double), P->stream));
-    } else {
-      KPME_CUDA_TRY(P, launch_clear(P, P->d_Qf, k3, P->d_sumq, also_zero));
-    }
+  if (lagrange(P)) {   // node charges Q = S_Y q of the per-cell form (every node written)
     void* Qm = P->prec.fp64 ? (void*)P->d_Q : (void*)P->d_Qf;
-    KPME_CUDA_TRY(P, launch_lagrange_spread(P, n, x, q, Qm, P->prec.fp64));
+    KPME_CUDA_TRY(P, launch_lagrange_sort(P, n, x, P->d_sumq, also_zero));
+    KPME_CUDA_TRY(P, launch_lagrange_spread(P, q, Qm, P->prec.fp64));
     out = {Qm, P->prec.fp64};
     return KPME_OK;
   }
@@ -758,7 +752,8 @@ kpme_status_t gather_mesh(kpme_plan_t P, int64_t n, const double* x, const doubl
                           double* energy, bool correct, bool sorted) {
   if (lagrange(P)) {   // S_X^* of the per-cell form
     if (!correct) KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-    KPME_CUDA_TRY(P, launch_lagrange_gather(P, n, x, q, P->d_Phi, P->prec.fp64, phi, F, energy, correct));
+    if (!sorted) KPME_CUDA_TRY(P, launch_lagrange_sort(P, n, x, nullptr, nullptr));
+    KPME_CUDA_TRY(P, launch_lagrange_gather(P, n, q, P->d_Phi, P->prec.fp64, phi, F, energy, correct));
     return KPME_OK;
   }
   if (!tiled(P)) {
@@ -889,7 +884,16 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->d_qpsi = acc + 2;
   P->allow_fused = getenv_flag("KPME_FUSED", true);
   P->tile = 0;
-  if (!lag && choose_tile(p.K, p.order) > 0) {
+  if (lag) {   // the cell sort of the per-cell form: counters and records
+    const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
+    const int Kc = p.K / p.order;
+    const size_t ncnt = (size_t)Kc * Kc * Kc * lagrange_sub(P);
+    if ((st = dalloc(P, (void**)&P->d_tcount, ncnt * sizeof(int))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_tstart, (ncnt + 1) * sizeof(int))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_rec_in, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
+    if ((st = dalloc(P, (void**)&P->d_rec, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
+  } else if (choose_tile(p.K, p.order) > 0) {
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
     if ((st = set_tile(P, choose_tile(p.K, p.order))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);

@@ -201,9 +201,14 @@ kpme_status_t sinc_search(kpme_plan_t P, const std::vector<double>& args, double
 cudaError_t launch_materialize_dense(kpme_plan_t P, const double* d_dense, const double* d_gmax, int count, void* dst,
                                      int slices, int kind);
 bool lagrange(kpme_plan_t P);   // per-cell Lagrange interpolation (KPME_INTERP_LAGRANGE)
-cudaError_t launch_lagrange_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, void* Q, bool dbl);
-cudaError_t launch_lagrange_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
-                                   bool dbl, double* phi, double* F, double* energy, bool correct);
+// per-cell form: counting sort of n particles by cell into the plan's records (also clears the
+// float64 accumulators zero0 and zero1 when given), then the per-cell spreading (node charges and
+// their sum into sumq) and gathering over the sorted records
+int lagrange_sub(kpme_plan_t P);   // counters per cell of the sort
+cudaError_t launch_lagrange_sort(kpme_plan_t P, int64_t n, const double* x, double* zero0, double* zero1);
+cudaError_t launch_lagrange_spread(kpme_plan_t P, const double* q, void* Q, bool dbl);
+cudaError_t launch_lagrange_gather(kpme_plan_t P, int64_t n, const double* q, const void* Phi, bool dbl, double* phi,
+                                   double* F, double* energy, bool correct);
 cudaError_t launch_materialize(kpme_plan_t P, const double* d_gen, int count, void* dst, int fmt_slices,
                                int fmt_kind);
 cudaError_t launch_virial_generator(kpme_plan_t P, double* d_gen);

@@ -755,10 +755,21 @@ __global__ void __launch_bounds__(kThreads) spread_nosort_kernel(MeshGeom G, int
 // ---- per-cell Lagrange interpolation: S_Y and S_X^* of §2.2 and §4.1 ----
 // Kc^3 cells, Ln equispaced nodes per axis and cell (t_l = -1 + 2l/(Ln - 1) in the cell's local
 // coordinate t in [-1, 1], Eq. interp1d); node l of cell i of an axis has index i Ln + l (K = Kc Ln
-// nodes per axis, not periodic: the periodicity lives in the node operator).  One warp per
-// particle: lanes 0..2 take the float64 cell coordinate of one axis and its Ln weights (and
-// derivatives) from the product formula into the warp's shared-memory slot; the Ln^2 (l0, l1)
-// rows of the stencil are then spread over the lanes, each visiting its row's Ln consecutive nodes.
+// nodes per axis, not periodic: the periodicity lives in the node operator).  The cells are
+// disjoint in node space, so after a counting sort of the particles by cell one CTA per cell owns
+// its Ln^3 node block: spreading writes every node exactly once (no atomics and no mesh clear;
+// an empty cell writes zeros) and gathering reads its block once into shared memory.  The cell
+// and local coordinate of a particle are float64 (the oracle's operations, rounded alike); the
+// weights and the sums run in the mesh's type.
+
+// sorted record of one particle: local coordinates of the three axes and the particle index
+struct LagRec {
+  double t[3];
+  int p, pad;
+};
+static_assert(sizeof(LagRec) == 2 * sizeof(float4), "a record is two float4 (the sort's scatter copies those)");
+
+constexpr int kLagThreads = 128;
 
 // cell index and local coordinate of one axis (the float64 operations of the oracle, rounded alike)
 __device__ __forceinline__ void lagrange_cell(double x, double c, double L, int Kc, int& i, double& t) {
@@ -772,152 +783,209 @@ __device__ __forceinline__ void lagrange_cell(double x, double c, double L, int 
   t = __dsub_rn(__dmul_rn(2.0, __dsub_rn(u, (double)ii)), 1.0);
 }
 
-// S_l(t) = prod_{k != l} (t - t_k)/(t_l - t_k) and, when dw != nullptr, dS_l/dt = sum_{k != l}
-// prod_{j != l, k} (t - t_j)/(t_l - t_j) / (t_l - t_k) through prefix and suffix products
-template <int LN>
-__device__ __forceinline__ void lagrange_weights(double t, double* w, double* dw) {
+// S_l(t) = prod_{k != l} (t - t_k) r_lk with r_lk = 1/(t_l - t_k) = (Ln - 1)/(2 (l - k)), a
+// constant folded at compile time (no divisions), and, when D, dS_l/dt by the product rule on
+// the running pair (P, P'): P' <- P' f + P r_lk, P <- P f for each factor f.
+template <typename T, int LN, bool D>
+__device__ __forceinline__ void lagrange_axis(T t, T* w, T* dw) {
 #pragma unroll
   for (int l = 0; l < LN; ++l) {
-    const double tl = -1.0 + 2.0 * l / (LN - 1);
-    double f[LN];
-    double S = 1.0;
+    T p = T(1), dp = T(0);
 #pragma unroll
-    for (int j = 0; j < LN; ++j) {
-      const double tj = -1.0 + 2.0 * j / (LN - 1);
-      f[j] = (j == l) ? 1.0 : (t - tj) / (tl - tj);
-      S *= f[j];
+    for (int k = 0; k < LN; ++k) {
+      if (k == l) continue;
+      const T r = T((LN - 1) / (2.0 * (l - k)));
+      const T f = (t - T(-1.0 + 2.0 * k / (LN - 1))) * r;
+      if (D) dp = dp * f + p * r;
+      p *= f;
     }
-    w[l] = S;
-    if (dw) {
-      double pre[LN + 1];
-      pre[0] = 1.0;
+    w[l] = p;
+    if (D) dw[l] = dp;
+  }
+}
+
+template <int LN>
+constexpr int lag_chunk() {   // particles whose weights are staged in shared memory at once
+  return LN >= 12 ? 16 : 32;
+}
+
+template <typename T>
+__device__ __forceinline__ T lag_block_sum(T v) {   // to thread 0 of a kLagThreads block
+  __shared__ T red[kLagThreads / 32];
 #pragma unroll
-      for (int j = 0; j < LN; ++j) pre[j + 1] = pre[j] * f[j];
-      double suf = 1.0, d = 0.0;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T s = T(0);
+  if (threadIdx.x == 0)
+    for (int i = 0; i < kLagThreads / 32; ++i) s += red[i];
+  return s;
+}
+
+// counting sort, pass 1: cell counters (sub counters per cell, chosen by the particle index, cut
+// the contention of the returned atomics) and the record of each particle
+__global__ void __launch_bounds__(kThreads) lagrange_count_kernel(MeshGeom G, int Kc, int sub, int64_t n,
+                                                                  const double* __restrict__ x, int* __restrict__ count,
+                                                                  int2* __restrict__ slot, LagRec* __restrict__ rec) {
+  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+    LagRec r;
+    int c = 0;
 #pragma unroll
-      for (int k = LN - 1; k >= 0; --k) {
-        if (k != l) d += pre[k] * suf / (tl - (-1.0 + 2.0 * k / (LN - 1)));
-        suf *= f[k];
+    for (int a = 0; a < 3; ++a) {
+      int ia;
+      lagrange_cell(x[3 * i + a], a == 0 ? G.c0 : (a == 1 ? G.c1 : G.c2), G.L, Kc, ia, r.t[a]);
+      c = c * Kc + ia;
+    }
+    r.p = (int)i;
+    r.pad = 0;
+    const int s = c * sub + (int)(i % sub);
+    slot[i] = make_int2(s, atomicAdd(count + s, 1));
+    rec[i] = r;
+  }
+}
+
+// S_Y q: one CTA per cell.  A chunk of the cell's particles has its weights staged in shared
+// memory (q folded into axis 0); each thread owns nodes of the block and sums over the chunk.
+// sumq receives the sum of the node charges, the total the m = 0 correction of the node
+// operator takes (equal to the particles' charge sum up to the rounding of the weights).
+template <typename T, int LN>
+__global__ void __launch_bounds__(kLagThreads) lagrange_spread_cell_kernel(int Kc, int sub,
+                                                                          const int* __restrict__ start,
+                                                                          const LagRec* __restrict__ rec,
+                                                                          const double* __restrict__ q,
+                                                                          T* __restrict__ Q, double* __restrict__ sumq) {
+  constexpr int NN = LN * LN * LN, NPT = (NN + kLagThreads - 1) / kLagThreads, CH = lag_chunk<LN>();
+  __shared__ T sw[CH][3][LN];
+  const int cell = blockIdx.x;
+  const int i0 = cell / (Kc * Kc), i1 = (cell / Kc) % Kc, i2 = cell % Kc;
+  const int64_t K = (int64_t)Kc * LN;
+  const int b = start[cell * sub], e = start[(cell + 1) * sub];
+  T acc[NPT];
+#pragma unroll
+  for (int k = 0; k < NPT; ++k) acc[k] = T(0);
+  for (int j0 = b; j0 < e; j0 += CH) {
+    const int m = min(CH, e - j0);
+    __syncthreads();   // the previous chunk's weights are consumed
+    for (int it = threadIdx.x; it < 3 * m; it += kLagThreads) {
+      const int j = it / 3, a = it - 3 * j;
+      const LagRec& r = rec[j0 + j];
+      T w[LN];
+      lagrange_axis<T, LN, false>((T)r.t[a], w, nullptr);
+      const T s = a == 0 ? (T)q[r.p] : T(1);
+#pragma unroll
+      for (int l = 0; l < LN; ++l) sw[j][a][l] = w[l] * s;
+    }
+    __syncthreads();
+    for (int j = 0; j < m; ++j) {
+#pragma unroll
+      for (int k = 0; k < NPT; ++k) {
+        const int v = threadIdx.x + k * kLagThreads;
+        if (NN % kLagThreads == 0 || v < NN) {
+          const int l0 = v / (LN * LN), l1 = (v / LN) % LN, l2 = v % LN;
+          acc[k] = fma(sw[j][0][l0] * sw[j][1][l1], sw[j][2][l2], acc[k]);
+        }
       }
-      dw[l] = d;
     }
   }
-}
-
-template <typename T, int LN>
-__global__ void __launch_bounds__(kThreads) lagrange_spread_kernel(MeshGeom G, int Kc, int64_t n,
-                                                                   const double* __restrict__ x,
-                                                                   const double* __restrict__ q, T* __restrict__ Q,
-                                                                   double* __restrict__ sumq) {
-  constexpr int W = kThreads / 32;
-  __shared__ double sw[W][3][LN];
-  __shared__ int sc[W][3];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int K = G.K;
   double qs = 0.0;
-  for (int64_t p = blockIdx.x * (int64_t)W + wib; p < n; p += (int64_t)gridDim.x * W) {
-    if (lane < 3) {
-      int i;
-      double t, w[LN];
-      lagrange_cell(x[3 * p + lane], lane == 0 ? G.c0 : (lane == 1 ? G.c1 : G.c2), G.L, Kc, i, t);
-      lagrange_weights<LN>(t, w, nullptr);
 #pragma unroll
-      for (int l = 0; l < LN; ++l) sw[wib][lane][l] = w[l];
-      sc[wib][lane] = i * LN;
+  for (int k = 0; k < NPT; ++k) {
+    const int v = threadIdx.x + k * kLagThreads;
+    if (NN % kLagThreads == 0 || v < NN) {
+      const int l0 = v / (LN * LN), l1 = (v / LN) % LN, l2 = v % LN;
+      Q[((i0 * LN + l0) * K + i1 * LN + l1) * K + i2 * LN + l2] = acc[k];
+      qs += (double)acc[k];
     }
-    __syncwarp();
-    const double qi = q[p];
-    if (lane == 0) qs += qi;
-    const int b0 = sc[wib][0], b1 = sc[wib][1], b2 = sc[wib][2];
-    for (int r = lane; r < LN * LN; r += 32) {
-      const int l0 = r / LN, l1 = r % LN;
-      const double w01 = qi * sw[wib][0][l0] * sw[wib][1][l1];
-      T* row = Q + ((int64_t)(b0 + l0) * K + (b1 + l1)) * K + b2;
-#pragma unroll
-      for (int l2 = 0; l2 < LN; ++l2) atomicAdd(row + l2, (T)(w01 * sw[wib][2][l2]));
-    }
-    __syncwarp();
   }
-  if (sumq) {
-    const double sq = block_sum_to_thread0<double>(qs);
-    if (threadIdx.x == 0 && sq != 0.0) atomicAdd(sumq, sq);
+  if (b < e) {   // uniform over the CTA
+    qs = lag_block_sum<double>(qs);
+    if (threadIdx.x == 0 && qs != 0.0) atomicAdd(sumq, qs);
   }
 }
 
+// S_X^*: one CTA per cell.  The cell's node block minus its first node's value (phi = Phi_ref +
+// sum S (Phi - Phi_ref), exact since the weights sum to one, keeps the sums small) sits in shared
+// memory with padded rows; the weights and derivatives of a chunk are staged as in spreading and
+// one warp per particle sums the Ln^2 rows over its lanes.
 template <typename T, int LN>
-__global__ void __launch_bounds__(kThreads) lagrange_gather_kernel(MeshGeom G, int Kc, int64_t n,
-                                                                   const double* __restrict__ x,
-                                                                   const double* __restrict__ q,
-                                                                   const T* __restrict__ Phi,
-                                                                   double* __restrict__ phi_out,
-                                                                   double* __restrict__ F_out,
-                                                                   double* __restrict__ energy,
-                                                                   const double* __restrict__ sumq, double corr_c,
-                                                                   double ke) {
-  constexpr int W = kThreads / 32;
-  __shared__ double sw[W][3][LN], sd[W][3][LN];
-  __shared__ int sc[W][3];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int K = G.K;
+__global__ void __launch_bounds__(kLagThreads) lagrange_gather_cell_kernel(
+    int Kc, int sub, double gscale, const int* __restrict__ start, const LagRec* __restrict__ rec,
+    const double* __restrict__ q, const T* __restrict__ Phi, double* __restrict__ phi_out, double* __restrict__ F_out,
+    double* __restrict__ energy, const double* __restrict__ sumq, double corr_c, double ke) {
+  constexpr int NR = LN * LN, RS = LN + 1, CH = lag_chunk<LN>(), W = kLagThreads / 32;
+  __shared__ T sphi[NR * RS];
+  __shared__ T sw[CH][3][LN], sd[CH][3][LN];
+  const int cell = blockIdx.x;
+  const int b = start[cell * sub], e = start[(cell + 1) * sub];
+  if (b == e) return;   // the whole CTA: nothing to gather
+  const int i0 = cell / (Kc * Kc), i1 = (cell / Kc) % Kc, i2 = cell % Kc;
+  const int64_t K = (int64_t)Kc * LN;
+  const T* base = Phi + ((int64_t)i0 * LN * K + i1 * LN) * K + i2 * LN;
+  const T ref = base[0];
+  for (int v = threadIdx.x; v < NR * LN; v += kLagThreads) {
+    const int r = v / LN, l2 = v - r * LN;
+    const int l0 = r / LN, l1 = r - l0 * LN;
+    sphi[r * RS + l2] = base[((int64_t)l0 * K + l1) * K + l2] - ref;
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double shift = corr_c * (sumq ? *sumq : 0.0);
-  const double gscale = 2.0 * Kc / G.L;   // dt/dx
-  double e = 0.0;
-  for (int64_t p = blockIdx.x * (int64_t)W + wib; p < n; p += (int64_t)gridDim.x * W) {
-    if (lane < 3) {
-      int i;
-      double t, w[LN], dw[LN];
-      lagrange_cell(x[3 * p + lane], lane == 0 ? G.c0 : (lane == 1 ? G.c1 : G.c2), G.L, Kc, i, t);
-      lagrange_weights<LN>(t, w, dw);
+  double e_acc = 0.0;
+  for (int j0 = b; j0 < e; j0 += CH) {
+    const int m = min(CH, e - j0);
+    __syncthreads();   // the node block is in place / the previous chunk is consumed
+    for (int it = threadIdx.x; it < 3 * m; it += kLagThreads) {
+      const int j = it / 3, a = it - 3 * j;
+      T w[LN], dw[LN];
+      lagrange_axis<T, LN, true>((T)rec[j0 + j].t[a], w, dw);
 #pragma unroll
       for (int l = 0; l < LN; ++l) {
-        sw[wib][lane][l] = w[l];
-        sd[wib][lane][l] = dw[l];
+        sw[j][a][l] = w[l];
+        sd[j][a][l] = dw[l];
       }
-      sc[wib][lane] = i * LN;
     }
-    __syncwarp();
-    const int b0 = sc[wib][0], b1 = sc[wib][1], b2 = sc[wib][2];
-    double a = 0.0, g0 = 0.0, g1 = 0.0, g2 = 0.0;
-    for (int r = lane; r < LN * LN; r += 32) {
-      const int l0 = r / LN, l1 = r % LN;
-      const T* row = Phi + ((int64_t)(b0 + l0) * K + (b1 + l1)) * K + b2;
-      double sv = 0.0, dv = 0.0;
+    __syncthreads();
+    for (int j = wid; j < m; j += W) {
+      T a = T(0), g0 = T(0), g1 = T(0), g2 = T(0);
+      for (int r = lane; r < NR; r += 32) {
+        const int l0 = r / LN, l1 = r - l0 * LN;
+        T sv = T(0), dv = T(0);
 #pragma unroll
-      for (int l2 = 0; l2 < LN; ++l2) {
-        const double v = (double)row[l2];
-        sv = fma(sw[wib][2][l2], v, sv);
-        dv = fma(sd[wib][2][l2], v, dv);
+        for (int l2 = 0; l2 < LN; ++l2) {
+          const T v = sphi[r * RS + l2];
+          sv = fma(sw[j][2][l2], v, sv);
+          dv = fma(sd[j][2][l2], v, dv);
+        }
+        const T w0 = sw[j][0][l0], w1 = sw[j][1][l1];
+        a = fma(w0 * w1, sv, a);
+        g0 = fma(sd[j][0][l0] * w1, sv, g0);
+        g1 = fma(w0 * sd[j][1][l1], sv, g1);
+        g2 = fma(w0 * w1, dv, g2);
       }
-      const double w0 = sw[wib][0][l0], w1 = sw[wib][1][l1];
-      a = fma(w0 * w1, sv, a);
-      g0 = fma(sd[wib][0][l0] * w1, sv, g0);
-      g1 = fma(w0 * sd[wib][1][l1], sv, g1);
-      g2 = fma(w0 * w1, dv, g2);
-    }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      a += __shfl_xor_sync(0xffffffffu, a, o);
-      g0 += __shfl_xor_sync(0xffffffffu, g0, o);
-      g1 += __shfl_xor_sync(0xffffffffu, g1, o);
-      g2 += __shfl_xor_sync(0xffffffffu, g2, o);
-    }
-    if (lane == 0) {
-      const double phi = (a - shift) * ke;
-      const double qi = q ? q[p] : 0.0;
-      if (phi_out) phi_out[p] = phi;
-      if (F_out) {
-        const double sc2 = -qi * ke * gscale;
-        F_out[3 * p + 0] = sc2 * g0;
-        F_out[3 * p + 1] = sc2 * g1;
-        F_out[3 * p + 2] = sc2 * g2;
+      for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_xor_sync(0xffffffffu, a, o);
+        g0 += __shfl_xor_sync(0xffffffffu, g0, o);
+        g1 += __shfl_xor_sync(0xffffffffu, g1, o);
+        g2 += __shfl_xor_sync(0xffffffffu, g2, o);
       }
-      e += 0.5 * qi * phi;
+      if (lane == 0) {
+        const int p = rec[j0 + j].p;
+        const double ph = ((double)a + (double)ref - shift) * ke;
+        const double qi = q ? q[p] : 0.0;
+        if (phi_out) phi_out[p] = ph;
+        if (F_out) {
+          const double sc2 = -qi * ke * gscale;
+          F_out[3 * p + 0] = sc2 * (double)g0;
+          F_out[3 * p + 1] = sc2 * (double)g1;
+          F_out[3 * p + 2] = sc2 * (double)g2;
+        }
+        e_acc += 0.5 * qi * ph;
+      }
     }
-    __syncwarp();
   }
   if (energy) {
-    const double sum = block_sum_to_thread0<double>(e);
-    if (threadIdx.x == 0 && sum != 0.0) atomicAdd(energy, sum);
+    const double s = lag_block_sum<double>(e_acc);
+    if (threadIdx.x == 0 && s != 0.0) atomicAdd(energy, s);
   }
 }
 
@@ -1017,57 +1085,80 @@ cudaError_t launch_clear(kpme_plan_t P, float* a, int64_t n, double* s0, double*
 
 namespace {
 
-template <typename T>
-cudaError_t lagrange_spread_t(kpme_plan_t P, int64_t n, const double* x, const double* q, T* Q) {
-  const MeshGeom G = geom(P);
-  const int Ln = P->p.order, Kc = P->p.K / Ln;
-  const int grid = grid_groups(P, n, 32);
-  switch (Ln) {
-    case 4: lagrange_spread_kernel<T, 4><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
-    case 6: lagrange_spread_kernel<T, 6><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
-    case 8: lagrange_spread_kernel<T, 8><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
-    case 12: lagrange_spread_kernel<T, 12><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
-    case 16: lagrange_spread_kernel<T, 16><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Q, P->d_sumq); break;
-    default: return cudaErrorInvalidValue;
+#define KPME_LAG_SWITCH(LN_CASE)  \
+  switch (Ln) {                   \
+    case 4: LN_CASE(4); break;    \
+    case 6: LN_CASE(6); break;    \
+    case 8: LN_CASE(8); break;    \
+    case 12: LN_CASE(12); break;  \
+    case 16: LN_CASE(16); break;  \
+    default: return cudaErrorInvalidValue; \
   }
+
+template <typename T>
+cudaError_t lagrange_spread_t(kpme_plan_t P, const double* q, T* Q) {
+  const int Ln = P->p.order, Kc = P->p.K / Ln, sub = lagrange_sub(P);
+  const int cells = Kc * Kc * Kc;
+  const LagRec* rec = reinterpret_cast<const LagRec*>(P->d_rec);
+#define KPME_LS(LN) \
+  lagrange_spread_cell_kernel<T, LN><<<cells, kLagThreads, 0, P->stream>>>(Kc, sub, P->d_tstart, rec, q, Q, \
+                                                                           P->d_sumq)
+  KPME_LAG_SWITCH(KPME_LS)
+#undef KPME_LS
   return cudaGetLastError();
 }
 
 template <typename T>
-cudaError_t lagrange_gather_t(kpme_plan_t P, int64_t n, const double* x, const double* q, const T* Phi, double* phi,
-                              double* F, double* energy, double c) {
-  const MeshGeom G = geom(P);
-  const int Ln = P->p.order, Kc = P->p.K / Ln;
-  const int grid = grid_groups(P, n, 32);
-  const double ke = P->p.coulomb_k;
-#define KPME_LG(LN)                                                                                              \
-  lagrange_gather_kernel<T, LN><<<grid, kThreads, 0, P->stream>>>(G, Kc, n, x, q, Phi, phi, F, energy, P->d_sumq, \
-                                                                  c, ke)
-  switch (Ln) {
-    case 4: KPME_LG(4); break;
-    case 6: KPME_LG(6); break;
-    case 8: KPME_LG(8); break;
-    case 12: KPME_LG(12); break;
-    case 16: KPME_LG(16); break;
-    default: return cudaErrorInvalidValue;
-  }
+cudaError_t lagrange_gather_t(kpme_plan_t P, const double* q, const T* Phi, double* phi, double* F, double* energy,
+                              double c) {
+  const int Ln = P->p.order, Kc = P->p.K / Ln, sub = lagrange_sub(P);
+  const int cells = Kc * Kc * Kc;
+  const LagRec* rec = reinterpret_cast<const LagRec*>(P->d_rec);
+  const double gscale = 2.0 * Kc / geom(P).L;   // dt/dx
+#define KPME_LG(LN)                                                                                            \
+  lagrange_gather_cell_kernel<T, LN><<<cells, kLagThreads, 0, P->stream>>>(Kc, sub, gscale, P->d_tstart, rec, q, \
+                                                                           Phi, phi, F, energy, P->d_sumq, c,    \
+                                                                           P->p.coulomb_k)
+  KPME_LAG_SWITCH(KPME_LG)
 #undef KPME_LG
   return cudaGetLastError();
 }
 
+#undef KPME_LAG_SWITCH
+
 }  // namespace
 
-cudaError_t launch_lagrange_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, void* Q, bool dbl) {
-  if (n <= 0) return cudaSuccess;
-  return dbl ? lagrange_spread_t<double>(P, n, x, q, (double*)Q) : lagrange_spread_t<float>(P, n, x, q, (float*)Q);
+int lagrange_sub(kpme_plan_t P) {
+  const int Kc = P->p.K / P->p.order;
+  return (int64_t)Kc * Kc * Kc >= 4096 ? 1 : kTileSub;
 }
 
-cudaError_t launch_lagrange_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
-                                   bool dbl, double* phi, double* F, double* energy, bool correct) {
+cudaError_t launch_lagrange_sort(kpme_plan_t P, int64_t n, const double* x, double* zero0, double* zero1) {
+  const int Kc = P->p.K / P->p.order, sub = lagrange_sub(P);
+  const int64_t ncnt = (int64_t)Kc * Kc * Kc * sub;
+  // counters and two float64 accumulators cleared in one launch (zero bits)
+  cudaError_t e = launch_clear(P, reinterpret_cast<float*>(P->d_tcount), ncnt, zero0, zero1);
+  if (e != cudaSuccess) return e;
+  LagRec* rec_in = reinterpret_cast<LagRec*>(P->d_rec_in);
+  const int grid = grid_for(P, n);
+  if (n > 0)
+    lagrange_count_kernel<<<grid, kThreads, 0, P->stream>>>(geom(P), Kc, sub, n, x, P->d_tcount, P->d_tslot,
+                                                            rec_in);
+  tile_scan_kernel<<<1, 1024, 0, P->stream>>>(P->d_tcount, (int)ncnt, P->d_tstart);
+  if (n > 0) tile_scatter_kernel<<<grid, kThreads, 0, P->stream>>>(n, P->d_tslot, P->d_tstart, P->d_rec_in, P->d_rec);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_lagrange_spread(kpme_plan_t P, const double* q, void* Q, bool dbl) {
+  return dbl ? lagrange_spread_t<double>(P, q, (double*)Q) : lagrange_spread_t<float>(P, q, (float*)Q);
+}
+
+cudaError_t launch_lagrange_gather(kpme_plan_t P, int64_t n, const double* q, const void* Phi, bool dbl, double* phi,
+                                   double* F, double* energy, bool correct) {
   if (n <= 0) return cudaSuccess;
   const double c = correct ? P->skp.c : 0.0;
-  return dbl ? lagrange_gather_t<double>(P, n, x, q, (const double*)Phi, phi, F, energy, c)
-             : lagrange_gather_t<float>(P, n, x, q, (const float*)Phi, phi, F, energy, c);
+  return dbl ? lagrange_gather_t<double>(P, q, (const double*)Phi, phi, F, energy, c)
+             : lagrange_gather_t<float>(P, q, (const float*)Phi, phi, F, energy, c);
 }
 
 cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q) {

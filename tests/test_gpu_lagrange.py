@@ -47,12 +47,34 @@ def test_lagrange_spread_and_gather_match_oracle(torch, Kc, Ln):
     assert rel(host(phi), phi_r) < 1e-12 and rel(host(F), F_r) < 1e-12
 
 
+@pytest.mark.parametrize("prec,Kc,Ln", [("fp64", 4, 16), ("fp64", 8, 8), ("fp64", 6, 12), ("fp32", 8, 8),
+                                         ("fp32", 16, 4)])
+def test_lagrange_crowded_boundary_and_empty_cells(torch, prec, Kc, Ln):
+    """One cell holding several chunks of particles, particles on cell corners (the upper cell owns
+    them, decided in float64 alike on both sides), and mostly empty cells."""
+    rng = np.random.default_rng(11)
+    h = L_BOX / Kc
+    crowd = rng.uniform(0.0, h, (150, 3)) + h * np.array([1.0, 2.0, 0.0])
+    corners = np.repeat(h * np.arange(Kc, dtype=np.float64)[:, None], 3, axis=1)
+    x = np.vstack([crowd, corners, rng.uniform(0.0, L_BOX, (20, 3))])
+    q = rng.choice([-1.0, 1.0], len(x))
+    plan = _plan(prec, Kc, Ln, len(x))
+    tol = 1e-12 if prec == "fp64" else 1e-4
+    Q = host(plan.spread(dev(torch, x), dev(torch, q)))
+    Qr = lg.spread(x, q, L_BOX, Kc, Ln)
+    assert np.abs(Q - Qr).max() <= tol * np.abs(Qr).max()
+    Phi = rng.standard_normal(Q.shape)
+    phi, F = plan.gather(dev(torch, x), dev(torch, q), dev(torch, Phi))
+    phi_r, F_r = lg.gather(x, q, L_BOX, Kc, Ln, Phi)
+    assert rel(host(phi), phi_r) < tol and rel(host(F), F_r) < tol
+
+
 # Equispaced nodes: at Ln = 16 the weights reach ~1e3 with cancelling signs (the Lebesgue
 # constant), which float32 node charges do not survive; the float forms are used with Ln <= 8
 # and the FP64 form carries the high orders (the paper's "relatively small orders" in double).
 @pytest.mark.parametrize("prec,Kc,Ln,tol,tol_f", [("fp64", 4, 16, 3e-9, 1e-7), ("fp64", 8, 8, 1e-12, 1e-11),
                                                  ("fp32", 8, 8, 5e-5, 2e-4), ("fp32", 16, 4, 2e-5, 1e-4),
-                                                 ("bf16x10", 8, 8, 2e-5, 1e-4), ("bf16x10", 16, 4, 2e-5, 1e-4)])
+                                                 ("bf16x10", 8, 8, 5e-6, 5e-5), ("bf16x10", 16, 4, 2e-6, 2e-5)])
 def test_lagrange_energy_forces_match_oracle(torch, prec, Kc, Ln, tol, tol_f):
     x, q = _cloud(500, 7)
     plan = _plan(prec, Kc, Ln, 500)
