@@ -2,7 +2,7 @@
 
 Only tests/, __graft_entry__.smoke() and bench.py's CPU baseline use this module.
 
-The periodic box (fractional coordinates s = (x - c_B)/L + 1/2 in [0, 1), reading Z1) is cut
+The periodic box (fractional coordinates s = (x - c_B)/L + 1/2 in [0, 1), reading R1) is cut
 into Kc^3 cubic cells (§4.1); every cell carries the product grid of Ln equispaced interpolation
 nodes per axis, t_l = -1 + 2 l/(Ln - 1) in the cell's local coordinate t in [-1, 1]
 (Eq. interp1d), so the node tensor has n = Kc Ln nodes per axis (the end nodes of neighbouring
@@ -14,7 +14,7 @@ particle's Ln^3 Lagrange weights on its own cell.  The reciprocal kernel on the 
     alpha(r) = exp(-pi^2 r^2 / xi^2) / r^2,   xi = beta L,
 
 is approximated by S_X^* A S_Y with A(g, h) = sum_m alpha(|m|) exp(2 i pi m.(y_g - y_h)) on the
-node positions y (Eq. formfinale), and the potential is phi = (1/(pi L)) H_M q (reading Z2).
+node positions y (Eq. formfinale), and the potential is phi = (1/(pi L)) H_M q (reading R2).
 With the quadrature SKP of alpha_M (Eq. quaddecompalpham) the node operator is
 
     A = sum_l w_l A_l (x) A_l (x) A_l - c_Lambda 1 1^T,

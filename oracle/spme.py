@@ -125,7 +125,7 @@ def virial_influence(K: int, n: int, box: float, beta: float) -> np.ndarray:
 
 def virial_tensor(Q, K: int, n: int, box: float, beta: float) -> np.ndarray:
     """Full reciprocal virial tensor of SPME (not given in the paper; the standard analytic
-    derivative of the mesh energy, reading Z8):
+    derivative of the mesh energy, reading R8):
 
       Pi_ab = sum_{m != 0} E(m) [delta_ab - 2 (1 + pi^2 |k|^2/beta^2) k_a k_b / |k|^2],
       E(m)  = 1/2 T(m) |S(m)|^2,  S = DFT of the charge mesh,  sum_m E(m) = E,

@@ -1,6 +1,6 @@
 // Full reciprocal virial tensor of SPME, evaluated in mode space.
 //
-// The paper gives no virial (reading Z8: the standard analytic strain derivative of the mesh
+// The paper gives no virial (reading R8: the standard analytic strain derivative of the mesh
 // energy is used):
 //   Pi_ab = sum_{m != 0} E(m) [delta_ab - 2 (1 + pi^2 |k|^2/beta^2) k_a k_b / |k|^2],
 //   E(m) = 1/2 T(m) |S(m)|^2,  T(m) = B(m) exp(-pi^2 |k|^2/beta^2) / (pi V |k|^2),  k = m / L,
