@@ -34,7 +34,8 @@ WORKLOAD_TEXT = {
     "batched": "64 independent neutral +-1 systems, N log-uniform in [2000, 50000], box 30-80 A, "
                "K in {32, 48, 64} (box/K <= 1.25 A), order 4, one graph launch per evaluation",
     "lagrange": "per-cell Lagrange form: 2e4 charges +-1, L=30 A, beta=0.1/A, modes |m|_inf <= 4, "
-                "8^3 cells of 8^3 equispaced nodes (64 per axis), quadrature SKP 1e-12, no virial",
+                "8^3 cells of 8^3 equispaced nodes (64 per axis), quadrature SKP 1e-12, no virial; node "
+                "operator in mode space (the terms' sum as one diagonal)",
 }
 DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16": "bf16", "bf16x3": "bf16",
          "bf16x6": "bf16", "bf16x10": "bf16"}
@@ -132,7 +133,7 @@ def _system(name):
 def _oracle_eval(s):
     """The oracle's evaluation of workload s and its plan-time build (returns (build_s, eval))."""
     t0 = time.perf_counter()
-    if s.meta.get("interp") == "lagrange":
+    if s.meta.get("interp", "bspline").startswith("lagrange"):
         from oracle import lagrange as lg
         Kc, M = s.meta["cells"], s.meta["modes"]
         fac = lg.sinc_factors(Kc, s.order, s.box, s.beta, M, s.skp_tol)
@@ -321,8 +322,8 @@ def main(argv=None):
 
     s = _system(args.workload)
     stream = torch.cuda.current_stream()
-    lag = s.meta.get("interp") == "lagrange"
-    extra = dict(interp="lagrange", modes=s.meta["modes"], skp_method="sinc") if lag else {}
+    lag = s.meta.get("interp", "bspline").startswith("lagrange")
+    extra = dict(interp=s.meta["interp"], modes=s.meta["modes"], skp_method="sinc") if lag else {}
     plan = Plan(s.box, s.K, s.order, s.beta, precision=args.precision, skp_tol=s.skp_tol, max_n=s.n, **extra)
     vir = not lag   # the per-cell form has no virial
     R, skp_err = plan.build_skp()
@@ -401,6 +402,16 @@ def main(argv=None):
             "ms_per_launch": per_launch_ms}
     if not tensor:
         roof = None
+    if lag and s.meta["interp"] == "lagrange_modes":
+        # the node operator in mode space: float64 transforms on the CUDA cores
+        fp64_peak = 1250.0   # GFLOP/s, nominal dense FP64 of a GB300
+        ach = mp_flops / (skp_ms * 1e-3) / 1e9 if skp_ms > 0 else None
+        roof = {"bound": "alu", "kernel": "modes_axis_kernel (mode-space node operator, float64: three forward "
+                                          "and three backward transforms, the diagonal fused)",
+                "achieved": ach, "peak": fp64_peak, "unit": "GFLOP/s", "frac": (ach / fp64_peak) if ach else None,
+                "traffic": None, "peak_source": "nominal FP64 rate (1.25 TFLOP/s), no measured FP64 peak",
+                "flops_per_step": mp_flops, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
+                "ms_per_launch": per_launch_ms}
     # spreading and gathering against HBM: algorithmic bytes per evaluation (positions and
     # charges in float64, the float32 mesh written or read once, potentials and forces out)
     hbm = peaks.get("hbm_gbs", 6800.0)
@@ -476,6 +487,29 @@ def main(argv=None):
         vt = {"ms_per_call": a.elapsed_time(b) / 10, "trace": float(Pi.trace().item()),
               "note": "kpme_virial_tensor: spread, three real-DFT mode products, float64 mode-space reduction"}
 
+    # the per-cell form's quadrature applied term by term (dense factors on the mode-product
+    # kernels of the precision), the paper's Algorithm 4 loop, beside the mode-space form
+    terms = None
+    if lag and s.meta["interp"] == "lagrange_modes" and rank == 0:
+        tp = Plan(s.box, s.K, s.order, s.beta, precision=args.precision, skp_tol=s.skp_tol, max_n=s.n,
+                  interp="lagrange", modes=s.meta["modes"], skp_method="sinc")
+        tp.build_skp()
+        if not args.no_autotune:
+            tp.autotune(x, q)
+        for _ in range(3):
+            tp.energy_forces(x, q, forces=True, dEdq=True, out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            tp.energy_forces(x, q, forces=True, dEdq=True, out=out)
+        b.record(stream)
+        b.synchronize()
+        t_ms = a.elapsed_time(b) / args.steps
+        terms = {"value": 1e3 / t_ms, "unit": "evals/s", "ms_per_step": t_ms,
+                 "note": "interp=lagrange: R dense Kronecker terms on the mode-product kernels (L2 not flushed)"}
+        tp.close()
+
     # FP64 GPU form at the same SKP (the baseline the tensor path must beat)
     fp64 = None
     if args.fp64_steps > 0:
@@ -505,7 +539,7 @@ def main(argv=None):
             "tflops_useful": useful / (ms_step * 1e-3) / 1e12,
             "roofline": roof, "particle_kernels": part, "virial_tensor": vt, "e2e": e2e,
             "gpu_launches": int(round(launches_per_step * args.steps)),
-            "fp64_form": fp64, "clocks": clocks, "cpu_baseline": cb,
+            "fp64_form": fp64, "skp_terms_form": terms, "clocks": clocks, "cpu_baseline": cb,
             "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
         }
         print(json.dumps(line), flush=True)

@@ -99,10 +99,17 @@ typedef enum {
 typedef enum {
   KPME_INTERP_BSPLINE = 0,    /* cardinal B-splines of order `order` on one periodic K^3 mesh
                                  (smooth PME; the path of the benchmarks)                    */
-  KPME_INTERP_LAGRANGE = 1    /* the paper's per-cell form (§2.2, §4.1, Algorithm 4):
+  KPME_INTERP_LAGRANGE = 1,   /* the paper's per-cell form (§2.2, §4.1, Algorithm 4):
                                  K / order cells per axis, `order` equispaced Lagrange nodes
                                  per cell and axis (K nodes per axis), modes |m|_inf <= modes,
-                                 quadrature SKP of alpha_M with dense axis factors           */
+                                 quadrature SKP of alpha_M with dense axis factors applied
+                                 term by term (the mode-product kernels of the precision)    */
+  KPME_INTERP_LAGRANGE_MODES = 2  /* the same form and quadrature, the node operator applied
+                                 in mode space: the terms share their Fourier factors
+                                 (Eq. VtV, V[lambda] = omega^(1/3) sqrt(alpha_lambda) W), so
+                                 the sum over lambda is one diagonal on the (2M+1)^3 real
+                                 modes between three forward and three backward transforms
+                                 of the node tensor (float64 arithmetic at every precision) */
 } kpme_interp_t;
 
 typedef struct {
@@ -117,14 +124,14 @@ typedef struct {
   int64_t max_n;      /* largest particle count of any call (scratch capacity)        */
   double coulomb_k;   /* scale of potentials, energies and forces (1 = Gaussian)      */
   int interp;         /* interpolation, a kpme_interp_t; 0 = B-spline                 */
-  int modes;          /* KPME_INTERP_LAGRANGE: largest mode M per axis (|m|_inf <= M) */
+  int modes;          /* per-cell forms: largest mode M per axis (|m|_inf <= M)       */
 } kpme_params_t;
 
 /* Fill *p with defaults (centre 0, radius 1, beta 0.35, order 4, K 32, tol 1e-8,
  * SVD, KPME_FP32, max_n 1<<20, coulomb_k 1, B-spline interpolation).  Never fails for
  * p != NULL.
  *
- * KPME_INTERP_LAGRANGE plans: order = Ln nodes per cell (4, 6, 8, 12 or 16), K = Kc Ln with
+ * KPME_INTERP_LAGRANGE(_MODES) plans: order = Ln nodes per cell (4, 6, 8, 12 or 16), K = Kc Ln with
  * Kc >= 1 cells per axis, 1 <= modes <= 64, skp_method = KPME_SKP_SINC (the quadrature SKP of
  * Eq. quaddecompalpham over the mode cube, built by kpme_build_skp; kpme_set_skp / kpme_get_skp,
  * the virial and kpme_virial_tensor are not available for them).  The potential is
@@ -324,7 +331,8 @@ typedef struct {
   double skp_rel_err;
   int64_t max_n;
   int64_t scratch_bytes;      /* device bytes owned by the plan                 */
-  double flops_useful;        /* 6 R K^4 per evaluation                         */
+  double flops_useful;        /* 6 R K^4 per evaluation (mode-space per-cell
+                                 form: its transforms, as flops_executed)       */
   double flops_executed;      /* mode-product flops actually issued per eval    */
   int kernels_per_eval;       /* kernel launches of one kpme_energy_forces      */
 } kpme_info_t;

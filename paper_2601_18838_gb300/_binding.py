@@ -37,7 +37,7 @@ class Params(C.Structure):
     ]
 
 
-INTERP = {"bspline": 0, "lagrange": 1}
+INTERP = {"bspline": 0, "lagrange": 1, "lagrange_modes": 2}
 
 
 class Tune(C.Structure):
@@ -153,7 +153,8 @@ class Plan:
                  max_n: int = 1 << 20, coulomb_k: float = 1.0, stream=None, interp: str = "bspline",
                  modes: int = 0):
         """interp="lagrange": the per-cell form (K / order cells per axis, `order` Lagrange nodes
-        per cell, modes |m|_inf <= `modes`); it needs skp_method="sinc"."""
+        per cell, modes |m|_inf <= `modes`); it needs skp_method="sinc".  interp="lagrange_modes":
+        the same form with the node operator applied in mode space (one diagonal)."""
         import torch
         L = lib()
         p = Params()
@@ -259,7 +260,7 @@ class Plan:
 
     def skp_c(self) -> float:
         """The m = 0 correction constant c of the installed SKP (0 for the SVD form)."""
-        if getattr(self, "interp", "bspline") == "lagrange":   # dense factors: sizes and c only
+        if getattr(self, "interp", "bspline") != "bspline":   # dense factors: sizes and c only
             r0, R, c = C.c_int(), C.c_int(), C.c_double()
             self._call("kpme_get_skp", C.byref(r0), C.byref(R), None, None, None, None, None, None, C.byref(c))
             return float(c.value)

@@ -21,7 +21,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libkpme.so")
-SOURCES = ["api.cu", "particles.cu", "skp_build.cu", "gemm_simt.cu", "gemm_tc.cu", "gemm_oz.cu", "gemm_ozt.cu", "gemm_ozf.cu", "noalloc.cu", "batch.cu", "tune.cu", "virial_tensor.cu"]
+SOURCES = ["api.cu", "particles.cu", "skp_build.cu", "gemm_simt.cu", "gemm_tc.cu", "gemm_oz.cu", "gemm_ozt.cu", "gemm_ozf.cu", "noalloc.cu", "batch.cu", "tune.cu", "virial_tensor.cu", "lagrange_modes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -102,6 +102,9 @@ void release_skp_buffers(kpme_plan_t P) {
   drop(P->d_Qs);
   drop(P->d_Y);
   drop(P->d_Z);
+  dfree(P->d_lmU);
+  dfree(P->d_lmD);
+  dfree(P->d_lmT);
   dfree(P->d_Qsl);
   dfree(P->d_Ysl);
   dfree(P->d_rmZ);
@@ -288,6 +291,20 @@ kpme_status_t install_skp(kpme_plan_t P) {
   release_skp_buffers(P);
   const SkpHost& S = P->skp;
   if (!S.valid) return KPME_OK;
+  if (lagrange_modes(P)) {   // Fourier rows, the diagonal and the transforms' scratch
+    const int K = P->p.K, r = 2 * P->p.modes + 1;
+    kpme_status_t s2;
+    if ((s2 = dalloc(P, (void**)&P->d_lmU, S.modal_U.size() * sizeof(double))) != KPME_OK) return s2;
+    if ((s2 = dalloc(P, (void**)&P->d_lmD, S.modal_D.size() * sizeof(double))) != KPME_OK) return s2;
+    const size_t nt = (size_t)r * K * K + (size_t)r * r * K + (size_t)r * r * r;
+    if ((s2 = dalloc(P, (void**)&P->d_lmT, nt * sizeof(double))) != KPME_OK) return s2;
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_lmU, S.modal_U.data(), S.modal_U.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, P->stream));
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_lmD, S.modal_D.data(), S.modal_D.size() * sizeof(double),
+                                     cudaMemcpyHostToDevice, P->stream));
+    KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
+    return KPME_OK;
+  }
   const int K = P->p.K, r0 = S.r0, R = S.R;
   const int64_t k3 = K3(P);
   const PrecInfo& pi = P->prec;
@@ -563,6 +580,11 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
   const int64_t k3 = K3(P);
   const PrecInfo& pi = P->prec;
   const SkpHost& S = P->skp;
+  if (lagrange_modes(P)) {
+    StepScope sc(P, STEP_SKP1, 1);
+    KPME_CUDA_TRY(P, launch_lagrange_modes(P, Q.p, Q.dbl, Phi, pi.fp64));
+    return KPME_OK;
+  }
   if (!pi.tensor) {
     const bool dbl = pi.fp64;
     const void* Qin = Q.p;
@@ -710,7 +732,10 @@ kpme_status_t virial_finish(kpme_plan_t P, const double* energy, double* out) {
 }
 
 bool tiled(kpme_plan_t P) { return !P->prec.fp64 && P->tile > 0 && !P->no_sort && !lagrange(P); }
-bool lagrange(kpme_plan_t P) { return P->p.interp == KPME_INTERP_LAGRANGE; }
+bool lagrange(kpme_plan_t P) {
+  return P->p.interp == KPME_INTERP_LAGRANGE || P->p.interp == KPME_INTERP_LAGRANGE_MODES;
+}
+bool lagrange_modes(kpme_plan_t P) { return P->p.interp == KPME_INTERP_LAGRANGE_MODES; }
 
 // Charge mesh of n particles: cell sort + tile-staged float32 spreading, float32 spreading
 // with no sort (lane groups, float32 atomics), or float64 atomics for the FP64 form.
@@ -823,7 +848,7 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   if (!params || !out) return KPME_ERR_INVALID_ARG;
   *out = nullptr;
   const kpme_params_t& p = *params;
-  const bool lag = p.interp == KPME_INTERP_LAGRANGE;
+  const bool lag = p.interp == KPME_INTERP_LAGRANGE || p.interp == KPME_INTERP_LAGRANGE_MODES;
   const bool geometry =
       lag ? ((p.order == 4 || p.order == 6 || p.order == 8 || p.order == 12 || p.order == 16) && p.K % p.order == 0 &&
              p.K >= p.order && p.K <= 512 && p.modes >= 1 && p.modes <= 64 && p.skp_method == KPME_SKP_SINC)
@@ -1221,6 +1246,10 @@ kpme_status_t kpme_get_info(kpme_plan_t P, kpme_info_t* info) {
   const double mp = 2.0 * K * K * K * K;   // one mode product of one term
   const double per_eval = (info->r0 + 2.0 * info->R) * mp;
   info->flops_executed = per_eval * (P->prec.tensor ? P->prec.n_products : 1);
+  if (lagrange_modes(P) && P->skp.valid) {   // three forward and three backward transforms
+    const double r = 2.0 * P->p.modes + 1.0;
+    info->flops_useful = info->flops_executed = 4.0 * (r * K * K * K + r * r * K * K + r * r * r * K) + r * r * r;
+  }
   int kernels = 1 /*spread*/ + 1 /*gather*/ + 1 /*stage 1*/ + 2 * (int)P->groups.size();
   if (P->prec.tensor) kernels += 1;
   info->kernels_per_eval = kernels;

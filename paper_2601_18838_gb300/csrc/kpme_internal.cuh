@@ -57,6 +57,9 @@ struct SkpHost {
   std::vector<int> outer_of;               // term -> outer index
   std::vector<double> gen3, gen2, gen1;    // r0 x K, R x K, R x K (dense: r0, R, R x K x K)
   bool dense = false;                      // full factor matrices instead of circulant generators
+  // mode-space form of the per-cell operator: real Fourier rows U ((2M+1) x K: 1, then cos and
+  // sin of 2 pi m y per m) and the diagonal on the (2M+1)^3 real modes
+  std::vector<double> modal_U, modal_D;
   std::vector<double> sig_outer, sig_inner;
   double c = 0.0;
   double rel_err = 0.0;
@@ -118,6 +121,9 @@ struct kpme_plan_s {
   void* d_facW = nullptr;          // real DFT matrix (cosine / sine rows), K x K, plan's mesh format
   double* d_bmod = nullptr;        // B-spline moduli |b(m)|^2, m = 0..K/2
   double* d_vt = nullptr;          // virial-tensor sums (E and six components)
+  double* d_lmU = nullptr;         // mode-space per-cell form: Fourier rows, diagonal,
+  double* d_lmD = nullptr;         //   and the transforms' intermediates (r n^2, r^2 n, r^3;
+  double* d_lmT = nullptr;         //   r = 2M + 1) in one allocation
   void* d_Qs = nullptr;            // tensor path: sliced Q
   void* d_Y = nullptr;             // stage-1 output (r0 tensors)
   void* d_Z = nullptr;             // stage-2 output (one term group)
@@ -200,7 +206,11 @@ kpme_status_t sinc_search(kpme_plan_t P, const std::vector<double>& args, double
                           double& best);
 cudaError_t launch_materialize_dense(kpme_plan_t P, const double* d_dense, const double* d_gmax, int count, void* dst,
                                      int slices, int kind);
-bool lagrange(kpme_plan_t P);   // per-cell Lagrange interpolation (KPME_INTERP_LAGRANGE)
+bool lagrange(kpme_plan_t P);         // per-cell Lagrange interpolation (either form)
+bool lagrange_modes(kpme_plan_t P);   // its node operator applied in mode space
+// Phi = U^T (x) U^T (x) U^T diag(D) U (x) U (x) U Q in float64 (lagrange_modes.cu); Q and Phi
+// are float64 when dbl, else float32
+cudaError_t launch_lagrange_modes(kpme_plan_t P, const void* Q, bool qdbl, void* Phi, bool pdbl);
 // per-cell form: counting sort of n particles by cell into the plan's records (also clears the
 // float64 accumulators zero0 and zero1 when given), then the per-cell spreading (node charges and
 // their sum into sumq) and gathering over the sorted records

@@ -678,6 +678,52 @@ kpme_status_t build_skp_lagrange(kpme_plan_t P, SkpHost& out) {
       const double t = -1.0 + 2.0 * l / (Ln - 1);
       y[i * Ln + l] = (i + 0.5 * (1.0 + t)) / Kc;
     }
+  if (lagrange_modes(P)) {   // the sum over the terms as one diagonal on the real modes
+    const int r = 2 * M + 1;
+    out = SkpHost();
+    out.dense = true;
+    out.modal_U.assign((size_t)r * K, 0.0);
+    for (int g = 0; g < K; ++g) {
+      out.modal_U[g] = 1.0;
+      for (int m = 1; m <= M; ++m) {
+        out.modal_U[(size_t)(2 * m - 1) * K + g] = std::cos(2.0 * M_PI * m * y[g]);
+        out.modal_U[(size_t)(2 * m) * K + g] = std::sin(2.0 * M_PI * m * y[g]);
+      }
+    }
+    std::vector<double> wl(R), lam(R), dsq(3 * M * M + 1, 0.0);
+    for (int t = 0; t < R; ++t) {
+      const int l = t - nq;
+      wl[t] = h / (1.0 + std::exp(-l * h));
+      lam[t] = std::log1p(std::exp(l * h));
+    }
+    for (int s2 = 1; s2 <= 3 * M * M; ++s2) {   // pre sum_l w_l prod_j a_l(m_j), by |m|^2
+      double acc = 0.0;
+      for (int t = 0; t < R; ++t) acc += wl[t] * std::exp(-(lam[t] + M_PI * M_PI / xi2) * s2);
+      dsq[s2] = pre * acc;
+    }
+    // real mode mu: 0 -> m = 0; 2m - 1, 2m -> cos, sin of mode m, the +-m pair folded (kappa 2)
+    auto mo = [](int mu) { return (mu + 1) / 2; };
+    auto kap = [](int mu) { return mu == 0 ? 1.0 : 2.0; };
+    out.modal_D.resize((size_t)r * r * r);
+    for (int a = 0; a < r; ++a)
+      for (int b = 0; b < r; ++b)
+        for (int c = 0; c < r; ++c) {
+          const int s2 = mo(a) * mo(a) + mo(b) * mo(b) + mo(c) * mo(c);
+          out.modal_D[((size_t)a * r + b) * r + c] = s2 == 0 ? 0.0 : dsq[s2] * kap(a) * kap(b) * kap(c);
+        }
+    out.r0 = R;
+    out.R = R;
+    out.r1.assign(R, 1);
+    out.outer_of.resize(R);
+    std::iota(out.outer_of.begin(), out.outer_of.end(), 0);
+    out.sig_outer.resize(R);
+    for (int t = 0; t < R; ++t) out.sig_outer[t] = pre * wl[t];
+    out.sig_inner.assign(R, 1.0);
+    out.c = 0.0;   // the diagonal has no m = 0 entry: the correction term is inside it
+    out.rel_err = best;
+    out.valid = true;
+    return KPME_OK;
+  }
   const size_t KK = (size_t)K * K;
   std::vector<double> cs((size_t)M * KK);   // cos(2 pi m (y_g - y_h)), m = 1..M
   for (int m = 1; m <= M; ++m)

@@ -142,10 +142,11 @@ def large(n: int = 1_000_000) -> System:
 
 def lagrange(n: int = 20_000) -> System:
     """The per-cell Lagrange form (§4.1): 2e4 charges +-1 in a 30 A box, beta = 0.1/A (xi = 3),
-    modes |m|_inf <= 4, 8 cells of 8 equispaced nodes per axis (64 nodes), quadrature SKP 1e-12."""
+    modes |m|_inf <= 4, 8 cells of 8 equispaced nodes per axis (64 nodes), quadrature SKP 1e-12,
+    node operator in mode space."""
     s = uniform_system("lagrange", 5, n, 30.0, 64, 8, skp_tol=1e-12)
     s.beta = 0.1
-    s.meta = {"interp": "lagrange", "modes": 4, "cells": 8}
+    s.meta = {"interp": "lagrange_modes", "modes": 4, "cells": 8}
     return s
 
 

@@ -128,3 +128,50 @@ def test_lagrange_autotune_keeps_results(torch):
     out = plan.energy_forces(xd, qd)
     ref = lg.reciprocal(x, q, L_BOX, BETA, 8, 8, M)
     assert rel(host(out["dEdq"]), ref["phi"]) < 2e-5 and rel(host(out["forces"]), ref["F"]) < 1e-4
+
+
+def _plan_modes(prec, Kc, Ln, max_n, tol=1e-12):
+    from paper_2601_18838_gb300 import Plan
+    return Plan(L_BOX, Kc * Ln, Ln, BETA, precision=prec, skp_tol=tol, skp_method="sinc", max_n=max_n,
+                interp="lagrange_modes", modes=M)
+
+
+# The mode-space form evaluates the same quadrature operator (its sum over the terms collapsed
+# into one diagonal) in float64; the float forms round only the node charges and potentials.
+@pytest.mark.parametrize("prec,Kc,Ln,tol,tol_f", [("fp64", 4, 16, 3e-9, 1e-7), ("fp64", 8, 8, 1e-12, 1e-11),
+                                                 ("fp64", 6, 12, 1e-10, 1e-9), ("fp32", 8, 8, 2e-6, 3e-5),
+                                                 ("bf16x10", 8, 8, 2e-6, 3e-5), ("bf16x10", 16, 4, 2e-6, 3e-5)])
+def test_lagrange_modes_match_oracle(torch, prec, Kc, Ln, tol, tol_f):
+    x, q = _cloud(500, 7)
+    plan = _plan_modes(prec, Kc, Ln, 500)
+    R, err = plan.build_skp()
+    assert R > 0 and err <= 1e-12 and plan.skp_c() == 0.0
+    out = plan.energy_forces(dev(torch, x), dev(torch, q))
+    ref = lg.reciprocal(x, q, L_BOX, BETA, Kc, Ln, M)            # exact node operator
+    e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
+    e_E = abs(out["energy"].item() - ref["E"]) / abs(ref["E"])
+    print(f"lagrange_modes {prec} Kc={Kc} Ln={Ln}: R={R} phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e}")
+    assert e_phi < tol and e_f < tol_f and e_E < tol
+    if prec == "fp64" and Ln == 8:
+        # the same quadrature summed term by term (the oracle's Algorithm 4 loop)
+        sk = lg.reciprocal(x, q, L_BOX, BETA, Kc, Ln, M, method="sinc", tol=1e-12)
+        assert rel(host(out["dEdq"]), sk["phi"]) < 1e-13 and rel(host(out["forces"]), sk["F"]) < 1e-12
+
+
+def test_lagrange_modes_non_neutral_autotune_and_potential(torch):
+    x, q = _cloud(300, 4)
+    q = q + 0.25                                                  # the m = 0 mode is not in the cube sum
+    plan = _plan_modes("fp64", 4, 16, 300)
+    plan.build_skp()
+    xd, qd = dev(torch, x), dev(torch, q)
+    plan.autotune(xd, qd)
+    out = plan.energy_forces(xd, qd)
+    ref = lg.reciprocal(x, q, L_BOX, BETA, 4, 16, M)
+    assert rel(host(out["dEdq"]), ref["phi"]) < 3e-9
+    # potentials at other points (a second cell sort of the targets)
+    t = np.random.default_rng(5).uniform(0.0, L_BOX, (77, 3))
+    p = plan.potential(xd, qd, dev(torch, t))
+    Qn = lg.spread(x, q, L_BOX, 4, 16)
+    Phi = lg.apply_exact(Qn, 4, 16, L_BOX, BETA, M)
+    p_r, _ = lg.gather(t, np.zeros(len(t)), L_BOX, 4, 16, Phi)
+    assert rel(host(p), p_r) < 3e-9
