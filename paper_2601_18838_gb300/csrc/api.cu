@@ -105,6 +105,8 @@ void release_skp_buffers(kpme_plan_t P) {
   dfree(P->d_lmU);
   dfree(P->d_lmD);
   dfree(P->d_lmT);
+  dfree(P->d_lmU2);
+  dfree(P->d_lmD2);
   dfree(P->d_Qsl);
   dfree(P->d_Ysl);
   dfree(P->d_rmZ);
@@ -296,12 +298,28 @@ kpme_status_t install_skp(kpme_plan_t P) {
     kpme_status_t s2;
     if ((s2 = dalloc(P, (void**)&P->d_lmU, S.modal_U.size() * sizeof(double))) != KPME_OK) return s2;
     if ((s2 = dalloc(P, (void**)&P->d_lmD, S.modal_D.size() * sizeof(double))) != KPME_OK) return s2;
-    const size_t nt = (size_t)r * K * K + (size_t)r * r * K + (size_t)r * r * r;
+    const size_t nt = (size_t)r * K * K + 2 * (size_t)r * r * K + (size_t)r * r * r;
     if ((s2 = dalloc(P, (void**)&P->d_lmT, nt * sizeof(double))) != KPME_OK) return s2;
     KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_lmU, S.modal_U.data(), S.modal_U.size() * sizeof(double),
                                      cudaMemcpyHostToDevice, P->stream));
     KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_lmD, S.modal_D.data(), S.modal_D.size() * sizeof(double),
                                      cudaMemcpyHostToDevice, P->stream));
+    // double-float pairs (hi = float32 rounding, lo = float32 rounding of the rest)
+    auto pairs = [](const std::vector<double>& v) {
+      std::vector<float2> o(v.size());
+      for (size_t i = 0; i < v.size(); ++i) {
+        const float hi = (float)v[i];
+        o[i] = make_float2(hi, (float)(v[i] - (double)hi));
+      }
+      return o;
+    };
+    const std::vector<float2> U2 = pairs(S.modal_U), D2 = pairs(S.modal_D);
+    if ((s2 = dalloc(P, &P->d_lmU2, U2.size() * sizeof(float2))) != KPME_OK) return s2;
+    if ((s2 = dalloc(P, &P->d_lmD2, D2.size() * sizeof(float2))) != KPME_OK) return s2;
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_lmU2, U2.data(), U2.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                                     P->stream));
+    KPME_CUDA_TRY(P, cudaMemcpyAsync(P->d_lmD2, D2.data(), D2.size() * sizeof(float2), cudaMemcpyHostToDevice,
+                                     P->stream));
     KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
     return KPME_OK;
   }
@@ -761,7 +779,7 @@ kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const doubl
   // the float32 mesh, the charge sum and the caller's accumulator in one launch
   KPME_CUDA_TRY(P, launch_clear(P, P->d_Qf, k3, P->d_sumq, also_zero));
   if (!tiled(P)) {
-    KPME_CUDA_TRY(P, launch_spread_nosort(P, n, x, q, P->d_Qf));
+    KPME_CUDA_TRY(P, launch_spread_nosort(P, n, x, q, P->d_Qf, P->d_coords));
     out = {P->d_Qf, false};
     return KPME_OK;
   }
@@ -783,7 +801,8 @@ kpme_status_t gather_mesh(kpme_plan_t P, int64_t n, const double* x, const doubl
   }
   if (!tiled(P)) {
     if (!correct) KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_sumq, 0, sizeof(double), P->stream));
-    KPME_CUDA_TRY(P, launch_gather(P, n, x, q, P->d_Phi, phi, F, energy, 1.0));
+    // the same positions as the spreading of this call: its mesh coordinates are reused
+    KPME_CUDA_TRY(P, launch_gather(P, n, x, q, P->d_Phi, phi, F, energy, 1.0, sorted ? P->d_coords : nullptr));
     return KPME_OK;
   }
   if (!sorted) KPME_CUDA_TRY(P, launch_sort(P, n, x, nullptr, nullptr));
@@ -918,7 +937,11 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
     if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_rec_in, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_rec, 2 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
-  } else if (choose_tile(p.K, p.order) > 0) {
+  } else {   // mesh coordinates shared by the no-sort spreading and gathering of one call
+    const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
+    if ((st = dalloc(P, (void**)&P->d_coords, 3 * nmax * sizeof(float4))) != KPME_OK) return fail(st);
+  }
+  if (!lag && choose_tile(p.K, p.order) > 0) {
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
     if ((st = set_tile(P, choose_tile(p.K, p.order))) != KPME_OK) return fail(st);
     if ((st = dalloc(P, (void**)&P->d_tslot, nmax * sizeof(int2))) != KPME_OK) return fail(st);
@@ -954,6 +977,7 @@ void kpme_destroy(kpme_plan_t P) {
   dfree(P->d_tslot);
   dfree(P->d_rec_in);
   dfree(P->d_rec);
+  dfree(P->d_coords);
   if (P->d_status) cudaFreeHost(P->d_status);
   for (auto& pe : P->pending) {
     cudaEventDestroy(pe.second.first);

@@ -103,6 +103,9 @@ struct kpme_plan_s {
   int2* d_tslot = nullptr;         // (tile, slot) per particle
   float4* d_rec_in = nullptr;      // per-particle records (cell, index, offsets), input order
   float4* d_rec = nullptr;         // the same records sorted by tile
+  float4* d_coords = nullptr;      // per particle and axis: mesh index and the double-float
+                                   // fraction (g, f hi, f lo) of the last no-sort spreading,
+                                   // reused by the gathering of the same call
   // meshes, K^3 each: Q float64 (FP64 form, or untiled fallback) / Qf float32, Phi float32
   // (float64 for FP64)
   double* d_Q = nullptr;
@@ -122,8 +125,10 @@ struct kpme_plan_s {
   double* d_bmod = nullptr;        // B-spline moduli |b(m)|^2, m = 0..K/2
   double* d_vt = nullptr;          // virial-tensor sums (E and six components)
   double* d_lmU = nullptr;         // mode-space per-cell form: Fourier rows, diagonal,
-  double* d_lmD = nullptr;         //   and the transforms' intermediates (r n^2, r^2 n, r^3;
-  double* d_lmT = nullptr;         //   r = 2M + 1) in one allocation
+  double* d_lmD = nullptr;         //   and the transforms' intermediates (r n^2, r^2 n, r^3,
+  double* d_lmT = nullptr;         //   r^2 n; r = 2M + 1) in one allocation
+  void* d_lmU2 = nullptr;          // the rows and the diagonal as double-float pairs (float2)
+  void* d_lmD2 = nullptr;
   void* d_Qs = nullptr;            // tensor path: sliced Q
   void* d_Y = nullptr;             // stage-1 output (r0 tensors)
   void* d_Z = nullptr;             // stage-2 output (one term group)
@@ -177,8 +182,10 @@ namespace kpme {
 
 // particles.cu
 cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, double* Q);
+// coords (may be NULL): the mesh coordinates of these positions from launch_spread_nosort
 cudaError_t launch_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
-                          double* phi, double* F, double* energy, double scale_phi_extra);
+                          double* phi, double* F, double* energy, double scale_phi_extra,
+                          const float4* coords = nullptr);
 cudaError_t launch_dot(kpme_plan_t P, const void* a, const void* b, int64_t count, double* out);
 cudaError_t launch_virial_finalize(kpme_plan_t P, const double* energy, const double* qpsi,
                                    double t0, double coef, double* virial);
@@ -194,7 +201,9 @@ kpme_status_t install_skp(kpme_plan_t P);
 constexpr int kTileCounters = 8;   // counters per tile of the cell sort (sub-ranges per tile)
 cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double* q, double* sumq);
 cudaError_t launch_spread_tiled(kpme_plan_t P, int64_t n, const double* q, float* Q);
-cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q);
+// coords (may be NULL): receives each particle's mesh coordinates (3 float4 per particle)
+cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q,
+                                 float4* coords = nullptr);
 cudaError_t launch_gather_tiled(kpme_plan_t P, int64_t n, const double* q, const float* Phi, double* phi, double* F,
                                 double* energy, bool correct);
 

@@ -2,6 +2,7 @@
 // potentials / forces (the B-spline form of the interpolation matrices S_Y and S_X^* of
 // §2.2, Eq. interpkrons, applied as in Algorithm 4), plus the float64 reductions.
 #include "kpme_internal.cuh"
+#include "df.cuh"
 
 namespace kpme {
 namespace {
@@ -113,7 +114,7 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(MeshGeom G, int64_t n,
                                                           const double* __restrict__ q, const T* __restrict__ Phi,
                                                           double* __restrict__ phi_out, double* __restrict__ F_out,
                                                           double* __restrict__ energy, const double* __restrict__ sumq,
-                                                          double corr_c, double ke) {
+                                                          double corr_c, double ke, const float4* __restrict__ coords) {
   const int K = G.K;
   const double shift = corr_c * (sumq ? *sumq : 0.0);
   const T gscale = (T)((double)K / G.L);
@@ -123,9 +124,17 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(MeshGeom G, int64_t n,
     T w[3][N], dw[3][N];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double f;
-      mesh_coord(x[3 * i + a], a == 0 ? G.c0 : (a == 1 ? G.c1 : G.c2), G.L, K, g[a], f);
-      bspline<T, N>((T)f, w[a], dw[a]);
+      T ft;
+      if (coords) {   // the spreading's coordinates: no float64 work here
+        const float4 c = coords[3 * i + a];
+        g[a] = __float_as_int(c.x);
+        ft = sizeof(T) == sizeof(float) ? (T)c.y : (T)((double)c.y + (double)c.z);
+      } else {
+        double f;
+        mesh_coord(x[3 * i + a], a == 0 ? G.c0 : (a == 1 ? G.c1 : G.c2), G.L, K, g[a], f);
+        ft = (T)f;
+      }
+      bspline<T, N>(ft, w[a], dw[a]);
     }
     T p = 0, g0 = 0, g1 = 0, g2 = 0;
 #pragma unroll
@@ -227,14 +236,14 @@ cudaError_t spread_t(kpme_plan_t P, int64_t n, const double* x, const double* q,
 
 template <typename T>
 cudaError_t gather_t(kpme_plan_t P, int64_t n, const double* x, const double* q, const T* Phi, double* phi,
-                     double* F, double* energy, double ke) {
+                     double* F, double* energy, double ke, const float4* coords) {
   const int grid = grid_for(P, n);
   const MeshGeom G = geom(P);
   const double c = P->skp.c;
   switch (P->p.order) {
-    case 4: gather_kernel<T, 4><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Phi, phi, F, energy, P->d_sumq, c, ke); break;
-    case 6: gather_kernel<T, 6><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Phi, phi, F, energy, P->d_sumq, c, ke); break;
-    case 8: gather_kernel<T, 8><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Phi, phi, F, energy, P->d_sumq, c, ke); break;
+    case 4: gather_kernel<T, 4><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Phi, phi, F, energy, P->d_sumq, c, ke, coords); break;
+    case 6: gather_kernel<T, 6><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Phi, phi, F, energy, P->d_sumq, c, ke, coords); break;
+    case 8: gather_kernel<T, 8><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Phi, phi, F, energy, P->d_sumq, c, ke, coords); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
@@ -249,11 +258,11 @@ cudaError_t launch_spread(kpme_plan_t P, int64_t n, const double* x, const doubl
 }
 
 cudaError_t launch_gather(kpme_plan_t P, int64_t n, const double* x, const double* q, const void* Phi,
-                          double* phi, double* F, double* energy, double scale) {
+                          double* phi, double* F, double* energy, double scale, const float4* coords) {
   if (n <= 0) return cudaSuccess;
   const double ke = P->p.coulomb_k * scale;
-  if (P->prec.fp64) return gather_t<double>(P, n, x, q, (const double*)Phi, phi, F, energy, ke);
-  return gather_t<float>(P, n, x, q, (const float*)Phi, phi, F, energy, ke);
+  if (P->prec.fp64) return gather_t<double>(P, n, x, q, (const double*)Phi, phi, F, energy, ke, nullptr);
+  return gather_t<float>(P, n, x, q, (const float*)Phi, phi, F, energy, ke, coords);
 }
 
 namespace {
@@ -434,37 +443,6 @@ __global__ void tile_scatter_kernel(int64_t n, const int2* __restrict__ tile_slo
     rec_out[2 * d] = rec_in[2 * i];
     rec_out[2 * d + 1] = rec_in[2 * i + 1];
   }
-}
-
-// ---- double-float helpers (value = hi + lo, |lo| <= ulp(hi)/2) ----
-struct df {
-  float hi, lo;
-};
-__device__ __forceinline__ df df_from(double v) {
-  const float h = (float)v;
-  return {h, (float)(v - (double)h)};
-}
-__device__ __forceinline__ df df_mul(df a, df b) {
-  const float p = a.hi * b.hi;
-  const float e = fmaf(a.hi, b.hi, -p);                  // exact error of the leading product
-  const float t = fmaf(a.hi, b.lo, fmaf(a.lo, b.hi, e));
-  const float h = p + t;
-  return {h, t - (h - p)};
-}
-__device__ __forceinline__ df df_add(df a, df b) {
-  const float s = a.hi + b.hi;
-  const float bb = s - a.hi;
-  const float e = (a.hi - (s - bb)) + (b.hi - bb);       // exact error of the leading sum
-  const float t = e + a.lo + b.lo;
-  const float h = s + t;
-  return {h, t - (h - s)};
-}
-__device__ __forceinline__ df df_scale(df a, float c) {  // c with few bits (small integers, 1/(k-1) below)
-  const float p = a.hi * c;
-  const float e = fmaf(a.hi, c, -p);
-  const float t = fmaf(a.lo, c, e);
-  const float h = p + t;
-  return {h, t - (h - p)};
 }
 
 // B-spline weights M_n(f + j) in double-float arithmetic (the order recursion of bspline()).
@@ -700,7 +678,8 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
 template <int N>
 __global__ void __launch_bounds__(kThreads) spread_nosort_kernel(MeshGeom G, int64_t n, const double* __restrict__ x,
                                                                  const double* __restrict__ q, float* __restrict__ Q,
-                                                                 double* __restrict__ sumq) {
+                                                                 double* __restrict__ sumq,
+                                                                 float4* __restrict__ coords) {
   constexpr int LG = Lanes<N>::value;
   constexpr int PB = kThreads / LG;   // particles per block and pass
   const int K = G.K;
@@ -719,7 +698,9 @@ __global__ void __launch_bounds__(kThreads) spread_nosort_kernel(MeshGeom G, int
     if (gl < 3) {
       double f;
       mesh_coord(x[3 * i + gl], gl == 0 ? G.c0 : (gl == 1 ? G.c1 : G.c2), G.L, K, myg, f);
-      bspline_df<N>(df_from(f), mine);
+      const df fd = df_from(f);
+      bspline_df<N>(fd, mine);
+      if (coords) coords[3 * i + gl] = make_float4(__int_as_float(myg), fd.hi, fd.lo, 0.0f);
     }
     int g[3];
 #pragma unroll
@@ -824,10 +805,9 @@ __device__ __forceinline__ T lag_block_sum(T v) {   // to thread 0 of a kLagThre
 
 // counting sort, pass 1: cell counters (sub counters per cell, chosen by the particle index, cut
 // the contention of the returned atomics) and the record of each particle
-__global__ void __launch_bounds__(kThreads) lagrange_count_kernel(MeshGeom G, int Kc, int sub, int64_t n,
-                                                                  const double* __restrict__ x, int* __restrict__ count,
-                                                                  int2* __restrict__ slot, LagRec* __restrict__ rec) {
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
+__global__ void lagrange_count_kernel(MeshGeom G, int Kc, int sub, int64_t n, const double* __restrict__ x,
+                                      int* __restrict__ count, int2* __restrict__ slot, LagRec* __restrict__ rec) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     LagRec r;
     int c = 0;
 #pragma unroll
@@ -915,6 +895,9 @@ __global__ void __launch_bounds__(kLagThreads) lagrange_gather_cell_kernel(
   constexpr int NR = LN * LN, RS = LN + 1, CH = lag_chunk<LN>(), W = kLagThreads / 32;
   __shared__ T sphi[NR * RS];
   __shared__ T sw[CH][3][LN], sd[CH][3][LN];
+  __shared__ int sp[CH];
+  __shared__ double sq[CH];
+  __shared__ T sres[CH][4];   // per particle: sum S (Phi - Phi_ref) and the three derivative sums
   const int cell = blockIdx.x;
   const int b = start[cell * sub], e = start[(cell + 1) * sub];
   if (b == e) return;   // the whole CTA: nothing to gather
@@ -929,14 +912,21 @@ __global__ void __launch_bounds__(kLagThreads) lagrange_gather_cell_kernel(
   }
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const double shift = corr_c * (sumq ? *sumq : 0.0);
+  const double ref_d = (double)ref;
   double e_acc = 0.0;
   for (int j0 = b; j0 < e; j0 += CH) {
     const int m = min(CH, e - j0);
     __syncthreads();   // the node block is in place / the previous chunk is consumed
     for (int it = threadIdx.x; it < 3 * m; it += kLagThreads) {
       const int j = it / 3, a = it - 3 * j;
+      const LagRec& rj = rec[j0 + j];
+      if (a == 0) {   // the particle's index and charge, for the warp that finishes it
+        const int p = rj.p;
+        sp[j] = p;
+        sq[j] = q ? q[p] : 0.0;
+      }
       T w[LN], dw[LN];
-      lagrange_axis<T, LN, true>((T)rec[j0 + j].t[a], w, dw);
+      lagrange_axis<T, LN, true>((T)rj.t[a], w, dw);
 #pragma unroll
       for (int l = 0; l < LN; ++l) {
         sw[j][a][l] = w[l];
@@ -969,18 +959,27 @@ __global__ void __launch_bounds__(kLagThreads) lagrange_gather_cell_kernel(
         g2 += __shfl_xor_sync(0xffffffffu, g2, o);
       }
       if (lane == 0) {
-        const int p = rec[j0 + j].p;
-        const double ph = ((double)a + (double)ref - shift) * ke;
-        const double qi = q ? q[p] : 0.0;
-        if (phi_out) phi_out[p] = ph;
-        if (F_out) {
-          const double sc2 = -qi * ke * gscale;
-          F_out[3 * p + 0] = sc2 * (double)g0;
-          F_out[3 * p + 1] = sc2 * (double)g1;
-          F_out[3 * p + 2] = sc2 * (double)g2;
-        }
-        e_acc += 0.5 * qi * ph;
+        sres[j][0] = a;
+        sres[j][1] = g0;
+        sres[j][2] = g1;
+        sres[j][3] = g2;
       }
+    }
+    // the float64 outputs of the chunk, one thread per particle (float64 operations issue at a
+    // small fraction of the float32 rate, so they run on full warps, not on one lane each)
+    __syncthreads();
+    for (int j = threadIdx.x; j < m; j += kLagThreads) {
+      const int p = sp[j];
+      const double ph = ((double)sres[j][0] + ref_d - shift) * ke;
+      const double qi = sq[j];
+      if (phi_out) phi_out[p] = ph;
+      if (F_out) {
+        const double sc2 = -qi * ke * gscale;
+        F_out[3 * p + 0] = sc2 * (double)sres[j][1];
+        F_out[3 * p + 1] = sc2 * (double)sres[j][2];
+        F_out[3 * p + 2] = sc2 * (double)sres[j][3];
+      }
+      e_acc += 0.5 * qi * ph;
     }
   }
   if (energy) {
@@ -1141,9 +1140,12 @@ cudaError_t launch_lagrange_sort(kpme_plan_t P, int64_t n, const double* x, doub
   if (e != cudaSuccess) return e;
   LagRec* rec_in = reinterpret_cast<LagRec*>(P->d_rec_in);
   const int grid = grid_for(P, n);
-  if (n > 0)
-    lagrange_count_kernel<<<grid, kThreads, 0, P->stream>>>(geom(P), Kc, sub, n, x, P->d_tcount, P->d_tslot,
-                                                            rec_in);
+  if (n > 0) {   // 64-thread blocks: the float64 cell coordinates spread over every SM
+    int64_t cb = (n + 63) / 64;
+    if (cb > (int64_t)P->sm_count * 32) cb = (int64_t)P->sm_count * 32;
+    lagrange_count_kernel<<<(unsigned)cb, 64, 0, P->stream>>>(geom(P), Kc, sub, n, x, P->d_tcount, P->d_tslot,
+                                                              rec_in);
+  }
   tile_scan_kernel<<<1, 1024, 0, P->stream>>>(P->d_tcount, (int)ncnt, P->d_tstart);
   if (n > 0) tile_scatter_kernel<<<grid, kThreads, 0, P->stream>>>(n, P->d_tslot, P->d_tstart, P->d_rec_in, P->d_rec);
   return cudaGetLastError();
@@ -1161,14 +1163,15 @@ cudaError_t launch_lagrange_gather(kpme_plan_t P, int64_t n, const double* q, co
              : lagrange_gather_t<float>(P, q, (const float*)Phi, phi, F, energy, c);
 }
 
-cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q) {
+cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, const double* q, float* Q,
+                                 float4* coords) {
   if (n <= 0) return cudaSuccess;
   const MeshGeom G = geom(P);
   const int grid = grid_groups(P, n, P->p.order <= 4 ? 4 : 8);
   switch (P->p.order) {
-    case 4: spread_nosort_kernel<4><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq); break;
-    case 6: spread_nosort_kernel<6><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq); break;
-    case 8: spread_nosort_kernel<8><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq); break;
+    case 4: spread_nosort_kernel<4><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq, coords); break;
+    case 6: spread_nosort_kernel<6><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq, coords); break;
+    case 8: spread_nosort_kernel<8><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq, coords); break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

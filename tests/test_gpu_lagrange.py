@@ -175,3 +175,17 @@ def test_lagrange_modes_non_neutral_autotune_and_potential(torch):
     Phi = lg.apply_exact(Qn, 4, 16, L_BOX, BETA, M)
     p_r, _ = lg.gather(t, np.zeros(len(t)), L_BOX, 4, 16, Phi)
     assert rel(host(p), p_r) < 3e-9
+
+
+@pytest.mark.parametrize("Kc,Ln,Mm", [(2, 4, 7), (2, 4, 9), (3, 6, 8)])
+def test_lagrange_modes_more_modes_than_nodes(torch, Kc, Ln, Mm):
+    """Mode rows r = 2M + 1 above the node count of an axis, and above the grouped kernels'
+    register budget (M > 7: one launch per transform)."""
+    from paper_2601_18838_gb300 import Plan
+    x, q = _cloud(120, 13)
+    plan = Plan(L_BOX, Kc * Ln, Ln, BETA, precision="fp64", skp_tol=1e-12, skp_method="sinc", max_n=120,
+                interp="lagrange_modes", modes=Mm)
+    plan.build_skp()
+    out = plan.energy_forces(dev(torch, x), dev(torch, q))
+    ref = lg.reciprocal(x, q, L_BOX, BETA, Kc, Ln, Mm)
+    assert rel(host(out["dEdq"]), ref["phi"]) < 1e-10 and rel(host(out["forces"]), ref["F"]) < 1e-9
