@@ -36,10 +36,13 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t a = ao / n_out;
     const Tin* src = in + a * n_in * B + b;
     double s = 0.0;
+    // unrolled so that the loads of several steps are in flight (the sum keeps its order)
     if (backward) {
+#pragma unroll 8
       for (int i = 0; i < n_in; ++i) s = fma(U[(int64_t)i * K + o], (double)src[(int64_t)i * B], s);
     } else {
       const double* u = U + (int64_t)o * K;
+#pragma unroll 8
       for (int i = 0; i < n_in; ++i) s = fma(u[i], (double)src[(int64_t)i * B], s);
     }
     if (diag) s *= diag[idx];
@@ -75,7 +78,8 @@ __global__ void __launch_bounds__(kThreads)
     const int64_t a = ao / n_out;
     const Tin* src = in + a * n_in * B + b;
     df s = {0.0f, 0.0f};
-    for (int i = 0; i < n_in; ++i) {
+#pragma unroll 8
+    for (int i = 0; i < n_in; ++i) {   // unrolled: the loads of several steps in flight
       const df u = ld(U + (backward ? (int64_t)i * K + o : (int64_t)o * K + i));
       s = df_fma(s, u, ld(src + (int64_t)i * B));
     }
@@ -93,6 +97,7 @@ __global__ void __launch_bounds__(kThreads)
   const int a = blockIdx.x;
   for (int mu = threadIdx.x; mu < r; mu += blockDim.x) {
     df s = {0.0f, 0.0f};
+#pragma unroll 8
     for (int i = 0; i < K; ++i) s = df_fma(s, ld(U + (int64_t)mu * K + i), ld(T2 + (int64_t)a * K + i));
     s = df_mul(s, ld(D + (int64_t)a * r + mu));
     t_sm[mu] = make_float2(s.hi, s.lo);
@@ -100,6 +105,7 @@ __global__ void __launch_bounds__(kThreads)
   __syncthreads();
   for (int g = threadIdx.x; g < K; g += blockDim.x) {
     df s = {0.0f, 0.0f};
+#pragma unroll 8
     for (int mu = 0; mu < r; ++mu) s = df_fma(s, ld(U + (int64_t)mu * K + g), ld(t_sm + mu));
     st(S2 + (int64_t)a * K + g, s);
   }
