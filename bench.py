@@ -403,13 +403,20 @@ def main(argv=None):
     if not tensor:
         roof = None
     if lag and s.meta["interp"] == "lagrange_modes":
-        # the node operator in mode space: float64 transforms on the CUDA cores
-        fp64_peak = 1250.0   # GFLOP/s, nominal dense FP64 of a GB300
+        # the node operator in mode space on the CUDA cores: double-float multiply-adds on the
+        # float32 pipe (float forms) or float64 (FP64 form)
+        if args.precision == "fp64":
+            alu_peak, src = 1250.0, "nominal FP64 rate of a GB300 (1.25 TFLOP/s)"
+        else:
+            # 152 SMs x 128 float32 lanes x 2070 MHz, 15 float32 instructions per double-float
+            # multiply-add (df_mul + df_add), 2 flops per multiply-add
+            alu_peak = 152 * 128 * 2.07 / 15 * 2
+            src = "float32 pipe (152 SMs x 128 lanes x 2070 MHz) / 15 instructions per double-float multiply-add"
         ach = mp_flops / (skp_ms * 1e-3) / 1e9 if skp_ms > 0 else None
-        roof = {"bound": "alu", "kernel": "modes_axis_kernel (mode-space node operator, float64: three forward "
-                                          "and three backward transforms, the diagonal fused)",
-                "achieved": ach, "peak": fp64_peak, "unit": "GFLOP/s", "frac": (ach / fp64_peak) if ach else None,
-                "traffic": None, "peak_source": "nominal FP64 rate (1.25 TFLOP/s), no measured FP64 peak",
+        roof = {"bound": "alu", "kernel": "modes_axis_df_kernel / modes_mid_df_kernel (mode-space node operator: "
+                                          "three forward and three backward transforms, the diagonal fused)",
+                "achieved": ach, "peak": alu_peak, "unit": "GFLOP/s", "frac": (ach / alu_peak) if ach else None,
+                "traffic": None, "peak_source": src,
                 "flops_per_step": mp_flops, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
                 "ms_per_launch": per_launch_ms}
     # spreading and gathering against HBM: algorithmic bytes per evaluation (positions and

@@ -598,8 +598,8 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
   const int64_t k3 = K3(P);
   const PrecInfo& pi = P->prec;
   const SkpHost& S = P->skp;
-  if (lagrange_modes(P)) {
-    StepScope sc(P, STEP_SKP1, 1);
+  if (lagrange_modes(P)) {   // five transform launches in double-float, six in float64
+    StepScope sc(P, STEP_SKP1, pi.fp64 ? 6 : 5);
     KPME_CUDA_TRY(P, launch_lagrange_modes(P, Q.p, Q.dbl, Phi, pi.fp64));
     return KPME_OK;
   }
@@ -1117,7 +1117,10 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
   (void)k3;
   MeshRef m;
   {
-    const int spread_launches = P->prec.fp64 ? (n > 0 ? 1 : 0) : (n > 0 ? (tiled(P) ? 5 : 2) : 1);
+    // per-cell form: clear, count, scan, scatter, per-cell spreading (count and scatter skipped
+    // when empty)
+    const int spread_launches = lagrange(P) ? (n > 0 ? 5 : 3)
+                                : P->prec.fp64 ? (n > 0 ? 1 : 0) : (n > 0 ? (tiled(P) ? 5 : 2) : 1);
     StepScope sc(P, STEP_SPREAD, spread_launches);
     if ((st = spread_mesh(P, n, x, q, m, energy)) != KPME_OK) return st;   // also clears energy
   }
