@@ -98,3 +98,38 @@ def test_lagrange_forces_match_energy_differences(cloud):
             xm[i, a] -= h
             fd = -(lg.reciprocal(xp, q, L, beta, 4, 10, M)["E"] - lg.reciprocal(xm, q, L, beta, 4, 10, M)["E"]) / (2 * h)
             assert abs(fd - r["F"][i, a]) < 1e-6 * max(1.0, abs(r["F"][i, a]))
+
+
+def test_quadrature_terms_collapse_to_one_mode_space_diagonal(cloud):
+    # Eq. VtV: every term's axis factor is W^* diag(a_lambda) W on the same Fourier rows of the
+    # node positions, so the sum over the terms is one diagonal in mode space.  Written here in
+    # the real rows the mode-space form uses (1, cos 2 pi m y, sin 2 pi m y; the +-m pairs folded
+    # with weight 2, the m = 0 entry zero), against the oracle's term-by-term loop.
+    from oracle import skp
+    x, q, L, beta, M, _ = cloud
+    Kc, Ln, tol = 4, 8, 1e-12
+    Qn = lg.spread(x, q, L, Kc, Ln)
+    w, A, c = lg.sinc_factors(Kc, Ln, L, beta, M, tol)
+    ref = lg.apply_skp(Qn, w, A, c, L)
+    m = np.arange(-M, M + 1)
+    msq = m[:, None, None] ** 2 + m[None, :, None] ** 2 + m[None, None, :] ** 2
+    nq, h, _ = skp.sinc_search(np.unique(msq[msq > 0]).astype(np.float64), tol)
+    wl, lam = skp.sinc_rule(nq, h)
+    assert np.allclose(wl, w)
+    y = lg.node_positions(Kc, Ln)
+    mu_m = np.array([0] + [k for k in range(1, M + 1) for _ in (0, 1)])         # mode of each row
+    U = np.vstack([np.ones_like(y)] + [f(2 * np.pi * k * y) for k in range(1, M + 1) for f in (np.cos, np.sin)])
+    kap = np.where(mu_m == 0, 1.0, 2.0)
+    s2 = mu_m[:, None, None] ** 2 + mu_m[None, :, None] ** 2 + mu_m[None, None, :] ** 2
+    xi2 = (beta * L) ** 2
+    D = np.einsum("l,labc->abc", wl, np.exp(-(lam[:, None, None, None] + math.pi ** 2 / xi2) * s2[None]))
+    D = np.where(s2 == 0, 0.0, D) * kap[:, None, None] * kap[None, :, None] * kap[None, None, :] / (math.pi * L)
+    That = np.einsum("ag,bh,ck,ghk->abc", U, U, U, Qn)
+    Phi = np.einsum("ag,bh,ck,abc->ghk", U, U, U, D * That)
+    assert _rel(Phi, ref) < 1e-12
+    # and the zeroed m = 0 entry is exactly the correction term: without it the diagonal is
+    # the uncorrected sum, off by c_Lambda sum(Q)
+    D0 = D.copy()
+    D0[0, 0, 0] = float(np.sum(wl)) / (math.pi * L)
+    Phi0 = np.einsum("ag,bh,ck,abc->ghk", U, U, U, D0 * That)
+    assert np.allclose(Phi0 - Phi, c * Qn.sum() / (math.pi * L), rtol=0, atol=1e-12 * np.abs(Phi).max())
