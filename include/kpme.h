@@ -109,7 +109,10 @@ typedef enum {
                                  (Eq. VtV, V[lambda] = omega^(1/3) sqrt(alpha_lambda) W), so
                                  the sum over lambda is one diagonal on the (2M+1)^3 real
                                  modes between three forward and three backward transforms
-                                 of the node tensor (float64 arithmetic at every precision) */
+                                 of the node tensor (double-float arithmetic on the float32
+                                 pipe for float32 meshes, float64 for KPME_FP64); the m = 0
+                                 correction is inside the diagonal (kpme_get_skp reports
+                                 c = 0)                                                      */
 } kpme_interp_t;
 
 typedef struct {
