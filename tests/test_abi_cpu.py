@@ -76,3 +76,26 @@ def test_weighted_half_range_svd_equals_full_grid():
     half = np.linalg.svd(Th.reshape(Kh * Kh, Kh).T, compute_uv=False)
     np.testing.assert_allclose(half, full[:Kh], rtol=1e-12, atol=1e-14 * full[0])
     assert np.all(full[Kh:] < 1e-13 * full[0])
+
+
+@pytest.mark.parametrize("interp", [1, 2])
+def test_per_cell_form_parameters_are_validated_without_gpu(L, interp):
+    from paper_2601_18838_gb300._binding import Params
+
+    def plan_status(**kw):
+        p = Params()
+        L.kpme_default_params(C.byref(p))
+        p.radius, p.interp, p.order, p.K, p.modes, p.skp_method = 10.0, interp, 8, 64, 4, 1
+        for k, v in kw.items():
+            setattr(p, k, v)
+        h = C.c_void_p()
+        st = L.kpme_plan(C.byref(p), None, C.byref(h))
+        assert not h.value
+        return st
+
+    # past validation, the missing GPU is the first error (KPME_ERR_CUDA)
+    assert plan_status() == 3
+    assert plan_status(order=16, K=32, modes=64) == 3
+    for bad in (dict(skp_method=0), dict(order=5), dict(order=10, K=60), dict(K=60), dict(modes=0),
+                dict(modes=65), dict(K=1024), dict(interp=3)):
+        assert plan_status(**bad) == 1, bad   # KPME_ERR_INVALID_ARG
