@@ -133,3 +133,17 @@ def test_quadrature_terms_collapse_to_one_mode_space_diagonal(cloud):
     D0[0, 0, 0] = float(np.sum(wl)) / (math.pi * L)
     Phi0 = np.einsum("ag,bh,ck,abc->ghk", U, U, U, D0 * That)
     assert np.allclose(Phi0 - Phi, c * Qn.sum() / (math.pi * L), rtol=0, atol=1e-12 * np.abs(Phi).max())
+
+
+def test_error_follows_nu_to_the_order_and_reaches_the_double_floor(cloud):
+    # §5.1: the overall error follows the interpolation error, O(nu^L) with nu ~ M r_c, so
+    # halving the cells at a fixed order divides it by about 2^L; with equispaced nodes high
+    # orders lose digits to rounding, and the ~1e-14 floor is reached with more cells instead.
+    x, q, L, beta, M, ref = cloud
+    cases = [(2, 8), (4, 8), (8, 8), (4, 6), (8, 6), (8, 12)]
+    e = {c: _rel(lg.reciprocal(x, q, L, beta, c[0], c[1], M)["phi"], ref["phi"]) for c in cases}
+    for Ln, pairs in ((8, [(2, 4), (4, 8)]), (6, [(4, 8)])):
+        for a, b in pairs:
+            ratio = e[(a, Ln)] / e[(b, Ln)]
+            assert 2 ** Ln / 3 < ratio < 3 * 2 ** Ln, (Ln, a, b, ratio)
+    assert e[(8, 12)] < 3e-13
