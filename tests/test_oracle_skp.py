@@ -135,3 +135,100 @@ def test_sinc_skp_with_correction_nonneutral():
     # SVD and quadrature SKPs agree to their tolerances
     r3 = skp.reciprocal(s.x, s.q, s.box, 16, 4, 0.4, 1e-9)
     assert np.linalg.norm(r3["phi"] - r["phi"]) / np.linalg.norm(p["phi"]) < 1e-7
+
+
+# ---- the two-level generator form handed to kpme_set_skp (§2.3 Eq. kronw, §2.4 Eq. VtV) ----
+# The operator is rebuilt here from the generators alone, with circulants formed by index
+# arithmetic and mode products written as explicit sums over one axis, following the
+# documented contract of kpme_set_skp: term t of outer index i applies C(gen1[t]) on axis 0,
+# C(gen2[t]) on axis 1 and C(gen3[i]) on axis 2, C(g)[k, k'] = g((k - k') mod K).
+
+def _circ_from_gen(g):
+    K = g.size
+    k = np.arange(K)
+    return g[(k[:, None] - k[None, :]) % K]
+
+
+def _apply_generators(Q, r1, gen3, gen2, gen1):
+    Phi = np.zeros_like(Q)
+    t = 0
+    for i, n_in in enumerate(r1):
+        C3 = _circ_from_gen(gen3[i])
+        Y = np.einsum("ck,abk->abc", C3, Q)            # axis 2
+        for _ in range(n_in):
+            Z = np.einsum("cj,ajk->ack", _circ_from_gen(gen2[t]), Y)    # axis 1
+            Phi += np.einsum("ca,ajk->cjk", _circ_from_gen(gen1[t]), Z)  # axis 0
+            t += 1
+    assert t == gen2.shape[0] == gen1.shape[0]
+    return Phi
+
+
+@pytest.mark.parametrize("K", [8, 12])
+def test_generator_closed_form(K):
+    # a mode pair a(m0) = a(-m0) = 1 gives g(d) = 2 cos(2 pi m0 d / K); m0 = 0 gives 1 and the
+    # Nyquist mode alone gives (-1)^d; g is the first column of the circulant
+    m = spme.wrapped_modes(K)
+    d = np.arange(K)
+    for m0 in range(K // 2 + 1):
+        a = (np.abs(m) == m0).astype(np.float64)
+        g = skp.generator(a)
+        if m0 == 0:
+            ref = np.ones(K)
+        elif m0 == K // 2:
+            ref = np.cos(np.pi * d)
+        else:
+            ref = 2.0 * np.cos(2 * np.pi * m0 * d / K)
+        np.testing.assert_allclose(g, ref, atol=1e-13)
+        np.testing.assert_allclose(g, skp.circulant(a)[:, 0], atol=1e-13)
+
+
+def test_generators_of_structured_two_level_skp():
+    # distinct factors on every axis and distinct weights at both levels, uneven r1: the
+    # generator form must reproduce the FFT convolution with sum s_i s_ij a0 (x) a1 (x) a2
+    K = 8
+    rng = np.random.default_rng(11)
+    r1 = [2, 1, 3]
+    outer = np.array([3.0, 2.0, 0.5])
+    inner = [np.array([1.5, 0.25]), np.array([0.75]), np.array([2.0, 0.5, 0.125])]
+    w, a0, a1, a2 = [], [], [], []
+    for i, n_in in enumerate(r1):
+        u = _even_vec(rng, K)
+        for j in range(n_in):
+            w.append(outer[i] * inner[i][j])
+            a0.append(_even_vec(rng, K))
+            a1.append(_even_vec(rng, K))
+            a2.append(u)
+    s = skp.SKP(K, np.array(w), np.array(a0), np.array(a1), np.array(a2), 0.0, r1, outer, inner)
+    gr1, g3, g2, g1 = skp.generators(s)
+    assert list(gr1) == r1 and g3.shape == (3, K) and g2.shape == g1.shape == (6, K)
+    Q = rng.standard_normal((K, K, K))
+    ref = spme.convolve_fft(Q, s.tensor())
+    np.testing.assert_allclose(_apply_generators(Q, gr1, g3, g2, g1), ref, atol=1e-12 * np.abs(ref).max())
+    # the plausible slips fail: factors of axes 0 and 1 swapped, or the inner weight shared
+    bad = _apply_generators(Q, gr1, g3, g1, g2)
+    assert np.abs(bad - ref).max() > 1e-3 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("K,tol", [(8, 1e-5), (12, 1e-8)])
+def test_generators_of_nkpa_match_apply(K, tol):
+    T = spme.influence(K, 4, 9.0, 0.45)
+    s = skp.nkpa(T, tol)
+    assert len(s.r1) > 1 and len(set(s.r1)) > 1          # several outer terms, uneven r1
+    r1, g3, g2, g1 = skp.generators(s)
+    rng = np.random.default_rng(K)
+    Q = rng.standard_normal((K, K, K))
+    ref = skp.apply(Q, s)
+    got = _apply_generators(Q, r1, g3, g2, g1)
+    assert np.linalg.norm(got - ref) <= 1e-13 * np.linalg.norm(ref)
+    np.testing.assert_allclose(ref, spme.convolve_fft(Q, s.tensor()), atol=1e-12 * np.abs(ref).max())
+
+
+def test_generators_full_rank_equal_pme_influence():
+    # untruncated NKPA: the generator form is the PME mesh operator B(m) C(m) itself
+    K = 8
+    T = spme.influence(K, 4, 9.0, 0.45)
+    s = skp.nkpa(T, 0.0)
+    Q = np.random.default_rng(3).standard_normal((K, K, K))
+    ref = spme.convolve_fft(Q, T)
+    got = _apply_generators(Q, *skp.generators(s))
+    assert np.linalg.norm(got - ref) <= 1e-12 * np.linalg.norm(ref)
