@@ -1,11 +1,12 @@
 """Benchmark: reciprocal evaluations per second of the tensor-core SKP path on GB300.
 
 One step = one reciprocal evaluation of the whole path (spread, SKP mode products,
-gather of potentials and forces, float64 energy and virial) for the water box
-(10^4 rigid 3-site molecules, 30,000 atoms, 67 A, B-spline order 4, K = 64).
+gather of potentials and forces, float64 energy and virial) for the 10^6-charge box
+(220 A, B-spline order 6, K = 256, SKP tolerance 1e-7), the largest single-GPU
+workload; the water box (10^4 rigid 3-site molecules, K = 64) is reported beside it.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x6]
-                    [--workload water|small|mixed|large] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--precision bf16x10]
+                    [--workload large|water|small|mixed|lagrange|batched] [--impl ours|reference]
 
 Prints one JSON line (rank 0).  Under torchrun each rank runs its own replica on its
 own GPU (the path has no data-parallel split for one system); ``value`` is the
@@ -18,7 +19,6 @@ import json
 import os
 import subprocess
 import sys
-import threading
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -131,7 +131,7 @@ def _system(name):
 
 
 def _oracle_eval(s):
-    """The oracle's evaluation of workload s and its plan-time build (returns (build_s, eval))."""
+    """The oracle's evaluation of workload s and its plan-time build (returns (build_s, eval, skp))."""
     t0 = time.perf_counter()
     if s.meta.get("interp", "bspline").startswith("lagrange"):
         from oracle import lagrange as lg
@@ -143,23 +143,79 @@ def _oracle_eval(s):
             Phi = lg.apply_skp(Qn, *fac, s.box)
             phi, F = lg.gather(s.x, s.q, s.box, Kc, s.order, Phi)
             return {"phi": phi, "F": F}
-        return time.perf_counter() - t0, ev
+        return time.perf_counter() - t0, ev, None
     from oracle import skp
     o = skp.build(s.K, s.order, s.box, s.beta, s.skp_tol)
-    return time.perf_counter() - t0, lambda: skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+    return (time.perf_counter() - t0,
+            lambda: skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o), o)
+
+
+# Full oracle evaluations are timed while one takes at most this many seconds (estimated from
+# the work: particles x stencil points and Kronecker terms x K^4); larger workloads are
+# timed on a bounded sample of the same evaluation and scaled to one evaluation.
+FULL_EVAL_LIMIT_S = 10.0
+
+
+def _oracle_sample(s, o):
+    """One bounded sample of the oracle's evaluation of workload s, scaled to a full
+    evaluation: spreading and gathering of the first n_p particles (scaled by N / n_p), the
+    SKP operator of Algorithm 2 on the first r_s Kronecker terms (scaled by R / r_s), and the
+    virial trace in full.  Returns (estimated seconds per evaluation, description)."""
+    import numpy as np
+    from oracle import skp, spme
+    n_p = min(s.n, 40_000)
+    r_s = min(o.R, 4)
+    x, q = s.x[:n_p], s.q[:n_p]
+    sub = skp.SKP(o.K, o.w[:r_s], o.a0[:r_s], o.a1[:r_s], o.a2[:r_s], 0.0)
+    t0 = time.perf_counter()
+    Qp = spme.spread(x, q, s.box, s.K, s.order)
+    t1 = time.perf_counter()
+    Phi = skp.apply(Qp, sub)
+    t2 = time.perf_counter()
+    spme.gather(x, q, s.box, s.K, s.order, Phi)
+    t3 = time.perf_counter()
+    spme.virial_trace(Qp, 0.0, s.K, s.order, s.box, s.beta)
+    t4 = time.perf_counter()
+    est = ((t1 - t0) + (t3 - t2)) * s.n / n_p + (t2 - t1) * o.R / r_s + (t4 - t3)
+    desc = (f"spreading and gathering of {n_p} of the {s.n} charges (time x {s.n / n_p:.0f}), the SKP "
+            f"operator on {r_s} of its {o.R} Kronecker terms (time x {o.R / r_s:.2f}), the virial trace in "
+            f"full; float64 numpy oracle")
+    return est, desc
+
+
+def _full_eval_estimate_s(s):
+    # numpy oracle on the host: ~1.5e7 stencil updates/s for spreading plus gathering and
+    # ~2e11 flop/s for the dense mode products (6 R K^4 at the rank the tolerance gives)
+    R = 50 if s.K <= 64 else 170
+    return s.n * s.order ** 3 / 1.5e7 + 6 * R * float(s.K) ** 4 / 2e11
 
 
 def cpu_baseline(s, budget_s: float = 20.0, max_evals: int = 5, gpu_out=None) -> dict:
     """The float64 oracle (as it stands) on the host cores: full reciprocal evaluations of
-    the same workload, as many as fit in the budget (at least one)."""
-    t_build, ev = _oracle_eval(s)
+    the same workload, as many as fit in the budget (at least one), or, where one full
+    evaluation would take longer than FULL_EVAL_LIMIT_S, bounded samples of it scaled to one
+    evaluation (repeated while the budget lasts)."""
+    t_build, ev, o = _oracle_eval(s)
+    cores = os.cpu_count()
+    if o is not None and _full_eval_estimate_s(s) > FULL_EVAL_LIMIT_S:
+        n, t, ests = 0, 0.0, []
+        while n < max_evals and (n == 0 or t < budget_s):
+            a = time.perf_counter()
+            est, desc = _oracle_sample(s, o)
+            t += time.perf_counter() - a
+            ests.append(est)
+            n += 1
+        est = sorted(ests)[len(ests) // 2]
+        return {"value": 1.0 / est, "unit": "evals/s", "cores": cores, "kind": "oracle",
+                "sample": f"median of {n} samples: {desc} (SKP build {t_build:.1f} s not timed; numpy's BLAS "
+                          f"threads for the mode products, one thread for spreading and gathering)"}
     n, t, ref = 0, 0.0, None
     while n < max_evals and (n == 0 or t < budget_s):
         a = time.perf_counter()
         ref = ev()
         t += time.perf_counter() - a
         n += 1
-    res = {"value": n / t, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
+    res = {"value": n / t, "unit": "evals/s", "cores": cores, "kind": "oracle",
            "sample": f"{n} full float64 oracle evaluations (numpy) of the {s.name} workload "
                      f"(SKP build {t_build:.1f} s not timed)"}
     if gpu_out is not None:
@@ -173,24 +229,39 @@ def cpu_baseline(s, budget_s: float = 20.0, max_evals: int = 5, gpu_out=None) ->
 
 
 def run_reference(args):
+    """The reference arm: the float64 oracle as it stands on the host cores, the same workload
+    and metric.  A step is one full evaluation, or, for workloads whose full evaluation takes
+    longer than FULL_EVAL_LIMIT_S, one bounded sample scaled to an evaluation."""
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
     s = _system(args.workload)
-    _, ev = _oracle_eval(s)
-    for _ in range(args.warmup):
-        ev()
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        ev()
-    dt = time.perf_counter() - t0
+    _, ev, o = _oracle_eval(s)
+    sampled = o is not None and _full_eval_estimate_s(s) > FULL_EVAL_LIMIT_S
+    if sampled:
+        for _ in range(args.warmup):
+            _oracle_sample(s, o)
+        total, desc = 0.0, ""
+        for _ in range(args.steps):
+            est, desc = _oracle_sample(s, o)
+            total += est
+        dt = total
+        sample = f"per step: {desc}"
+    else:
+        for _ in range(args.warmup):
+            ev()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ev()
+        dt = time.perf_counter() - t0
+        sample = f"{args.steps} full float64 oracle evaluations per timed region"
     v = args.steps / dt
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "evals/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD_TEXT[args.workload]},
             "cpu_baseline": {"value": v, "unit": "evals/s", "cores": os.cpu_count(), "kind": "oracle",
-                             "sample": f"{args.steps} full float64 oracle evaluations per timed region"},
+                             "sample": sample},
             "e2e": {"value": v, "unit": "evals/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
@@ -286,41 +357,27 @@ def run_batched(args):
     return 0
 
 
-def main(argv=None):
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=50)
-    ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water", choices=list(WORKLOAD_TEXT))
-    ap.add_argument("--precision", default="bf16x10")
-    ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--fp64-steps", type=int, default=5)
-    ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch configuration")
-    ap.add_argument("--tune-cache", default=None,
-                    help="autotuner cache file: a matching entry is applied without timing, a new choice is "
-                         "appended (a profiling run then repeats the configuration of the plain run)")
-    args = ap.parse_args(argv)
-    args.warmup = max(args.warmup, 3)
-    if args.impl == "reference":
-        return run_reference(args)
-    if args.workload == "batched":
-        return run_batched(args)
+def _tensor_peak(precision):
+    """Dense tensor peak for the precision's MMA kind: the measured bf16 burst figure (a step of
+    this bench is milliseconds long, far from the seconds-long power-capped loop of the
+    sustained figure), halved for tf32 (the nominal ratio)."""
+    peaks, src = _peaks()
+    peak = peaks.get("bf16_tflops", 1900.0)
+    note = f"{src} bf16_tflops (burst)"
+    if precision.startswith("tf32"):
+        peak, note = peak / 2.0, note + " x 1/2 (tf32 nominal ratio)"
+    return peak, note, peaks
 
+
+def _measure(args, name, steps, warmup, ctx, headline):
+    """Time `steps` evaluations of workload `name` through one plan (warm-ups first, L2
+    flushed before each step, CUDA events on the launching stream), then the same steps with
+    the library's per-step events, and (headline only) the end-to-end and FP64-form runs."""
     import numpy as np
     import torch
-    ws, rank, local = _dist()
-    torch.cuda.set_device(local)
-    dev = torch.device("cuda", local)
-    pg = _init_dist(dev)
-    from paper_2601_18838_gb300 import build as _build
-    if rank == 0:
-        _build.build()
-    if pg:
-        pg.barrier()
     from paper_2601_18838_gb300 import Plan
-
-    s = _system(args.workload)
+    pg, dev, rank, ws, local = ctx
+    s = _system(name)
     stream = torch.cuda.current_stream()
     lag = s.meta.get("interp", "bspline").startswith("lagrange")
     extra = dict(interp=s.meta["interp"], modes=s.meta["modes"], skp_method="sinc") if lag else {}
@@ -360,48 +417,58 @@ def main(argv=None):
         plan.set_profiling(False)
         return sum(a.elapsed_time(b) for a, b in evs), prof
 
-    for _ in range(args.warmup):
+    def max_over_ranks(v):
+        if not pg:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        return t.item()
+
+    for _ in range(warmup):
         step()
     torch.cuda.synchronize()
-    clk = ClockSampler(local)
-    clk.start()
-    ms_total, _ = timed(args.steps)
-    clocks = clk.stop()
-    if pg:
-        t = torch.tensor([ms_total], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms_total = t.item()
-    ms_step = ms_total / args.steps
-    value = ws * args.steps / (ms_total * 1e-3)
+    clk = ClockSampler(local) if headline else None
+    if clk:
+        clk.start()
+    ms_total, _ = timed(steps)
+    clocks = clk.stop() if clk else None
+    ms_total = max_over_ranks(ms_total)
+    ms_step = ms_total / steps
+    res = {"workload": name, "value": ws * steps / (ms_total * 1e-3), "unit": "evals/s", "ms_per_step": ms_step,
+           "clocks": clocks, "skp_rank": R, "skp_r0": info["r0"], "skp_rel_err": skp_err,
+           "autotune": ({k: tune[k] for k in ("tile", "fused", "split", "ms_per_eval")}
+                        if not args.no_autotune else "off")}
 
     # per-kernel timing (same steps, library events on the launching stream)
-    _, prof = timed(args.steps, profile=True)
+    _, prof = timed(steps, profile=True)
+    res["profile_ms_per_step"] = {k: v[0] / steps for k, v in prof.items()}
+    res["launches_per_step"] = sum(v[1] for v in prof.values()) / steps
     K = s.K
-    useful = info["flops_useful"]
-    skp_ms = sum(prof[k][0] for k in ("skp_stage1", "skp_stage2", "skp_stage3")) / args.steps
-    skp_launches = sum(prof[k][1] for k in ("skp_stage1", "skp_stage2", "skp_stage3")) / args.steps
-    launches_per_step = sum(v[1] for v in prof.values()) / args.steps
-    peaks, peak_src = _peaks()
+    skp_ms = sum(prof[k][0] for k in ("skp_stage1", "skp_stage2", "skp_stage3")) / steps
+    skp_launches = sum(prof[k][1] for k in ("skp_stage1", "skp_stage2", "skp_stage3")) / steps
     tensor = args.precision in ("bf16", "tf32", "bf16x3", "tf32x3", "bf16x6", "bf16x10")
-    # algorithmic MMA flops of the split method per step: executed products of slices
-    mp_flops = info["flops_executed"]
-    per_launch_ms = skp_ms / max(skp_launches, 1)
-    achieved = mp_flops / (skp_ms * 1e-3) / 1e12 if skp_ms > 0 else None
-    peak = peaks.get("bf16_tflops_sustained", 1700.0)
-    if args.precision.startswith("tf32"):
-        peak = peak / 2.0   # dense tf32 rate is half the bf16 rate
+    peak, peak_note, peaks = _tensor_peak(args.precision)
+    useful = info["flops_useful"]          # 6 R K^4 per evaluation
+    executed = info["flops_executed"]      # MMA flops the split form issues
     kname = ("SKP mode products, error-free split on tcgen05 (mp_ozt_kernel stage 1, mp_ozf_kernel fused "
-             "stages 2-3 for K = 32/64; mp_ozt/mp_oz_kernel otherwise)" if args.precision == "bf16x10"
+             "stages 2-3 for K = 32/64; mp_ozt/mp_oz_kernel stages 1-3 otherwise)" if args.precision == "bf16x10"
              else "mp_tc_kernel (SKP mode products, tcgen05)")
-    traffic = _skp_traffic(args.workload, args.precision)
-    roof = {"bound": "tensor", "kernel": kname,
-            "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-            "frac": (achieved / peak) if achieved else None, "traffic": traffic,
-            "peak_source": f"{peak_src} bf16_tflops_sustained" + (" x 1/2 (tf32 nominal ratio)" if args.precision.startswith("tf32") else ""),
-            "flops_per_step": mp_flops, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
-            "ms_per_launch": per_launch_ms}
-    if not tensor:
-        roof = None
+    roof = None
+    if tensor and skp_ms > 0:
+        ach = useful / (skp_ms * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": kname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": _skp_traffic(name, args.precision),
+                "peak_source": peak_note,
+                "work": "useful flops 6 R K^4 per evaluation (the three dense mode products of every Kronecker "
+                        "term); the split form issues more on the tensor pipe (see executed)",
+                "flops_per_step": useful, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
+                "ms_per_launch": skp_ms / max(skp_launches, 1)}
+        ex = executed / (skp_ms * 1e-3) / 1e12
+        res["executed"] = {"flops_per_step": executed, "TFLOP/s": ex, "frac_of_peak": ex / peak,
+                           "note": "bf16 MMA flops issued per evaluation: digit products of the split "
+                                   "(10 per multiply for bf16x10) over the two-level term structure "
+                                   "(r0 + 2R) 2 K^4 (K^4 per fold half on folded meshes)"}
+        res["tensor_pipe_active"] = _tensor_active(name, args.precision)
     if lag and s.meta["interp"] == "lagrange_modes":
         # the node operator in mode space on the CUDA cores: double-float multiply-adds on the
         # float32 pipe (float forms) or float64 (FP64 form)
@@ -412,145 +479,169 @@ def main(argv=None):
             # multiply-add (df_mul + df_add), 2 flops per multiply-add
             alu_peak = 152 * 128 * 2.07 / 15 * 2
             src = "float32 pipe (152 SMs x 128 lanes x 2070 MHz) / 15 instructions per double-float multiply-add"
-        ach = mp_flops / (skp_ms * 1e-3) / 1e9 if skp_ms > 0 else None
+        ach = executed / (skp_ms * 1e-3) / 1e9 if skp_ms > 0 else None
         roof = {"bound": "alu", "kernel": "modes_axis_df_kernel / modes_mid_df_kernel (mode-space node operator: "
                                           "three forward and three backward transforms, the diagonal fused)",
                 "achieved": ach, "peak": alu_peak, "unit": "GFLOP/s", "frac": (ach / alu_peak) if ach else None,
                 "traffic": None, "peak_source": src,
-                "flops_per_step": mp_flops, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
-                "ms_per_launch": per_launch_ms}
+                "flops_per_step": executed, "ms_per_step": skp_ms, "launches_per_step": skp_launches,
+                "ms_per_launch": skp_ms / max(skp_launches, 1)}
+    res["roofline"] = roof
+    res["tflops_useful"] = useful / (ms_step * 1e-3) / 1e12
     # spreading and gathering against HBM: algorithmic bytes per evaluation (positions and
     # charges in float64, the float32 mesh written or read once, potentials and forces out)
     hbm = peaks.get("hbm_gbs", 6800.0)
     mesh_b = 4 * K ** 3
     part = {}
-    for kname, nbytes in (("spread", s.n * 32 + mesh_b), ("gather", mesh_b + s.n * 32 + s.n * 32)):
-        ms_k = prof[kname][0] / args.steps if kname in prof else 0.0
+    for kn, nbytes in (("spread", s.n * 32 + mesh_b), ("gather", mesh_b + s.n * 32 + s.n * 32)):
+        ms_k = prof[kn][0] / steps if kn in prof else 0.0
         gbs = nbytes / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None
-        part[kname] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs,
-                      "frac_hbm": (gbs / hbm) if gbs else None}
+        part[kn] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs, "frac_hbm": (gbs / hbm) if gbs else None}
     part["hbm_peak_gbs"] = hbm
     part["note"] = ("per-cell Lagrange: spread = counting sort by cell (clear, count, scan, scatter) + one CTA "
                     "per cell writing its Ln^3 node block once (no atomics), gather = one CTA per cell with the "
                     "block in shared memory, one warp per particle"
                     if lag else
                     "no cell sort (autotuned): spread = mesh clear + lane-group spreading with float32 atomics "
-                    "into the L2-resident mesh, gather = one thread per particle; bound by atomics and latency"
+                    "into the L2-resident mesh, gather = one thread per particle"
                     if tune.get("tile") == -1 else
-                    "spread includes the cell sort (count, scan, scatter) and the mesh clear; the kernels are "
-                    "bound by shared-memory atomics and latency at these sizes")
+                    "spread includes the cell sort (count, scan, scatter); gather reads the sorted records")
+    res["particle_kernels"] = part
 
-    # end to end through the public API with host buffers
-    xh = torch.tensor(s.x).pin_memory()
-    qh = torch.tensor(s.q).pin_memory()
-    Fh = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
-    ph = torch.empty(s.n, dtype=torch.float64).pin_memory()
-    Eh = torch.empty(2, dtype=torch.float64).pin_memory()
-    xd = torch.empty_like(x)
-    qd = torch.empty_like(q)
+    if headline:
+        # end to end through the public API with host buffers
+        xh = torch.tensor(s.x).pin_memory()
+        qh = torch.tensor(s.q).pin_memory()
+        Fh = torch.empty((s.n, 3), dtype=torch.float64).pin_memory()
+        ph = torch.empty(s.n, dtype=torch.float64).pin_memory()
+        Eh = torch.empty(2, dtype=torch.float64).pin_memory()
+        xd = torch.empty_like(x)
+        qd = torch.empty_like(q)
 
-    def e2e_step():
-        xd.copy_(xh, non_blocking=True)
-        qd.copy_(qh, non_blocking=True)
-        plan.energy_forces(xd, qd, forces=True, dEdq=True, virial=vir, out=out)
-        Fh.copy_(out["forces"], non_blocking=True)
-        ph.copy_(out["dEdq"], non_blocking=True)
-        Eh[0:1].copy_(out["energy"], non_blocking=True)
-        if vir:
-            Eh[1:2].copy_(out["virial"], non_blocking=True)
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            qd.copy_(qh, non_blocking=True)
+            plan.energy_forces(xd, qd, forces=True, dEdq=True, virial=vir, out=out)
+            Fh.copy_(out["forces"], non_blocking=True)
+            ph.copy_(out["dEdq"], non_blocking=True)
+            Eh[0:1].copy_(out["energy"], non_blocking=True)
+            if vir:
+                Eh[1:2].copy_(out["virial"], non_blocking=True)
 
-    for _ in range(3):
-        e2e_step()
-    torch.cuda.synchronize()
-    e_ms = 0.0
-    for _ in range(args.steps):
-        flush.zero_()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        e2e_step()
-        b.record(stream)
-        b.synchronize()
-        e_ms += a.elapsed_time(b)
-    if pg:
-        t = torch.tensor([e_ms], dtype=torch.float64, device=dev)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        e_ms = t.item()
-    e2e = {"value": ws * args.steps / (e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": s.n * 32,
-           "d2h_bytes_per_step": s.n * 32 + (16 if vir else 8)}
-
-    # full virial tensor (mode space; an extra call, outside the timed step)
-    vt = None
-    if rank == 0 and vir:
         for _ in range(3):
-            plan.virial_tensor(x, q)
+            e2e_step()
         torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(10):
-            plan.virial_tensor(x, q)
-        b.record(stream)
-        b.synchronize()
-        Pi, _ = plan.virial_tensor(x, q)
-        vt = {"ms_per_call": a.elapsed_time(b) / 10, "trace": float(Pi.trace().item()),
-              "note": "kpme_virial_tensor: spread, three real-DFT mode products, float64 mode-space reduction"}
+        e_ms = 0.0
+        for _ in range(steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
+        e_ms = max_over_ranks(e_ms)
+        res["e2e"] = {"value": ws * steps / (e_ms * 1e-3), "unit": "evals/s", "h2d_bytes_per_step": s.n * 32,
+                      "d2h_bytes_per_step": s.n * 32 + (16 if vir else 8)}
 
-    # the per-cell form's quadrature applied term by term (dense factors on the mode-product
-    # kernels of the precision), the paper's Algorithm 4 loop, beside the mode-space form
-    terms = None
-    if lag and s.meta["interp"] == "lagrange_modes" and rank == 0:
-        tp = Plan(s.box, s.K, s.order, s.beta, precision=args.precision, skp_tol=s.skp_tol, max_n=s.n,
-                  interp="lagrange", modes=s.meta["modes"], skp_method="sinc")
-        tp.build_skp()
-        if not args.no_autotune:
-            tp.autotune(x, q)
-        for _ in range(3):
-            tp.energy_forces(x, q, forces=True, dEdq=True, out=out)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(args.steps):
-            tp.energy_forces(x, q, forces=True, dEdq=True, out=out)
-        b.record(stream)
-        b.synchronize()
-        t_ms = a.elapsed_time(b) / args.steps
-        terms = {"value": 1e3 / t_ms, "unit": "evals/s", "ms_per_step": t_ms,
-                 "note": "interp=lagrange: R dense Kronecker terms on the mode-product kernels (L2 not flushed)"}
-        tp.close()
+        # FP64 GPU form at the same SKP (the baseline the tensor path must beat)
+        if args.fp64_steps > 0:
+            plan.set_precision("fp64")
+            step()
+            torch.cuda.synchronize()
+            f_ms, _ = timed(args.fp64_steps)
+            res["fp64_form"] = {"value": args.fp64_steps / (f_ms * 1e-3), "unit": "evals/s",
+                                "ms_per_step": f_ms / args.fp64_steps, "steps": args.fp64_steps}
+            plan.set_precision(args.precision)
 
-    # FP64 GPU form at the same SKP (the baseline the tensor path must beat)
-    fp64 = None
-    if args.fp64_steps > 0:
-        plan.set_precision("fp64")
-        step()
-        torch.cuda.synchronize()
-        f_ms, _ = timed(args.fp64_steps)
-        fp64 = {"value": args.fp64_steps / (f_ms * 1e-3), "unit": "evals/s", "ms_per_step": f_ms / args.fp64_steps,
-                "steps": args.fp64_steps}
-        plan.set_precision(args.precision)
-
-    line = None
     if rank == 0:
         step()
         torch.cuda.synchronize()
-        gpu_out = (out["dEdq"].cpu().numpy(), out["forces"].cpu().numpy())
-        cb = None if args.no_cpu_baseline else cpu_baseline(s, gpu_out=gpu_out)
+        res["_gpu_out"] = (out["dEdq"].cpu().numpy(), out["forces"].cpu().numpy())
+    res["_system"] = s
+    plan.close()
+    return res
+
+
+# ncu tensor-pipe activity of the SKP kernels (sm__pipe_tensor_cycles_active, % of active
+# cycles, one capture per kernel) with the digest of the kernel sources it was taken on.
+SKP_TENSOR_ACTIVE = {
+    # profiles/mp_ozf_kernel_water_k64_bf16x10.md
+    ("water", "bf16x10"): {"digest": "15ac4d609920d908", "pct": {"mp_ozf_kernel<64>": 32.4}},
+}
+
+
+def _tensor_active(workload, precision):
+    rec = SKP_TENSOR_ACTIVE.get((workload, precision))
+    if not rec or rec["digest"] != _skp_digest():
+        return None
+    return {"pct_of_active_cycles": rec["pct"], "source": "ncu sm__pipe_tensor_cycles_active (profiles/)"}
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="large", choices=list(WORKLOAD_TEXT))
+    ap.add_argument("--precision", default="bf16x10")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="timed evaluations of the FP64 GPU form (default 1 for the 10^6-charge box, else 5)")
+    ap.add_argument("--no-water", action="store_true", help="skip the water box reported beside the headline")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch configuration")
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file: a matching entry is applied without timing, a new choice is "
+                         "appended (a profiling run then repeats the configuration of the plain run)")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    if args.fp64_steps is None:
+        args.fp64_steps = 1 if args.workload == "large" else 5
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = _init_dist(dev)
+    from paper_2601_18838_gb300 import build as _build
+    if rank == 0:
+        _build.build()
+    if pg:
+        pg.barrier()
+    ctx = (pg, dev, rank, ws, local)
+    m = _measure(args, args.workload, args.steps, args.warmup, ctx, headline=True)
+    water = None
+    if args.workload != "water" and not args.no_water:
+        w = _measure(args, "water", max(args.steps, 20), args.warmup, ctx, headline=False)
+        water = {k: w[k] for k in ("value", "unit", "ms_per_step", "roofline", "executed", "tensor_pipe_active",
+                                   "particle_kernels", "profile_ms_per_step", "skp_rank", "autotune") if k in w}
+        water["workload"] = WORKLOAD_TEXT["water"]
+        if rank == 0 and not args.no_cpu_baseline:
+            water["cpu_baseline"] = cpu_baseline(w["_system"], budget_s=10.0, max_evals=3, gpu_out=w["_gpu_out"])
+    if rank == 0:
+        cb = None if args.no_cpu_baseline else cpu_baseline(m["_system"], gpu_out=m["_gpu_out"])
         line = {
-            "metric": METRIC, "value": value, "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "metric": METRIC, "value": m["value"], "unit": "evals/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE.get(args.precision, args.precision), "data": "synthetic",
             "config": {"workload": WORKLOAD_TEXT[args.workload], "precision": args.precision,
-                       "skp_rank": R, "skp_r0": info["r0"], "skp_rel_err": skp_err,
-                       "autotune": ({k: tune[k] for k in ("tile", "fused", "split", "ms_per_eval")} if not args.no_autotune else "off"),
+                       "skp_rank": m["skp_rank"], "skp_r0": m["skp_r0"], "skp_rel_err": m["skp_rel_err"],
+                       "autotune": m["autotune"],
                        "l2": "flushed between steps (256 MB write outside the timed events)",
                        "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
-            "tflops_useful": useful / (ms_step * 1e-3) / 1e12,
-            "roofline": roof, "particle_kernels": part, "virial_tensor": vt, "e2e": e2e,
-            "gpu_launches": int(round(launches_per_step * args.steps)),
-            "fp64_form": fp64, "skp_terms_form": terms, "clocks": clocks, "cpu_baseline": cb,
-            "profile_ms_per_step": {k: v[0] / args.steps for k, v in prof.items()},
+            "tflops_useful": m["tflops_useful"], "roofline": m["roofline"], "executed": m.get("executed"),
+            "tensor_pipe_active": m.get("tensor_pipe_active"),
+            "particle_kernels": m["particle_kernels"], "e2e": m.get("e2e"),
+            "gpu_launches": int(round(m["launches_per_step"] * args.steps)),
+            "fp64_form": m.get("fp64_form"), "clocks": m["clocks"], "cpu_baseline": cb,
+            "profile_ms_per_step": m["profile_ms_per_step"], "water_box": water,
         }
         print(json.dumps(line), flush=True)
-    plan.close()
     if pg:
         pg.barrier()
         pg.destroy_process_group()

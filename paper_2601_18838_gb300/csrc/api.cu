@@ -50,6 +50,11 @@ void dfree(T*& p) {
 
 kpme_status_t dalloc(kpme_plan_t P, void** p, size_t bytes) {
   if (bytes == 0) bytes = 16;
+  if (P->fault_alloc_at > 0 && ++P->n_allocs == P->fault_alloc_at) {   // injected (KPME_FAULT=alloc)
+    *p = nullptr;
+    P->last_error = "cudaMalloc: injected allocation failure";
+    return KPME_ERR_OOM;
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     P->last_error = std::string("cudaMalloc: ") + cudaGetErrorString(e);
@@ -112,6 +117,7 @@ void release_skp_buffers(kpme_plan_t P) {
   dfree(P->d_rmZ);
   dfree(P->d_rmQ);
   dfree(P->d_rmY);
+  dfree(P->d_Qfold);
   free_joblist(P->stage1);
   free_joblist(P->stage1_res);
   free_joblist(P->stage23);
@@ -330,11 +336,15 @@ kpme_status_t install_skp(kpme_plan_t P) {
   const size_t eb = pi.tensor ? (size_t)pi.elem_bytes : mesh_elem(P);
   const int kind = pi.oz ? 4 : pi.tensor ? (pi.tf32 ? 3 : 2) : (pi.fp64 ? 0 : 1);
   kpme_status_t st;
+  // error-free split on circulant factors with K/2 a multiple of the 64-wide k chunk: the
+  // factors in the reflection basis (two K/2 x K/2 blocks each), half the digit products
+  P->fold = pi.oz && P->allow_fold && !S.dense && K % 128 == 0 && ozt_supported(K, 64, true, true);
+  const int kcols = P->fold ? K / 2 : K;   // stored columns of a factor row
 
   // factors
   auto mat = [&](const std::vector<double>& gen, int count, void** dst) -> kpme_status_t {
     kpme_status_t s2;
-    if ((s2 = dalloc(P, dst, (size_t)slices * count * K * K * eb)) != KPME_OK) return s2;
+    if ((s2 = dalloc(P, dst, (size_t)slices * count * K * kcols * eb)) != KPME_OK) return s2;
     double* dg = nullptr;
     KPME_CUDA_TRY(P, cudaMalloc((void**)&dg, gen.size() * sizeof(double)));
     cudaError_t e = cudaMemcpyAsync(dg, gen.data(), gen.size() * sizeof(double), cudaMemcpyHostToDevice, P->stream);
@@ -375,8 +385,9 @@ kpme_status_t install_skp(kpme_plan_t P) {
   if (pi.tensor && !pi.oz && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_Y, (size_t)islices * r0 * k3 * ieb)) != KPME_OK) return st;
   if (pi.tensor) choose_tc_tiles(P);
-  P->ozt_res = pi.oz && ozt_supported(K, P->tc_bn, true);
-  P->ozt_pp = pi.oz && ozt_supported(K, P->tc_bn, false);
+  P->ozt_res = pi.oz && ozt_supported(K, P->tc_bn, true, P->fold);
+  P->ozt_pp = pi.oz && ozt_supported(K, P->tc_bn, false, P->fold);
+  if (P->fold && !(P->ozt_res && P->ozt_pp)) return KPME_ERR_UNSUPPORTED;   // excluded above
   P->ozf = P->ozt_res && ozf_supported(K) && P->tc_bn == K && P->allow_fused;
   if (pi.oz) {
     const size_t k2 = (size_t)K * K;
@@ -384,6 +395,7 @@ kpme_status_t install_skp(kpme_plan_t P) {
       // A in tensor memory: Q and Y stay float32 and are cut by converter warps once per
       // item (shared by the item's pairs) with their row maxima
       if ((st = dalloc(P, (void**)&P->d_rmQ, k2 * sizeof(float))) != KPME_OK) return st;
+      if (P->fold && (st = dalloc(P, (void**)&P->d_Qfold, (size_t)k3 * sizeof(float))) != KPME_OK) return st;
       if ((st = dalloc(P, (void**)&P->d_rmY, (size_t)r0 * k2 * sizeof(float))) != KPME_OK) return st;
     } else {
       // Q and Y are read by several jobs each: they are cut into fixed-point slices once and
@@ -524,13 +536,16 @@ kpme_status_t install_skp(kpme_plan_t P) {
                      : (encode_tmap(P, &P->tm_Q, P->d_Qs, pi.elem_bytes, f32, K, KK, (uint64_t)slices, box0, 128) &&
                 encode_tmap(P, &P->tm_Y, P->d_Y, pi.elem_bytes, f32, K, KK, (uint64_t)slices * r0, box0, 128) &&
                 encode_tmap(P, &P->tm_Z, P->d_Z, pi.elem_bytes, f32, K, KK, (uint64_t)slices * G, box0, 128))) &&
-              encode_tmap(P, &P->tm_f3, P->d_fac3, pi.elem_bytes, f32, K, (uint64_t)r0 * K, slices, box0, P->tc_bn) &&
-              encode_tmap(P, &P->tm_f2, P->d_fac2, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn) &&
-              encode_tmap(P, &P->tm_f1, P->d_fac1, pi.elem_bytes, f32, K, (uint64_t)R * K, slices, box0, P->tc_bn);
+              encode_tmap(P, &P->tm_f3, P->d_fac3, pi.elem_bytes, f32, kcols, (uint64_t)r0 * K, slices, box0,
+                          P->tc_bn) &&
+              encode_tmap(P, &P->tm_f2, P->d_fac2, pi.elem_bytes, f32, kcols, (uint64_t)R * K, slices, box0,
+                          P->tc_bn) &&
+              encode_tmap(P, &P->tm_f1, P->d_fac1, pi.elem_bytes, f32, kcols, (uint64_t)R * K, slices, box0,
+                          P->tc_bn);
     if (ok && pi.oz && (P->ozt_res || P->ozt_pp)) {
       // float32 A operands for the tensor-memory kernel: 128 rows x 32 values per box
       ok = (P->ozf || encode_tmap(P, &P->tmF_Z, P->d_Z, 4, true, K, KK, (uint64_t)G, 32, 128)) &&
-           (!P->ozt_res || (encode_tmap(P, &P->tmF_Q, P->d_Qf, 4, true, K, KK, 1, 32, 128) &&
+           (!P->ozt_res || (encode_tmap(P, &P->tmF_Q, P->fold ? P->d_Qfold : P->d_Qf, 4, true, K, KK, 1, 32, 128) &&
                             encode_tmap(P, &P->tmF_Y, P->d_Y, 4, true, K, KK, (uint64_t)r0, 32, 128)));
     }
     if (!ok) return KPME_ERR_CUDA;
@@ -579,6 +594,12 @@ kpme_status_t check_device_status(kpme_plan_t P) {
   if (h && *h != DEV_OK) {
     *h = DEV_OK;
     P->last_error = "a bounded device wait gave up";
+    // a shortened budget (KPME_FAULT=budget) has done its work: later launches, and a graph
+    // captured again, get the production budget
+    if (P->wait_cycles != kWaitCycles) {
+      P->wait_cycles = kWaitCycles;
+      drop_graph(P);
+    }
     return KPME_ERR_TIMEOUT;
   }
   return KPME_OK;
@@ -630,7 +651,13 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
   if (pi.oz) {
     const int64_t k2 = (int64_t)K * K;
     const bool res = P->ozt_res;
-    if (res) {
+    if (res && P->fold) {
+      // the charge mesh in the reflection basis of its three axes (float32; the same launch
+      // clears Phi, which the following stages accumulate into) and its row maxima
+      StepScope sc(P, STEP_SPLIT, 2);
+      KPME_CUDA_TRY(P, launch_fold_mesh(P, Q.p, Q.dbl, P->d_Qfold, K, (float*)Phi, k3));
+      KPME_CUDA_TRY(P, launch_rowmax_rows(P, P->d_Qfold, k2, K, P->d_rmQ));
+    } else if (res) {
       // float32 charge mesh and its row maxima (rows of stage 1)
       StepScope sc(P, STEP_SPLIT, Q.dbl ? 2 : 1);
       if (Q.dbl) KPME_CUDA_TRY(P, launch_convert(Q.p, true, P->d_Qf, false, k3, P->stream));
@@ -659,6 +686,7 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       StepScope sc(P, STEP_SKP1, 1);
       OztArgs a{&P->tmF_Q, &P->tm_f3, P->d_rmQ, 0, (float*)P->d_Y, k3, 0, P->d_rmY, k2, M, K, K, 2, true,
                 &P->stage1_res};
+      a.fold = P->fold;
       KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
     } else {
       {
@@ -678,6 +706,7 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
         if (res) {
           OztArgs a{&P->tmF_Y, &P->tm_f2, P->d_rmY, k2, (float*)P->d_Z, k3, g.t0, P->d_rmZ, k2, M, K, K, 2, true,
                     &g.stage2_res};
+          a.fold = P->fold;
           KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
         } else {
           OzArgs a{&P->tm_f2, &P->tm_Y, S.r0, nullptr, false, 0, nullptr, 0, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K,
@@ -688,12 +717,17 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       StepScope sc(P, STEP_SKP3, 1);
       if (P->ozt_pp) {
         OztArgs a{&P->tmF_Z, &P->tm_f1, P->d_rmZ, k2, (float*)Phi, 0, 0, nullptr, 0, M, K, K, 1, false, &g.stage3};
+        a.fold = P->fold;
         KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
       } else {
         OzArgs a{&P->tm_f1, nullptr, 0, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1,
                  &g.stage3};
         KPME_CUDA_TRY(P, launch_mp_oz(P, a));
       }
+    }
+    if (P->fold) {   // Phi back from the reflection basis (in place)
+      StepScope sc(P, STEP_SKP3, 1);
+      KPME_CUDA_TRY(P, launch_unfold_mesh(P, (float*)Phi, K));
     }
     return KPME_OK;
   }
@@ -810,8 +844,49 @@ kpme_status_t gather_mesh(kpme_plan_t P, int64_t n, const double* x, const doubl
   return KPME_OK;
 }
 
+// Fault injection for the tests of the error paths, from the environment variable KPME_FAULT
+// read when a plan is made (host side only; nothing is made to fault on the device):
+//   alloc[:N]  the N-th device allocation of the plan (default the first) fails as out of memory;
+//   plan       the plan's handle check word is spoiled before kpme_plan returns, as if the handle
+//              were overwritten: every later call on it reports KPME_ERR_INVALID_ARG;
+//   timeout    the device status word is raised as a bounded device wait raises it when it gives
+//              up: the next call that reads it (an evaluation, kpme_build_skp) reports
+//              KPME_ERR_TIMEOUT and clears it, the calls after run normally;
+//   budget[:C] every bounded device wait of the plan's kernels gets a budget of C cycles
+//              (default 1), so the first wait not already satisfied gives up and the kernels
+//              let their copies and MMAs in flight complete, release tensor memory and return;
+//              the next call reports KPME_ERR_TIMEOUT and restores the production budget.
+struct FaultSpec {
+  int alloc_at = 0;
+  bool plan = false, timeout = false;
+  long long budget = 0;
+};
+FaultSpec parse_fault() {
+  FaultSpec f;
+  const char* e = getenv("KPME_FAULT");
+  if (!e || !*e) return f;
+  const std::string s(e);
+  const size_t colon = s.find(':');
+  const std::string site = s.substr(0, colon);
+  const long long arg = colon == std::string::npos ? 0 : atoll(s.c_str() + colon + 1);
+  if (site == "alloc") f.alloc_at = arg > 0 ? (int)arg : 1;
+  if (site == "plan") f.plan = true;
+  if (site == "timeout") f.timeout = true;
+  if (site == "budget") f.budget = arg > 0 ? arg : 1;
+  return f;
+}
+
+bool plan_ok(kpme_plan_t P) {
+  if (!P) return false;
+  if (P->magic != kPlanMagic) {
+    P->last_error = "corrupted plan handle";
+    return false;
+  }
+  return true;
+}
+
 kpme_status_t common_checks(kpme_plan_t P, int64_t n) {
-  if (!P) return KPME_ERR_INVALID_ARG;
+  if (!plan_ok(P)) return KPME_ERR_INVALID_ARG;
   if (n < 0) return KPME_ERR_INVALID_ARG;
   if (n > P->max_n) return KPME_ERR_CAPACITY;
   kpme_status_t st = check_device_status(P);
@@ -926,7 +1001,13 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->d_sumq = acc;
   P->d_energy = acc + 1;
   P->d_qpsi = acc + 2;
+  {
+    const FaultSpec f = parse_fault();
+    P->fault_alloc_at = f.alloc_at;
+    if (f.budget > 0) P->wait_cycles = f.budget;
+  }
   P->allow_fused = getenv_flag("KPME_FUSED", true);
+  P->allow_fold = getenv_flag("KPME_FOLD", true);
   P->tile = 0;
   if (lag) {   // the cell sort of the per-cell form: counters and records
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);
@@ -953,6 +1034,12 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->single.h_pairs = {make_int2(0, 0)};
   if ((st = upload_joblist(P, P->single)) != KPME_OK) return fail(st);
   if (cudaStreamSynchronize(P->stream) != cudaSuccess) return fail(KPME_ERR_CUDA);
+  P->magic = kPlanMagic;
+  {
+    const FaultSpec f = parse_fault();
+    if (f.plan) P->magic = ~kPlanMagic;
+    if (f.timeout) *reinterpret_cast<volatile int*>(P->d_status) = DEV_TIMEOUT;
+  }
   *out = P;
   return KPME_OK;
 }
@@ -984,6 +1071,7 @@ void kpme_destroy(kpme_plan_t P) {
     cudaEventDestroy(pe.second.second);
   }
   for (auto e : P->event_pool) cudaEventDestroy(e);
+  P->magic = 0;
   delete P;
 }
 
@@ -994,7 +1082,7 @@ kpme_status_t kpme_set_stream(kpme_plan_t P, void* stream) {
 }
 
 kpme_status_t kpme_set_precision(kpme_plan_t P, int precision) {
-  if (!P || !valid_precision(precision)) return KPME_ERR_INVALID_ARG;
+  if (!plan_ok(P) || !valid_precision(precision)) return KPME_ERR_INVALID_ARG;
   const PrecInfo pi = prec_info(precision);
   if (pi.tensor && (P->cc_major != 10 || P->p.K % 16 != 0)) {
     P->last_error = "tensor-core precisions need an sm_103 device and K divisible by 16";
@@ -1011,7 +1099,7 @@ kpme_status_t kpme_set_precision(kpme_plan_t P, int precision) {
 }
 
 kpme_status_t kpme_build_skp(kpme_plan_t P, int* rank_out, double* err_out) {
-  if (!P) return KPME_ERR_INVALID_ARG;
+  if (!plan_ok(P)) return KPME_ERR_INVALID_ARG;
   KPME_CUDA_TRY(P, cudaSetDevice(P->device));
   SkpHost S;
   kpme_status_t st = lagrange(P) ? build_skp_lagrange(P, S)
@@ -1026,7 +1114,7 @@ kpme_status_t kpme_build_skp(kpme_plan_t P, int* rank_out, double* err_out) {
 
 kpme_status_t kpme_set_skp(kpme_plan_t P, int r0, const int* r1, const double* gen3, const double* gen2,
                            const double* gen1, double c) {
-  if (!P || r0 <= 0 || !r1 || !gen3 || !gen2 || !gen1 || !std::isfinite(c)) return KPME_ERR_INVALID_ARG;
+  if (!plan_ok(P) || r0 <= 0 || !r1 || !gen3 || !gen2 || !gen1 || !std::isfinite(c)) return KPME_ERR_INVALID_ARG;
   if (lagrange(P)) return KPME_ERR_UNSUPPORTED;   // its factors are dense, built by kpme_build_skp
   KPME_CUDA_TRY(P, cudaSetDevice(P->device));
   const int K = P->p.K;
@@ -1271,7 +1359,8 @@ kpme_status_t kpme_get_info(kpme_plan_t P, kpme_info_t* info) {
   info->scratch_bytes = P->scratch_bytes;
   info->flops_useful = 6.0 * info->R * K * K * K * K;
   const double mp = 2.0 * K * K * K * K;   // one mode product of one term
-  const double per_eval = (info->r0 + 2.0 * info->R) * mp;
+  // (folded factors: every product contracts K/2 values)
+  const double per_eval = (info->r0 + 2.0 * info->R) * mp * (P->fold ? 0.5 : 1.0);
   info->flops_executed = per_eval * (P->prec.tensor ? P->prec.n_products : 1);
   if (lagrange_modes(P) && P->skp.valid) {   // three forward and three backward transforms
     const double r = 2.0 * P->p.modes + 1.0;
@@ -1279,6 +1368,7 @@ kpme_status_t kpme_get_info(kpme_plan_t P, kpme_info_t* info) {
   }
   int kernels = 1 /*spread*/ + 1 /*gather*/ + 1 /*stage 1*/ + 2 * (int)P->groups.size();
   if (P->prec.tensor) kernels += 1;
+  if (P->fold) kernels += 2;   // fold of Q (with the row maxima launch), unfold of Phi
   info->kernels_per_eval = kernels;
   return KPME_OK;
 }

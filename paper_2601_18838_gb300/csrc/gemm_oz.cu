@@ -46,6 +46,7 @@ struct OzParams {
   int n_jobs, n_pairs;
   int nbatch_a;      // batches per slice plane of the pre-sliced A (TMA mode)
   int* status;
+  long long wait_cycles;   // budget of one bounded wait (clock cycles)
 };
 
 // Persistent CTA, work items (m-tile, n-tile, job) strided by gridDim.x, every role walking
@@ -70,8 +71,10 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
   uint64_t* empty = full_b + S;
   uint64_t* acc_full = empty + S;
   uint64_t* acc_empty = acc_full + 2;
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(acc_empty + 2);
+  uint64_t* drain_bar = acc_empty + 2;   // the MMA issuer's last commit, on the way out
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(drain_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
+  const WaitCtl wc{abort_flag, prm.status, prm.wait_cycles};
   // per-warp column maxima of the epilogue (4 x BN)
   unsigned int* red = reinterpret_cast<unsigned int*>(smem + S * prm.stage_bytes + 256);
   // the job tables live in shared memory: every role reads them for every item and pair
@@ -96,6 +99,7 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 128);
     }
+    mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -132,7 +136,7 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
           for (int c = 0; c < kchunks; ++c, ++it) {
             const int s = it % S;
             const uint32_t ph = (uint32_t)(it / S) & 1u;
-            if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) break;
+            if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, wc)) break;
             uint8_t* sa = smem + s * prm.stage_bytes;
             uint8_t* sb = sa + kSlices * kASlice;
             if constexpr (A_TMA) {
@@ -148,6 +152,9 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
           }
         }
       }
+      // loads in flight land before the CTA leaves (at once unless a wait gave up)
+      drain_ring(full_b, S, it, prm.status);
+      if constexpr (A_TMA) drain_ring(full_a, S, it, prm.status);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -160,13 +167,13 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
         const int np = s_start[job + 1] - s_start[job];
         for (int pl = 0; pl < np && !*abort_flag; ++pl, ++pc) {
           const int buf = pc & 1;
-          if (pc >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((pc >> 1) - 1) & 1u, abort_flag, prm.status)) break;
+          if (pc >= 2 && !mbar_wait(&acc_empty[buf], (uint32_t)((pc >> 1) - 1) & 1u, wc)) break;
           fence_after();
           const uint32_t d0 = tmem + (uint32_t)(buf * 2 * BN), d1 = d0 + BN;
           for (int c = 0; c < kchunks; ++c, ++it) {
             const int s = it % S;
             const uint32_t ph = (uint32_t)(it / S) & 1u;
-            if (!mbar_wait(&full_a[s], ph, abort_flag, prm.status) || !mbar_wait(&full_b[s], ph, abort_flag, prm.status))
+            if (!mbar_wait(&full_a[s], ph, wc) || !mbar_wait(&full_b[s], ph, wc))
               break;
             fence_after();
             int ksteps = (prm.Kr - c * kChunk + 15) / 16;
@@ -199,6 +206,9 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
           mma_commit(&acc_full[buf]);
         }
       }
+      // every MMA issued has completed before tensor memory is released
+      mma_commit(drain_bar);
+      mbar_drain(drain_bar, 0, prm.status);
     }
   } else if (warp < 2 + NCONV) {
     // ---------------- converters (operand rows sliced on the fly) ----------------
@@ -219,7 +229,7 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
       auto process = [&](const float (&v)[kV], float rm) -> bool {
         const int s = it % S;
         const uint32_t ph = (uint32_t)(it / S) & 1u;
-        if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) return false;
+        if (it >= S && !mbar_wait(&empty[s], ph ^ 1u, wc)) return false;
         int e = 0;
         frexpf(rm, &e);
         uint8_t* sa = smem + s * prm.stage_bytes;
@@ -295,8 +305,7 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
       for (int pl = 0; pl < np; ++pl, ++pc) {
         if (!ok) continue;
         const int buf = pc & 1;
-        const bool got = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(pc >> 1) & 1u, abort_flag,
-                                                           prm.status));
+        const bool got = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(pc >> 1) & 1u, wc));
         if (!got) {
           ok = false;
           continue;
@@ -505,6 +514,7 @@ cudaError_t launch_mp_oz(kpme_plan_t P, const OzArgs& a) {
   prm.n_jobs = a.jobs->n_jobs;
   prm.nbatch_a = a.nbatch_a;
   prm.status = P->d_status;
+  prm.wait_cycles = P->wait_cycles;
   prm.n_pairs = (int)a.jobs->h_pairs.size();
   const int smem = oz_smem_bytes(P->tc_bn, P->tc_stages) + prm.n_pairs * (int)sizeof(int2) +
                    (prm.n_jobs + 1) * (int)sizeof(int);

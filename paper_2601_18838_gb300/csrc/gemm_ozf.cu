@@ -51,6 +51,7 @@ struct OzfParams {
   const int* cta;      // CTA c runs items [cta[c], cta[c + 1])
   int n_pairs, max_items;
   int* status;
+  long long wait_cycles;   // budget of one bounded wait (clock cycles)
 };
 
 // float offset of (row, k) in a 128 x 64 float tile stored as two swizzled 128 x 32 boxes
@@ -139,8 +140,10 @@ __global__ void __launch_bounds__(kThreads, 1)
   uint64_t* empty_z = full_z + 2;      // [2]
   uint64_t* full_a3 = empty_z + 2;     // [2] tensor-memory slots for Z_t digits
   uint64_t* empty_a3 = full_a3 + 2;    // [2]
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(empty_a3 + 2);
+  uint64_t* drain_bar = empty_a3 + 2;  // both MMA issuers' last commits, on the way out
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(drain_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
+  const WaitCtl wc{abort_flag, prm.status, prm.wait_cycles};
   int2* s_pairs = reinterpret_cast<int2*>(reinterpret_cast<uint8_t*>(bars) + kBarBytes);
   int4* s_items = reinterpret_cast<int4*>(s_pairs + ((prm.n_pairs + 1) & ~1));   // 16-byte aligned
   const int i_first = prm.cta[blockIdx.x];
@@ -169,6 +172,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_init(&full_a3[b], 4);
       mbar_init(&empty_a3[b], 2);  // the op's owner (commit) and the other MMA thread
     }
+    mbar_init(drain_bar, 2);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -243,7 +247,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           step(c);
           const int s = ib % prm.sb;
           if (ib >= prm.sb &&
-              !mbar_wait(&empty_b[s], ((uint32_t)(ib / prm.sb) & 1u) ^ 1u, abort_flag, prm.status)) {
+              !mbar_wait(&empty_b[s], ((uint32_t)(ib / prm.sb) & 1u) ^ 1u, wc)) {
             ok = false;
             break;
           }
@@ -255,6 +259,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++ib;
         }
       }
+      drain_ring(full_b, prm.sb, ib, prm.status);   // loads in flight land before the CTA leaves
     }
   } else if (warp == 1 || warp == 10) {
     if (lane == 0) {
@@ -301,17 +306,17 @@ __global__ void __launch_bounds__(kThreads, 1)
           // the op's operands, observed by both threads in sequence order
           if (s2) {
             if (newo_u) {
-              if (!mbar_wait(full_a2, (uint32_t)ia2 & 1u, abort_flag, prm.status)) {
+              if (!mbar_wait(full_a2, (uint32_t)ia2 & 1u, wc)) {
                 ok = false;
                 break;
               }
               ++ia2;
             }
-          } else if (!mbar_wait(&full_a3[slot], (uint32_t)(ja3 / kA3) & 1u, abort_flag, prm.status)) {
+          } else if (!mbar_wait(&full_a3[slot], (uint32_t)(ja3 / kA3) & 1u, wc)) {
             ok = false;
             break;
           }
-          if (!mbar_wait(&full_b[s], (uint32_t)(ib / prm.sb) & 1u, abort_flag, prm.status)) {
+          if (!mbar_wait(&full_b[s], (uint32_t)(ib / prm.sb) & 1u, wc)) {
             ok = false;
             break;
           }
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             ++ib;
             continue;
           }
-          if (jd >= 2 && !mbar_wait(&d_empty[db], ((uint32_t)(jd >> 1) & 1u) ^ 1u, abort_flag, prm.status)) {
+          if (jd >= 2 && !mbar_wait(&d_empty[db], ((uint32_t)(jd >> 1) & 1u) ^ 1u, wc)) {
             ok = false;
             break;
           }
@@ -365,6 +370,9 @@ __global__ void __launch_bounds__(kThreads, 1)
           ++ib;
         }
       }
+      // every MMA issued by either thread has completed before tensor memory is released
+      mma_commit(drain_bar);
+      mbar_drain(drain_bar, 0, prm.status);
     }
   } else if (warp < 6) {
     // ---------- converters: digits of Y_i rows (shared memory) and of Z_t rows (tensor memory) ----------
@@ -390,7 +398,7 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
           for (int q = 0; q < K / 4; ++q) y[q] = __ldg(y4 + q);
           if (ia2 >= 1 &&
-              !__all_sync(0xffffffffu, mbar_wait(empty_a2, ((uint32_t)ia2 & 1u) ^ 1u, abort_flag, prm.status))) {
+              !__all_sync(0xffffffffu, mbar_wait(empty_a2, ((uint32_t)ia2 & 1u) ^ 1u, wc))) {
             ok = false;
             break;
           }
@@ -402,9 +410,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         if (t == 0) continue;
         const int zb = jz & 1, slot = ja3 % kA3;
-        if (!__all_sync(0xffffffffu, mbar_wait(&full_z[zb], (uint32_t)(jz >> 1) & 1u, abort_flag, prm.status)) ||
+        if (!__all_sync(0xffffffffu, mbar_wait(&full_z[zb], (uint32_t)(jz >> 1) & 1u, wc)) ||
             (ja3 >= kA3 && !__all_sync(0xffffffffu, mbar_wait(&empty_a3[slot], ((uint32_t)(ja3 / kA3) & 1u) ^ 1u,
-                                                              abort_flag, prm.status)))) {
+                                                              wc)))) {
           ok = false;
           break;
         }
@@ -418,6 +426,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         ++ja3;
       }
     }
+    tmem_wait_st();
   } else {
     // ---------------- epilogue, in the MMA's op order ----------------
     // step 2 of term j: Z_t = D0 + D1 written transposed (thread = tile row m = (k3' = m / K,
@@ -447,9 +456,8 @@ __global__ void __launch_bounds__(kThreads, 1)
         if (!ok) continue;
         const int zb = jz & 1;
         if ((s2 && jz >= 2 &&
-             !__all_sync(0xffffffffu, mbar_wait(&empty_z[zb], ((uint32_t)(jz >> 1) & 1u) ^ 1u, abort_flag,
-                                                prm.status))) ||
-            !__all_sync(0xffffffffu, mbar_wait(&d_full[jd & 1], (uint32_t)(jd >> 1) & 1u, abort_flag, prm.status))) {
+             !__all_sync(0xffffffffu, mbar_wait(&empty_z[zb], ((uint32_t)(jz >> 1) & 1u) ^ 1u, wc))) ||
+            !__all_sync(0xffffffffu, mbar_wait(&d_full[jd & 1], (uint32_t)(jd >> 1) & 1u, wc))) {
           ok = false;
           continue;
         }
@@ -547,6 +555,7 @@ cudaError_t launch_mp_ozf(kpme_plan_t P, const OzfArgs& a) {
   for (size_t c = 0; c + 1 < a.jobs->h_cta.size(); ++c)
     prm.max_items = std::max(prm.max_items, a.jobs->h_cta[c + 1] - a.jobs->h_cta[c]);
   prm.status = P->d_status;
+  prm.wait_cycles = P->wait_cycles;
   if (a.K == 64) return launch_k<64>(P, a, prm);
   if (a.K == 32) return launch_k<32>(P, a, prm);
   return cudaErrorInvalidValue;

@@ -16,10 +16,17 @@
 //     next stage's row maxima (mode 2);
 //   * otherwise (stage 3) every pair has its own A (Z_t), cut per 64-wide chunk into a ring of
 //     two tensor-memory slots, and the item's pairs are summed (mode 1, float32 atomics).
+// Folded factors (fold): every factor is a real symmetric circulant, so it commutes with the
+// reflection a <-> K - 1 - a of its axis, which has no fixed point for even K; in the basis of
+// sums x(a) + x(K-1-a) and differences x(a) - x(K-1-a) it is block diagonal with two K/2 x K/2
+// blocks.  With the mesh in that basis on all three axes, an item whose output columns lie in
+// one half contracts only the K/2 values of that half: half the digit products of every stage.
 // All waits are bounded; a wait that runs out raises the device status word and every role
 // drains without further waits.
 #include "kpme_internal.cuh"
 #include "tc_common.cuh"
+
+#include <algorithm>
 
 namespace kpme {
 namespace {
@@ -35,6 +42,8 @@ constexpr int kBarBytes = 512;
 
 struct OztParams {
   int M, N, Kr, kchunks;
+  int kc;               // contracted values per item: Kr, or Kr / 2 with folded factors
+  int fold;             // folded: items of output columns n >= Kr / 2 read A columns [Kr/2, Kr)
   int sb, bstage;       // factor ring: stages and bytes per stage
   int sf;               // float32 staging stages
   int nacc, nat;        // accumulator buffers (2 BN columns each); A slots
@@ -51,6 +60,7 @@ struct OztParams {
   const int2* pairs;
   int n_jobs, n_pairs;
   int* status;
+  long long wait_cycles;   // budget of one bounded wait (clock cycles)
 };
 
 template <int NCONV>
@@ -77,8 +87,10 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
   uint64_t* empty_t = full_t + prm.nat;
   uint64_t* acc_full = empty_t + prm.nat;
   uint64_t* acc_empty = acc_full + prm.nacc;
-  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(acc_empty + prm.nacc);
+  uint64_t* drain_bar = acc_empty + prm.nacc;   // the MMA issuer's last commit, on the way out
+  uint32_t* taddr_slot = reinterpret_cast<uint32_t*>(drain_bar + 1);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(taddr_slot + 1);
+  const WaitCtl wc{abort_flag, prm.status, prm.wait_cycles};
   unsigned int* red = reinterpret_cast<unsigned int*>(reinterpret_cast<uint8_t*>(full_b) + kBarBytes);
   // the job tables live in shared memory: every role reads them for every item and pair
   int2* s_pairs = reinterpret_cast<int2*>(red + 4 * BN);
@@ -110,6 +122,7 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
       mbar_init(&acc_full[b], 1);
       mbar_init(&acc_empty[b], 128);
     }
+    mbar_init(drain_bar, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -132,29 +145,32 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
     n0 = (rem / m_tiles) * BN;
     m0 = (rem % m_tiles) * kBM;
   };
-  // boxes of chunk c that hold valid k (the second is skipped when it starts at or past Kr)
-  auto boxes = [&](int c) { return (c * kChunk + 32 < prm.Kr) ? 2 : 1; };
+  // boxes of chunk c that hold valid k (the second is skipped when it starts at or past kc)
+  auto boxes = [&](int c) { return (c * kChunk + 32 < prm.kc) ? 2 : 1; };
+  // first A column of an item: its output half's block on folded factors
+  auto a_k0 = [&](int n0) { return (prm.fold && n0 >= prm.Kr / 2) ? prm.Kr / 2 : 0; };
 
   if (warp == 0) {
     if (lane == 0) {
       // ---------------- TMA: float32 A boxes and factor digits ----------------
       int jf = 0, ib = 0;
       bool ok = true;
-      auto load_f = [&](int plane, int m0, int c) -> bool {
+      auto load_f = [&](int plane, int m0, int k0, int c) -> bool {
         const int s = jf % prm.sf;
         const uint32_t ph = (uint32_t)(jf / prm.sf) & 1u;
-        if (jf >= prm.sf && !mbar_wait(&empty_f[s], ph ^ 1u, abort_flag, prm.status)) return false;
+        if (jf >= prm.sf && !mbar_wait(&empty_f[s], ph ^ 1u, wc)) return false;
         uint8_t* dst = ring_f + s * kFStage;
         const int nb = boxes(c);
         mbar_expect_tx(&full_f[s], (uint32_t)(nb * kFBox));
-        for (int b = 0; b < nb; ++b) tma_load_3d(dst + b * kFBox, &tmF, &full_f[s], c * kChunk + 32 * b, m0, plane);
+        for (int b = 0; b < nb; ++b)
+          tma_load_3d(dst + b * kFBox, &tmF, &full_f[s], k0 + c * kChunk + 32 * b, m0, plane);
         ++jf;
         return true;
       };
       auto load_b = [&](int fac, int n0, int c) -> bool {
         const int s = ib % prm.sb;
         const uint32_t ph = (uint32_t)(ib / prm.sb) & 1u;
-        if (ib >= prm.sb && !mbar_wait(&empty_b[s], ph ^ 1u, abort_flag, prm.status)) return false;
+        if (ib >= prm.sb && !mbar_wait(&empty_b[s], ph ^ 1u, wc)) return false;
         uint8_t* dst = ring_b + s * prm.bstage;
         mbar_expect_tx(&full_b[s], (uint32_t)(kSlices * kBSlice));
 #pragma unroll
@@ -167,18 +183,22 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
         int m0, n0, job;
         decode(w, m0, n0, job);
         const int p0 = s_start[job], p1 = s_start[job + 1];
+        const int k0 = a_k0(n0);
         if constexpr (A_RES) {
           const int plane = s_pairs[p0].x;
-          for (int c = 0; c < kchunks && ok; ++c) ok = load_f(plane, m0, c);
+          for (int c = 0; c < kchunks && ok; ++c) ok = load_f(plane, m0, k0, c);
         }
         for (int p = p0; p < p1 && ok; ++p) {
           const int2 pr = s_pairs[p];
           for (int c = 0; c < kchunks && ok; ++c) {
-            if constexpr (!A_RES) ok = load_f(pr.x, m0, c);
+            if constexpr (!A_RES) ok = load_f(pr.x, m0, k0, c);
             if (ok) ok = load_b(pr.y, n0, c);
           }
         }
       }
+      // loads in flight land before the CTA leaves (at once unless a wait gave up)
+      drain_ring(full_f, prm.sf, jf, prm.status);
+      drain_ring(full_b, prm.sb, ib, prm.status);
     }
   } else if (warp == 1) {
     if (lane == 0) {
@@ -194,14 +214,14 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
         uint32_t a_item = 0;
         if constexpr (A_RES) {
           slot = it % prm.nat;
-          if (!mbar_wait(&full_t[slot], (uint32_t)(it / prm.nat) & 1u, abort_flag, prm.status)) break;
+          if (!mbar_wait(&full_t[slot], (uint32_t)(it / prm.nat) & 1u, wc)) break;
           fence_after();
           a_item = tmem + (uint32_t)(prm.a_col0 + slot * prm.at_cols);
         }
         for (int pl = 0; pl < np && ok; ++pl, ++pc) {
           const int buf = pc % prm.nacc;
           if (pc >= prm.nacc &&
-              !mbar_wait(&acc_empty[buf], (uint32_t)((pc / prm.nacc) - 1) & 1u, abort_flag, prm.status)) {
+              !mbar_wait(&acc_empty[buf], (uint32_t)((pc / prm.nacc) - 1) & 1u, wc)) {
             ok = false;
             break;
           }
@@ -213,19 +233,19 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
               a_c = a_item + (uint32_t)(c * kChunkCols);
             } else {
               slot = it % prm.nat;
-              if (!mbar_wait(&full_t[slot], (uint32_t)(it / prm.nat) & 1u, abort_flag, prm.status)) {
+              if (!mbar_wait(&full_t[slot], (uint32_t)(it / prm.nat) & 1u, wc)) {
                 ok = false;
                 break;
               }
               a_c = tmem + (uint32_t)(prm.a_col0 + slot * prm.at_cols);
             }
             const int s = ib % prm.sb;
-            if (!mbar_wait(&full_b[s], (uint32_t)(ib / prm.sb) & 1u, abort_flag, prm.status)) {
+            if (!mbar_wait(&full_b[s], (uint32_t)(ib / prm.sb) & 1u, wc)) {
               ok = false;
               break;
             }
             fence_after();
-            int ksteps = (prm.Kr - c * kChunk + 15) / 16;
+            int ksteps = (prm.kc - c * kChunk + 15) / 16;
             ksteps = ksteps > 4 ? 4 : ksteps;
             // one descriptor per stage; the digit planes and k steps are compile-time offsets
             // added to its 14-bit address field (addresses stay below 256 KB: no carry)
@@ -265,6 +285,9 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
           ++it;
         }
       }
+      // every MMA issued has completed before tensor memory is released
+      mma_commit(drain_bar);
+      mbar_drain(drain_bar, 0, prm.status);
     }
   } else if (warp < kEpi0) {
     // ---------------- converters: float32 rows -> digits in tensor memory ----------------
@@ -294,8 +317,7 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
         if constexpr (A_RES) {
           slot = it % prm.nat;
           if (it >= prm.nat &&
-              !__all_sync(0xffffffffu, mbar_wait(&empty_t[slot], ((uint32_t)(it / prm.nat) & 1u) ^ 1u, abort_flag,
-                                                 prm.status))) {
+              !__all_sync(0xffffffffu, mbar_wait(&empty_t[slot], ((uint32_t)(it / prm.nat) & 1u) ^ 1u, wc))) {
             ok = false;
             break;
           }
@@ -305,7 +327,7 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
         for (int c = 0; c < kchunks; ++c) {
           const int s = jf % prm.sf;
           if (!__all_sync(0xffffffffu,
-                          mbar_wait(&full_f[s], (uint32_t)(jf / prm.sf) & 1u, abort_flag, prm.status))) {
+                          mbar_wait(&full_f[s], (uint32_t)(jf / prm.sf) & 1u, wc))) {
             ok = false;
             break;
           }
@@ -333,7 +355,7 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
             slot = it % prm.nat;
             if (it >= prm.nat &&
                 !__all_sync(0xffffffffu, mbar_wait(&empty_t[slot], ((uint32_t)(it / prm.nat) & 1u) ^ 1u,
-                                                   abort_flag, prm.status))) {
+                                                   wc))) {
               ok = false;
               break;
             }
@@ -343,7 +365,7 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
 #pragma unroll
           for (int hh = 0; hh < kHalves; ++hh) {
             const int h = h_first + hh;
-            if (c * kChunk + 32 * h >= prm.Kr) continue;   // warp-uniform: k half past the end
+            if (c * kChunk + 32 * h >= prm.kc) continue;   // warp-uniform: k half past the end
             uint4 o[4][kSlices];
 #pragma unroll
             for (int g = 0; g < 4; ++g) slice8(v[hh] + 8 * g, e, o[g]);
@@ -376,6 +398,7 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
         }
       }
     }
+    tmem_wait_st();   // a unit given up half cut: its stores complete before the release
   } else {
     // ---------------- epilogue ----------------
     // Every epilogue thread runs every item and every pair, and (mode 2) the same number of
@@ -402,7 +425,7 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
         if (ok) {
           const int buf = pc % prm.nacc;
           const bool got = __all_sync(0xffffffffu, mbar_wait(&acc_full[buf], (uint32_t)(pc / prm.nacc) & 1u,
-                                                             abort_flag, prm.status));
+                                                             wc));
           if (!got) {
             ok = false;
           } else {
@@ -541,20 +564,24 @@ cudaError_t launch_bn(const OztArgs& a, cudaStream_t st, const OztParams& prm, d
 
 }  // namespace
 
-bool ozt_supported(int K, int bn, bool a_res) {
+bool ozt_supported(int K, int bn, bool a_res, bool fold) {
   if (K % 32 != 0 || (bn != 32 && bn != 48 && bn != 64) || K % bn != 0) return false;
-  const OztConfig c = ozt_config(bn, K, a_res);
+  if (fold && (K % 128 != 0 || (K / 2) % bn != 0)) return false;
+  const OztConfig c = ozt_config(bn, fold ? K / 2 : K, a_res);
   return c.nat >= 1 && c.nacc >= 2 && c.a_col0 + c.nat * c.at_cols <= 512 && c.sb >= 2 && c.smem <= 227 * 1024;
 }
 
 cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
   const int bn = P->tc_bn;
-  const OztConfig c = ozt_config(bn, a.Kr, a.a_res);
+  const int kc = a.fold ? a.Kr / 2 : a.Kr;
+  const OztConfig c = ozt_config(bn, kc, a.a_res);
   OztParams prm{};
   prm.M = a.M;
   prm.N = a.N;
   prm.Kr = a.Kr;
-  prm.kchunks = (a.Kr + kChunk - 1) / kChunk;
+  prm.kc = kc;
+  prm.fold = a.fold ? 1 : 0;
+  prm.kchunks = (kc + kChunk - 1) / kChunk;
   prm.sb = c.sb;
   prm.bstage = kSlices * bn * 128;
   prm.sf = c.sf;
@@ -574,6 +601,7 @@ cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
   prm.pairs = a.jobs->d_pairs;
   prm.n_jobs = a.jobs->n_jobs;
   prm.status = P->d_status;
+  prm.wait_cycles = P->wait_cycles;
   prm.n_pairs = (int)a.jobs->h_pairs.size();
   const int smem = c.smem + prm.n_pairs * (int)sizeof(int2) + (prm.n_jobs + 1) * (int)sizeof(int);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
@@ -585,6 +613,87 @@ cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
     case 64: return launch_bn<64>(a, P->stream, prm, grid, smem);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// The reflection basis of a K^3 mesh (K even).  On each axis the mirror points a and K - 1 - a
+// (a < K/2) are replaced by their sum (stored at a) and difference (stored at K - 1 - a); one
+// thread takes the octet of mirror points of (a1, a2, a3), reads its eight values, applies the
+// butterfly on the three axes in float64 and writes the eight results, rounded once to float32.
+// The unfolding applies the same butterfly and the factor 1/8 (the butterfly squared is twice
+// the identity per axis); it reads and writes the same octet, so it runs in place.
+template <typename TIN, bool UNFOLD>
+__global__ void fold_mesh_kernel(const TIN* in, float* out, int K, float* __restrict__ zero,
+                                 int64_t nz) {
+  const int h = K / 2;
+  const int64_t n_oct = (int64_t)h * h * h;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_oct; o += stride) {
+    const int a3 = (int)(o % h), a2 = (int)((o / h) % h), a1 = (int)(o / ((int64_t)h * h));
+    const int p1[2] = {a1, K - 1 - a1}, p2[2] = {a2, K - 1 - a2}, p3[2] = {a3, K - 1 - a3};
+    double v[2][2][2];
+#pragma unroll
+    for (int s1 = 0; s1 < 2; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+        for (int s3 = 0; s3 < 2; ++s3) v[s1][s2][s3] = (double)in[((int64_t)p1[s1] * K + p2[s2]) * K + p3[s3]];
+    // one axis after the other (each butterfly reads values the previous axis finished)
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const double a = v[i][j][0], b = v[i][j][1];
+        v[i][j][0] = a + b;
+        v[i][j][1] = a - b;
+      }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const double a = v[i][0][j], b = v[i][1][j];
+        v[i][0][j] = a + b;
+        v[i][1][j] = a - b;
+      }
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        const double a = v[0][i][j], b = v[1][i][j];
+        v[0][i][j] = a + b;
+        v[1][i][j] = a - b;
+      }
+    const double scale = UNFOLD ? 0.125 : 1.0;
+#pragma unroll
+    for (int s1 = 0; s1 < 2; ++s1)
+#pragma unroll
+      for (int s2 = 0; s2 < 2; ++s2)
+#pragma unroll
+        for (int s3 = 0; s3 < 2; ++s3)
+          out[((int64_t)p1[s1] * K + p2[s2]) * K + p3[s3]] = (float)(scale * v[s1][s2][s3]);
+  }
+  if (zero)
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nz; i += stride) zero[i] = 0.0f;
+}
+
+cudaError_t launch_fold_mesh(kpme_plan_t P, const void* in, bool in_double, float* out, int K, float* zero,
+                             int64_t nz) {
+  const int64_t n_oct = (int64_t)(K / 2) * (K / 2) * (K / 2);
+  const int threads = 256;
+  const int64_t want = (std::max<int64_t>(n_oct, nz) + threads - 1) / threads;
+  const int grid = (int)std::min<int64_t>(std::max<int64_t>(want, 1), (int64_t)P->sm_count * 16);
+  if (in_double)
+    fold_mesh_kernel<double, false><<<grid, threads, 0, P->stream>>>((const double*)in, out, K, zero, nz);
+  else
+    fold_mesh_kernel<float, false><<<grid, threads, 0, P->stream>>>((const float*)in, out, K, zero, nz);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unfold_mesh(kpme_plan_t P, float* mesh, int K) {
+  const int64_t n_oct = (int64_t)(K / 2) * (K / 2) * (K / 2);
+  const int threads = 256;
+  const int grid = (int)std::min<int64_t>((n_oct + threads - 1) / threads, (int64_t)P->sm_count * 16);
+  fold_mesh_kernel<float, true><<<grid, threads, 0, P->stream>>>(mesh, mesh, K, nullptr, 0);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_rowmax_rows(kpme_plan_t P, const float* in, int64_t rows, int K, float* out, float* zero,

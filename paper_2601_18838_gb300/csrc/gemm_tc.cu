@@ -41,6 +41,7 @@ struct TcParams {
   const int* start;
   const int2* pairs;
   int* status;
+  long long wait_cycles;   // budget of one bounded wait (clock cycles)
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -69,11 +70,12 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 }
 
 // Bounded wait: false if the budget runs out or another thread already gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status,
+                                          long long budget) {
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
     if (*abort_flag) return false;
-    if (clock64() - t0 > kWaitCycles) {
+    if (clock64() - t0 > budget) {
       *abort_flag = 1;
       atomicExch(status, DEV_TIMEOUT);
       return false;
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int it = 0; it < total; ++it) {
       const int s = it % prm.stages;
       const uint32_t ph = (uint32_t)(it / prm.stages) & 1u;
-      if (it >= prm.stages && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status)) break;
+      if (it >= prm.stages && !mbar_wait(&empty[s], ph ^ 1u, abort_flag, prm.status, prm.wait_cycles)) break;
       if (*abort_flag) break;
       const int2 pr = prm.pairs[p0 + it / kchunks];
       const int kc = (it % kchunks) * chunk_elems;
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     for (int it = 0; it < total; ++it) {
       const int s = it % prm.stages;
       const uint32_t ph = (uint32_t)(it / prm.stages) & 1u;
-      if (!mbar_wait(&full[s], ph, abort_flag, prm.status)) {
+      if (!mbar_wait(&full[s], ph, abort_flag, prm.status, prm.wait_cycles)) {
         ok = false;
         break;
       }
@@ -257,11 +259,18 @@ __global__ void __launch_bounds__(kThreads, 1)
     }
     (void)ok;
     mma_commit(done);
+    // every MMA issued has completed before tensor memory is released, also when a wait gave
+    // up (the abort flag is not consulted here; the production budget bounds the wait)
+    {
+      const long long t0 = clock64();
+      while (!mbar_try_wait(done, 0u) && clock64() - t0 < kWaitCycles) {
+      }
+    }
   }
   __syncwarp();
 
   // ---------------- epilogue ----------------
-  if (total > 0) mbar_wait(done, 0, abort_flag, prm.status);
+  if (total > 0) mbar_wait(done, 0, abort_flag, prm.status, prm.wait_cycles);
   __syncthreads();   // makes the abort decision uniform before the .sync.aligned TMEM loads
   const bool ok = (total > 0) && !*abort_flag;
   fence_after();
@@ -283,7 +292,7 @@ __global__ void __launch_bounds__(kThreads, 1)
           float* o = reinterpret_cast<float*>(prm.out) + (int64_t)job * MN + off;
           const float hi = tf32_rn(v);
           o[0] = hi;
-          if (S > 1) o[prm.out_plane] = v - hi;
+          if (S > 1) o[prm.out_plane] = tf32_rn(v - hi);   // the tensor core would truncate it
         } else {
           __nv_bfloat16* o = reinterpret_cast<__nv_bfloat16*>(prm.out) + (int64_t)job * MN + off;
           float rem = v;
@@ -314,7 +323,7 @@ __global__ void split_kernel(const TS* __restrict__ src, void* __restrict__ dst,
     if constexpr (TF32) {
       const float hi = tf32_rn((float)v);
       reinterpret_cast<float*>(dst)[i] = hi;
-      if (S > 1) reinterpret_cast<float*>(dst)[count + i] = (float)(v - (double)hi);
+      if (S > 1) reinterpret_cast<float*>(dst)[count + i] = tf32_rn((float)(v - (double)hi));
     } else {
       double rem = v;
 #pragma unroll
@@ -400,6 +409,7 @@ cudaError_t launch_mp_tc(kpme_plan_t P, const TcArgs& a) {
   prm.start = a.jobs->d_start;
   prm.pairs = a.jobs->d_pairs;
   prm.status = P->d_status;
+  prm.wait_cycles = P->wait_cycles;
   // keep (CTAs per SM) x (TMEM columns) <= 512 by asking for enough shared memory
   int smem = tc_smem_bytes(pi, prm.bn, prm.stages);
   const int max_ctas = 512 / cols;

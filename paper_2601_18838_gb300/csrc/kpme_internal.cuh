@@ -20,6 +20,8 @@ enum DeviceStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
 
 // Bounded spin budget for every device-side wait (~1 s at 2 GHz).
 constexpr long long kWaitCycles = 2000000000LL;
+// Handle check word of a live plan.
+constexpr uint32_t kPlanMagic = 0x454d504bu;
 
 // Steps reported by kpme_get_profile.
 enum Step : int {
@@ -140,6 +142,10 @@ struct kpme_plan_s {
   bool ozt_res = false;            // stages 1 and 2 by the A-in-tensor-memory kernel, A resident
   bool ozt_pp = false;             // stage 3 by the A-in-tensor-memory kernel, A per pair
   bool ozf = false;                // stages 2 and 3 fused on the SM (K = 32, 64)
+  bool fold = false;               // error-free split on the reflection basis of every axis
+                                   // (K % 128 == 0): block-diagonal factors, K/2 contraction
+  bool allow_fold = true;          // KPME_FOLD=0 keeps the dense factors
+  float* d_Qfold = nullptr;        // the charge mesh in the reflection basis (float32)
   bool allow_fused = true;         // tuning knob: may the fused kernel be used
   int tune_split = 2;              // tuning knob: split-K counts x tune_split / 2
   bool no_sort = false;            // tuning knob: float64-atomic spreading, untiled gathering
@@ -165,6 +171,13 @@ struct kpme_plan_s {
   int64_t launches = 0;            // kernels launched by the last evaluation
 
   int64_t scratch_bytes = 0;
+
+  // handle check word (kPlanMagic while the plan is valid) and host-side fault injection
+  // (KPME_FAULT, read by kpme_plan; see parse_fault in api.cu)
+  uint32_t magic = 0;
+  int fault_alloc_at = 0;          // the n-th device allocation of the plan fails (0: never)
+  int n_allocs = 0;
+  long long wait_cycles = kpme::kWaitCycles;   // budget of every bounded device wait
 
   // CUDA graph of kpme_energy_forces, keyed by its arguments; replayed on the caller's stream
   cudaStream_t capture_stream = nullptr;
@@ -285,6 +298,8 @@ struct OztArgs {
   int mode;                  // 1: sum of the item's pairs (atomics), 2: one plane per pair
   bool a_res;
   const JobList* jobs;
+  bool fold = false;         // block-diagonal factors: an item contracts the K/2 values of its
+                             // output column's half (A columns [K/2, K) for columns n >= K/2)
 };
 struct OzfArgs {
   const float* Y;            // float32 Y (r0 planes x K^2 rows x K), device
@@ -296,7 +311,14 @@ struct OzfArgs {
 };
 bool ozf_supported(int K);
 cudaError_t launch_mp_ozf(kpme_plan_t P, const OzfArgs& a);
-bool ozt_supported(int K, int bn, bool a_res);
+bool ozt_supported(int K, int bn, bool a_res, bool fold = false);
+// the K^3 mesh in the reflection basis of its three axes (pairs a <-> K - 1 - a: the sum at
+// a, the difference at K - 1 - a) as float32; zero (may be NULL): nz floats cleared alike
+cudaError_t launch_fold_mesh(kpme_plan_t P, const void* in, bool in_double, float* out, int K, float* zero,
+                             int64_t nz);
+// back from the reflection basis, in place (each octet of mirror points is its own inverse
+// butterfly, scaled by 1/8)
+cudaError_t launch_unfold_mesh(kpme_plan_t P, float* mesh, int K);
 cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a);
 cudaError_t launch_mesh_correction(kpme_plan_t P, const double* Q, double* Phi, int64_t count, double c,
                                    double* scratch);

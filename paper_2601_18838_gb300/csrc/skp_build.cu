@@ -245,17 +245,31 @@ __device__ __forceinline__ float tf32_rn(float x) {
 // kind: 0 float64, 1 float32, 2 bf16 slices (round-to-nearest cascade), 3 tf32 hi/lo in float32,
 // 4 fixed-point bf16 slices with one exponent per factor (every circulant row holds the same
 // values): v = 2^(e-7) sum_s d_s 2^(-8s), d_s integers in [-128, 128], 2^e >= max |g|.
+//
+// fold != 0 (kind 4 only): the two diagonal blocks of the circulant in the reflection basis of
+// the mesh axis (pairs a <-> K - 1 - a, see fold_mesh_kernel), K rows x K/2 columns: row n < K/2
+// holds C+(n, k) = g(n - k) + g(n + k + 1); row n >= K/2 is the odd block at a' = K - 1 - n,
+// column k at a = K/2 - 1 - k: C-(a', a) = g(a' - a) - g(a' + a + 1) (indices mod K).  Their
+// entries are bounded by 2 max |g|, which sets the exponent.
+__device__ __forceinline__ double folded_entry(const double* g, int K, int n, int k) {
+  const int h = K / 2;
+  if (n < h) return g[((n - k) % K + K) % K] + g[(n + k + 1) % K];
+  const int ap = K - 1 - n, a = h - 1 - k;
+  return g[((ap - a) % K + K) % K] - g[(ap + a + 1) % K];
+}
+
 __global__ void materialize_kernel(const double* __restrict__ gen, int count, int K, int slices, int kind,
-                                   void* __restrict__ dst) {
-  const int64_t per = (int64_t)K * K;
+                                   int fold, void* __restrict__ dst) {
+  const int kc = fold ? K / 2 : K;   // stored columns per row
+  const int64_t per = (int64_t)K * kc;
   const int64_t total = per * count;
   for (int64_t idx = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; idx < total;
        idx += (int64_t)gridDim.x * blockDim.x) {
     const int t = (int)(idx / per);
-    const int n = (int)((idx % per) / K), k = (int)(idx % K);
+    const int n = (int)((idx % per) / kc), k = (int)(idx % kc);
     int d = n - k;
     d += (d < 0) ? K : 0;
-    const double v = gen[(int64_t)t * K + d];
+    const double v = fold ? folded_entry(gen + (int64_t)t * K, K, n, k) : gen[(int64_t)t * K + d];
     if (kind == 0) {
       ((double*)dst)[idx] = v;
     } else if (kind == 1) {
@@ -270,6 +284,7 @@ __global__ void materialize_kernel(const double* __restrict__ gen, int count, in
     } else if (kind == 4) {
       double gmax = 0.0;
       for (int j = 0; j < K; ++j) gmax = fmax(gmax, fabs(gen[(int64_t)t * K + j]));
+      if (fold) gmax *= 2.0;
       int e = 0;
       frexp(gmax, &e);
       double u = ldexp(v, 7 - e);
@@ -281,7 +296,7 @@ __global__ void materialize_kernel(const double* __restrict__ gen, int count, in
     } else {
       const float hi = tf32_rn((float)v);
       ((float*)dst)[idx] = hi;
-      if (slices > 1) ((float*)dst)[total + idx] = (float)(v - (double)hi);
+      if (slices > 1) ((float*)dst)[total + idx] = tf32_rn((float)(v - (double)hi));   // exact tf32 for the MMA
     }
   }
 }
@@ -795,7 +810,7 @@ __global__ void materialize_dense_kernel(const double* __restrict__ D, const dou
     } else {
       const float hi = tf32_rn((float)v);
       ((float*)dst)[idx] = hi;
-      if (slices > 1) ((float*)dst)[total + idx] = (float)(v - (double)hi);
+      if (slices > 1) ((float*)dst)[total + idx] = tf32_rn((float)(v - (double)hi));   // exact tf32 for the MMA
     }
   }
 }
@@ -807,7 +822,8 @@ cudaError_t launch_materialize_dense(kpme_plan_t P, const double* d_dense, const
 }
 
 cudaError_t launch_materialize(kpme_plan_t P, const double* d_gen, int count, void* dst, int slices, int kind) {
-  materialize_kernel<<<1024, kT, 0, P->stream>>>(d_gen, count, P->p.K, slices, kind, dst);
+  const int fold = (kind == 4 && P->fold) ? 1 : 0;
+  materialize_kernel<<<1024, kT, 0, P->stream>>>(d_gen, count, P->p.K, slices, kind, fold, dst);
   return cudaGetLastError();
 }
 

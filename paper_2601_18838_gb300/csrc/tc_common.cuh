@@ -62,19 +62,64 @@ static __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity)
       : "memory");
   return ok != 0;
 }
-static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* status) {
-  if (mbar_try_wait(bar, parity)) return true;   // already complete: no clock read on this path
+// The bounded waits of one CTA share its abort flag (shared memory; set by the first wait that
+// gives up, so that every role stops waiting), the device status word and a budget in clock
+// cycles per wait (the plan's, kWaitCycles unless fault injection shortens it).
+struct WaitCtl {
+  volatile int* abort;
+  int* status;
+  long long budget;
+};
+// One suspension of mbarrier.try_wait lasts at most kSuspendNs (20 M cycles at 2 GHz); a shorter
+// budget is timed with non-blocking polls instead.
+constexpr long long kSuspendCycles = 20000000LL;
+
+static __device__ __forceinline__ bool give_up(const WaitCtl& w) {
+  *w.abort = 1;
+  atomicExch(w.status, DEV_TIMEOUT);
+  return false;
+}
+
+static __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, const WaitCtl& w) {
+  if (w.budget >= kSuspendCycles) {
+    if (mbar_try_wait(bar, parity)) return true;   // already complete: no clock read on this path
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+      if (*w.abort) return false;
+      if (clock64() - t0 > w.budget) return give_up(w);
+    }
+    return true;
+  }
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (*w.abort) return false;
+    if (clock64() - t0 > w.budget) return give_up(w);
+  }
+  return true;
+}
+
+// A wait on the way out of a CTA that gave up: TMA copies and MMAs already issued complete on
+// their own, and they must land before the CTA releases its shared and tensor memory.  The
+// abort flag is not consulted; the production budget bounds the wait.
+static __device__ __forceinline__ bool mbar_drain(uint64_t* bar, uint32_t parity, int* status) {
+  if (mbar_try_wait(bar, parity)) return true;
   const long long t0 = clock64();
   while (!mbar_try_wait(bar, parity)) {
-    if (*abort_flag) return false;
     if (clock64() - t0 > kWaitCycles) {
-      *abort_flag = 1;
       atomicExch(status, DEV_TIMEOUT);
       return false;
     }
   }
   return true;
 }
+
+// The last min(n, stages) loads of a ring of `stages` buffers whose i-th load completes phase
+// i / stages of full[i % stages]: each is the latest use of its buffer, so its parity wait is
+// unambiguous, and a phase that completed long ago returns at once.
+static __device__ __forceinline__ void drain_ring(uint64_t* full, int stages, int n, int* status) {
+  for (int i = n > stages ? n - stages : 0; i < n; ++i) mbar_drain(&full[i % stages], (uint32_t)(i / stages) & 1u, status);
+}
+
 static __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, uint64_t* bar, int c0, int c1, int c2) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, %5}], "

@@ -90,12 +90,14 @@ def test_per_cell_form_parameters_are_validated_without_gpu(L, interp):
             setattr(p, k, v)
         h = C.c_void_p()
         st = L.kpme_plan(C.byref(p), None, C.byref(h))
-        assert not h.value
+        if h.value:   # a GPU is present and the plan was made
+            L.kpme_destroy(h)
+            assert st == 0
         return st
 
-    # past validation, the missing GPU is the first error (KPME_ERR_CUDA)
-    assert plan_status() == 3
-    assert plan_status(order=16, K=32, modes=64) == 3
+    # past validation: KPME_OK with a GPU, else the missing GPU is the first error (KPME_ERR_CUDA)
+    assert plan_status() in (0, 3)
+    assert plan_status(order=16, K=32, modes=64) in (0, 3)
     for bad in (dict(skp_method=0), dict(order=5), dict(order=10, K=60), dict(K=60), dict(modes=0),
                 dict(modes=65), dict(K=1024), dict(interp=3)):
         assert plan_status(**bad) == 1, bad   # KPME_ERR_INVALID_ARG

@@ -9,9 +9,43 @@ from tests._gpu_util import cuda_or_skip, dev, host, rel
 
 pytestmark = pytest.mark.gpu
 
-# tolerances on relative RMS error against the float64 oracle (potentials, forces)
-TOL = {"fp64": (1e-12, 1e-11), "fp32": (5e-6, 2e-5), "tf32x3": (5e-6, 3e-5), "bf16x6": (1e-6, 1e-5),
-       "bf16x3": (1e-4, 5e-4), "tf32": (2e-2, 5e-2), "bf16": (5e-2, 2e-1), "bf16x10": (1e-6, 1e-5)}
+# Relative RMS error bars against the float64 SKP oracle (potentials, forces): 1e-6 / 1e-5 for
+# the float32 and split forms, 1e-3 for the single-product forms (plain BF16; plain TF32 is
+# held to the same bar), whose force bar is taken at the same 1:10 ratio, 1e-2.  FP64 is held
+# to its own arithmetic.
+BAR = {"fp64": (1e-12, 1e-11), "fp32": (1e-6, 1e-5), "tf32x3": (1e-6, 1e-5), "bf16x6": (1e-6, 1e-5),
+       "bf16x3": (1e-6, 1e-5), "bf16x10": (1e-6, 1e-5), "tf32": (1e-3, 1e-2), "bf16": (1e-3, 1e-2)}
+TOL = BAR
+FORMS = ["fp64", "fp32", "tf32x3", "bf16x6", "bf16x3", "tf32", "bf16", "bf16x10"]
+
+# Forms that miss their bar, with the errors measured on one GB300 (phi, F): strict xfails, so
+# a change that brings a form under its bar turns the test red until the mark is removed.
+MISSES = {
+    ("small", "bf16x3"): "phi 4.9e-6, F 1.9e-5: 16 significant bits per operand (2^-17 per value)",
+    ("small", "bf16"): "phi 3.2e-3, F 1.0e-2: 8 significant bits per operand",
+    ("water", "fp32"): "phi 1.9e-6, F 8.0e-6: per-multiply-add float32 rounding over the three stages",
+    ("water", "tf32x3"): "phi 7.1e-6, F 1.4e-5: 22-bit operands and the tensor core's float32 accumulation",
+    ("water", "bf16x6"): "phi 5.8e-6, F 1.3e-5: the tensor core's float32 accumulation of floating slices",
+    ("water", "bf16x3"): "phi 5.9e-5, F 2.8e-4: 16 significant bits per operand",
+    ("water", "tf32"): "phi 4.8e-3, F 2.8e-2: 11 significant bits per operand",
+    ("water", "bf16"): "phi 3.2e-2, F 1.3e-1: 8 significant bits per operand",
+    ("apply_water", "fp32"): "Phi 3.7e-6: per-multiply-add float32 rounding",
+    ("apply_water", "tf32x3"): "Phi 8.6e-6",
+    ("apply_water", "bf16x6"): "Phi 7.5e-6",
+    ("apply_water", "bf16x3"): "Phi 1.4e-4",
+    ("apply_water", "tf32"): "Phi 1.4e-2",
+    ("apply_water", "bf16"): "Phi 6.0e-2",
+    ("apply_small", "bf16x3"): "Phi 6.6e-6",
+    ("apply_small", "bf16"): "Phi 3.8e-3",
+}
+
+
+def _forms(box, forms=FORMS):
+    out = []
+    for f in forms:
+        why = MISSES.get((box, f))
+        out.append(pytest.param(f, marks=pytest.mark.xfail(reason=f"measured {why}", strict=True)) if why else f)
+    return out
 
 
 @pytest.fixture(scope="module")
@@ -102,9 +136,7 @@ def test_skp_build_matches_oracle(torch):
     assert rel(Phi_gpu, Phi_ref) < 4 * s.skp_tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x6", "bf16x3", "tf32", "bf16", "bf16x10"])
-def test_apply_with_oracle_factors(torch, prec):
-    s = wl.small()
+def _apply_case(torch, s, prec):
     o = _oracle_skp(s)
     r1, g3, g2, g1 = skp.generators(o)
     plan = _plan(s, prec)
@@ -112,9 +144,23 @@ def test_apply_with_oracle_factors(torch, prec):
     Q = spme.spread(s.x, s.q, s.box, s.K, s.order)
     Phi_ref = skp.apply(Q, o)
     Phi = host(plan.apply(dev(torch, Q)))
-    e = rel(Phi, Phi_ref)
+    plan.close()
+    return rel(Phi, Phi_ref)
+
+
+# bf16x6 on the small box measures 1.05e-6, too close to the bar for a strict mark either way
+@pytest.mark.parametrize("prec", _forms("apply_small", [f for f in FORMS if f != "bf16x6"]))
+def test_apply_with_oracle_factors(torch, prec):
+    e = _apply_case(torch, wl.small(), prec)
     print(f"{prec}: rel Phi {e:.3e}")
-    assert e < TOL[prec][0] * (10 if prec in ("fp32", "tf32x3", "bf16x6") else 1)
+    assert e < BAR[prec][0]
+
+
+@pytest.mark.parametrize("prec", _forms("apply_water"))
+def test_apply_with_oracle_factors_water(torch, prec):
+    e = _apply_case(torch, wl.water(), prec)
+    print(f"water {prec}: rel Phi {e:.3e}")
+    assert e < BAR[prec][0]
 
 
 @pytest.mark.parametrize("prec,order,sort", [("fp64", 6, True), ("fp32", 6, True), ("fp32", 6, False),
@@ -132,7 +178,7 @@ def test_gather(torch, prec, order, sort):
     assert rel(host(phi), phi_r) < tol and rel(host(F), F_r) < tol
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32", "tf32x3", "bf16x6", "bf16x3", "bf16x10"])
+@pytest.mark.parametrize("prec", _forms("small"))
 def test_energy_forces_small(torch, prec):
     s = wl.small()
     o = _oracle_skp(s)
@@ -144,44 +190,48 @@ def test_energy_forces_small(torch, prec):
     e_E = abs(out["energy"].item() - ref["E"]) / abs(ref["E"])
     e_W = abs(out["virial"].item() - ref["W"]) / abs(ref["W"])
     print(f"{prec}: phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e} W {e_W:.2e}")
-    tp, tf = TOL[prec]
+    tp, tf = BAR[prec]
+    plan.close()
     assert e_phi < tp and e_f < tf and e_E < 10 * tp and e_W < 10 * tp
 
 
-@pytest.mark.parametrize("prec", [
-    "fp64",
-    "bf16x10",
-    pytest.param("bf16x6", marks=pytest.mark.xfail(
-        reason="floating bf16 slices accumulate in the tensor core's float32 accumulator; measured "
-               "phi 4.8e-6 / F 1.2e-5 on this box, above the 1e-6 / 1e-5 bar", strict=False)),
-])
-def test_energy_forces_water_box(torch, prec):
-    # the 67 A water box (30,000 atoms, K = 64): the precision target is 1e-6 / 1e-5
+@pytest.fixture(scope="module")
+def water_ref():
     s = wl.water()
     o = _oracle_skp(s)
-    ref = skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+    return s, o, skp.reciprocal(s.x, s.q, s.box, s.K, s.order, s.beta, s.skp_tol, skp=o)
+
+
+@pytest.mark.parametrize("prec", _forms("water"))
+def test_energy_forces_water_box(torch, water_ref, prec):
+    # the 67 A water box (30,000 atoms, K = 64) at the bars of its form
+    s, o, ref = water_ref
     x, q = dev(torch, s.x), dev(torch, s.q)
     plan = _plan(s, prec)
     plan.set_skp(*skp.generators(o))
     out = plan.energy_forces(x, q)
     e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
     print(f"water {prec}: phi {e_phi:.2e} F {e_f:.2e}")
-    tp, tf = TOL[prec]
+    tp, tf = BAR[prec]
+    plan.close()
     assert e_phi < tp and e_f < tf
 
 
-@pytest.mark.parametrize("K,order,n,L,fused", [
-    (32, 4, 1001, 18.0, "1"),    # fused stages 2-3, BN = 32 (four k3' per tile)
-    (32, 4, 1001, 18.0, "0"),    # tensor-memory A, resident and per pair
-    (48, 4, 2050, 30.0, "1"),    # K % 32 != 0: shared-memory A kernel, row maxima across warps
-    (64, 4, 3001, 40.0, "1"),    # fused, BN = 64
-    (64, 4, 3001, 40.0, "0"),
-    (96, 6, 4003, 70.0, "1"),    # tensor-memory A, two 64-wide chunks (second half empty)
-    (128, 4, 5003, 90.0, "1"),   # tensor-memory A, two full chunks, two column tiles
+@pytest.mark.parametrize("K,order,n,L,fused,fold", [
+    (32, 4, 1001, 18.0, "1", "1"),     # fused stages 2-3, BN = 32 (four k3' per tile)
+    (32, 4, 1001, 18.0, "0", "1"),     # tensor-memory A, resident and per pair
+    (48, 4, 2050, 30.0, "1", "1"),     # K % 32 != 0: shared-memory A kernel, row maxima across warps
+    (64, 4, 3001, 40.0, "1", "1"),     # fused, BN = 64
+    (64, 4, 3001, 40.0, "0", "1"),
+    (96, 6, 4003, 70.0, "1", "1"),     # tensor-memory A, two 64-wide chunks (second half empty)
+    (128, 4, 5003, 90.0, "1", "0"),    # tensor-memory A, two full chunks, two column tiles
+    (128, 4, 5003, 90.0, "1", "1"),    # reflection basis: one 64-wide chunk per half
+    (256, 6, 20011, 150.0, "1", "1"),  # reflection basis, two chunks per half, four column tiles
 ])
-def test_error_free_split_sizes(torch, monkeypatch, K, order, n, L, fused):
+def test_error_free_split_sizes(torch, monkeypatch, K, order, n, L, fused, fold):
     # ragged particle counts and the kernel variants of the error-free split
     monkeypatch.setenv("KPME_FUSED", fused)
+    monkeypatch.setenv("KPME_FOLD", fold)
     s = wl.random_system(n, L, K, order, seed=K + n)
     o = _oracle_skp(s)
     ref = skp.reciprocal(s.x, s.q, s.box, K, order, s.beta, s.skp_tol, skp=o)
@@ -191,8 +241,12 @@ def test_error_free_split_sizes(torch, monkeypatch, K, order, n, L, fused):
     e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
     e_E = abs(host(out["energy"])[0] - ref["E"]) / abs(ref["E"])
     e_W = abs(host(out["virial"])[0] - ref["W"]) / abs(ref["W"])
-    print(f"bf16x10 K={K} fused={fused}: phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e} W {e_W:.2e}")
+    print(f"bf16x10 K={K} fused={fused} fold={fold}: phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e} W {e_W:.2e}")
     assert e_phi < 1e-6 and e_f < 1e-5 and e_E < 1e-6 and e_W < 1e-5
+    # the stage entry point on the same mesh: the operator alone, float64 in and out
+    Q = spme.spread(s.x, s.q, s.box, K, order)
+    assert rel(host(plan.apply(dev(torch, Q))), skp.apply(Q, o)) < 1e-6
+    plan.close()
 
 
 def test_potential_targets_differ_from_sources(torch):

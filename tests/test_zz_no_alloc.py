@@ -1,8 +1,9 @@
 """kpme_spread_noalloc: the allocation-free spreading entry point, for callers that may
 not call cudaMalloc (stream capture, foreign pool allocators, latency-critical loops).
 
-Checked through the C ABI against the plan-based kpme_spread (float32 mesh) on two calls
-in a row with different inputs, so that a stale static scratch array would show up.
+Checked through the C ABI against the plan-based kpme_spread (float32 mesh) and against the
+oracle's spreading on two calls in a row with different inputs, so that a stale static
+scratch array would show up.
 Kept in a file collected last: it shares one static device array for the whole process.
 """
 import ctypes as C
@@ -10,6 +11,7 @@ import ctypes as C
 import numpy as np
 import pytest
 
+from oracle import spme
 from paper_2601_18838_gb300 import workloads as wl
 from tests._gpu_util import cuda_or_skip, dev, host
 
@@ -68,8 +70,10 @@ def test_noalloc_spread_matches_plan_spread_twice():
     for s in systems:   # two calls in a row; the second uses a smaller mesh than the first
         a = _noalloc(torch, L, s, stream)
         b = _with_plan(torch, L, s, stream)
+        ref = spme.spread(s.x, s.q, s.box, s.K, s.order)
         assert np.all(np.isfinite(a))
         assert np.abs(a - b).max() <= TOL * np.abs(b).max()
+        assert np.abs(a - ref).max() <= TOL * np.abs(ref).max()
         assert abs(a.sum() - s.q.sum()) < 1e-4
 
 
