@@ -471,7 +471,7 @@ template <int BN, int NCONV, bool A_TMA>
 cudaError_t launch_bn(cudaStream_t st, const CUtensorMap* tmA, const CUtensorMap* tmB, const OzParams& prm, dim3 grid,
                       int smem) {
   auto kern = mp_oz_kernel<BN, NCONV, A_TMA>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   kern<<<grid, oz_threads<NCONV>(), smem, st>>>(*tmA, *tmB, prm);
   return cudaGetLastError();

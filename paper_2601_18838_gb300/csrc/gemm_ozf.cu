@@ -529,7 +529,7 @@ cudaError_t launch_k(kpme_plan_t P, const OzfArgs& a, OzfParams prm) {
   const int smem = prm.sb * bstage + fixed;
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   auto kern = mp_ozf_kernel<K>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   const dim3 grid((unsigned)a.jobs->h_cta.size() - 1);   // one CTA per range of the static schedule
   kern<<<grid, kThreads, smem, P->stream>>>(*a.tmB2, *a.tmB1, prm);

@@ -550,7 +550,7 @@ template <int BN, int NCONV, bool A_RES>
 cudaError_t launch_cfg(cudaStream_t st, const CUtensorMap* tmF, const CUtensorMap* tmB, const OztParams& prm,
                        dim3 grid, int smem) {
   auto kern = mp_ozt_kernel<BN, NCONV, A_RES>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   kern<<<grid, ozt_threads<NCONV>(), smem, st>>>(*tmF, *tmB, prm);
   return cudaGetLastError();

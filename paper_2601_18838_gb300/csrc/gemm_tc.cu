@@ -339,7 +339,7 @@ __global__ void split_kernel(const TS* __restrict__ src, void* __restrict__ dst,
 template <bool TF32, int S>
 cudaError_t launch_t(kpme_plan_t P, const TcArgs& a, TcParams prm, dim3 grid, int smem) {
   auto kern = mp_tc_kernel<TF32, S>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = raise_smem_cap(reinterpret_cast<const void*>(kern));
   if (e != cudaSuccess) return e;
   kern<<<grid, kThreads, smem, P->stream>>>(*a.tmA, *a.tmB, prm);
   return cudaGetLastError();

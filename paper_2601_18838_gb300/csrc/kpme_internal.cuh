@@ -23,6 +23,24 @@ constexpr long long kWaitCycles = 2000000000LL;
 // Handle check word of a live plan.
 constexpr uint32_t kPlanMagic = 0x454d504bu;
 
+// The cap on a kernel's dynamic shared memory (cudaFuncAttributeMaxDynamicSharedMemorySize) is
+// a property of the function, not of one launch: a kernel launched several times in one
+// captured graph with different sizes must carry a cap that covers every launch, since a node
+// launched on its own (a replayed or profiled node) is checked against the function's current
+// cap.  Every such kernel is given the device's opt-in maximum once; each launch still passes
+// its own size.  (The cap counts dynamic memory only: the opt-in maximum less the function's
+// static shared memory.)
+inline cudaError_t raise_smem_cap(const void* func) {
+  int dev = 0, cap = 0;
+  cudaFuncAttributes fa{};
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&cap, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, func);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(func, cudaFuncAttributeMaxDynamicSharedMemorySize, cap - (int)fa.sharedSizeBytes);
+  return e;
+}
+
 // Steps reported by kpme_get_profile.
 enum Step : int {
   STEP_SPREAD = 0, STEP_SPLIT, STEP_SKP1, STEP_SKP2, STEP_SKP3, STEP_GATHER, STEP_VIRIAL, NUM_STEPS

@@ -1029,14 +1029,14 @@ cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double*
 
 template <int N>
 void spread_tiled(kpme_plan_t P, const Tiling& tl, int nt, size_t smem, const double* q, float* Q) {
-  cudaFuncSetAttribute(spread_tile_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (raise_smem_cap(reinterpret_cast<const void*>(spread_tile_kernel<N>)) != cudaSuccess) return;   // reported
   spread_tile_kernel<N><<<nt, kThreads, smem, P->stream>>>(tl, q, P->d_tstart, P->d_rec, Q);
 }
 
 template <int N>
 void gather_tiled(kpme_plan_t P, const Tiling& tl, int nt, size_t smem, const double* q, const float* Phi,
                   double* phi, double* F, double* energy, double c) {
-  cudaFuncSetAttribute(gather_tile_kernel<N>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (raise_smem_cap(reinterpret_cast<const void*>(gather_tile_kernel<N>)) != cudaSuccess) return;   // reported
   gather_tile_kernel<N><<<nt, kThreads, smem, P->stream>>>(geom(P), tl, q, P->d_tstart, P->d_rec, Phi, phi, F,
                                                              energy, P->d_sumq, c, P->p.coulomb_k);
 }
