@@ -119,8 +119,10 @@ __global__ void __launch_bounds__(oz_threads<NCONV>(), 1)
     const int per_job = m_tiles * n_tiles;
     job = w / per_job;
     const int rem = w - job * per_job;
-    n0 = (rem / m_tiles) * BN;
-    m0 = (rem % m_tiles) * kBM;
+    // column tiles innermost: the items that read the same A rows run on neighbouring CTAs at
+    // the same time, so the rows come from DRAM once and from L2 for the other column tiles
+    n0 = (rem % n_tiles) * BN;
+    m0 = (rem / n_tiles) * kBM;
   };
 
   if (warp == 0) {

@@ -25,6 +25,7 @@
 // drains without further waits.
 #include "kpme_internal.cuh"
 #include "tc_common.cuh"
+#include "df.cuh"
 
 #include <algorithm>
 
@@ -142,8 +143,10 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
     const int per_job = m_tiles * n_tiles;
     job = w / per_job;
     const int rem = w - job * per_job;
-    n0 = (rem / m_tiles) * BN;
-    m0 = (rem % m_tiles) * kBM;
+    // column tiles innermost: the items that read the same A rows run on neighbouring CTAs at
+    // the same time, so the rows come from DRAM once and from L2 for the other column tiles
+    n0 = (rem % n_tiles) * BN;
+    m0 = (rem / n_tiles) * kBM;
   };
   // boxes of chunk c that hold valid k (the second is skipped when it starts at or past kc)
   auto boxes = [&](int c) { return (c * kChunk + 32 < prm.kc) ? 2 : 1; };
@@ -527,7 +530,9 @@ OztConfig ozt_config(int bn, int K, bool a_res) {
   OztConfig c{};
   const int kchunks = (K + kChunk - 1) / kChunk;
   const int bstage = kSlices * bn * 128;
-  c.sf = 2;
+  // A per pair (stage 3) streams a new float32 A for every pair from DRAM: three staging
+  // buffers keep more of it in flight; A resident across an item's pairs needs two
+  c.sf = a_res ? 2 : 3;
   c.sb = (200 * 1024 - c.sf * kFStage) / bstage;
   if (c.sb > 8) c.sb = 8;
   const int acc_cols = 2 * bn;
@@ -618,58 +623,63 @@ cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
 // The reflection basis of a K^3 mesh (K even).  On each axis the mirror points a and K - 1 - a
 // (a < K/2) are replaced by their sum (stored at a) and difference (stored at K - 1 - a); one
 // thread takes the octet of mirror points of (a1, a2, a3), reads its eight values, applies the
-// butterfly on the three axes in float64 and writes the eight results, rounded once to float32.
-// The unfolding applies the same butterfly and the factor 1/8 (the butterfly squared is twice
-// the identity per axis); it reads and writes the same octet, so it runs in place.
+// butterfly on the three axes in double-float arithmetic (float32 pairs: the float64 pipe of
+// this GPU would bound the pass) and writes the eight results, rounded once to float32.  The
+// unfolding applies the same butterfly and the factor 1/8 (the butterfly squared is twice the
+// identity per axis); it reads and writes the same octet, so it runs in place.
+__device__ __forceinline__ df df_of(float v) { return {v, 0.0f}; }
+__device__ __forceinline__ df df_of(double v) { return df_from(v); }
+__device__ __forceinline__ df df_neg(df a) { return {-a.hi, -a.lo}; }
+
 template <typename TIN, bool UNFOLD>
-__global__ void fold_mesh_kernel(const TIN* in, float* out, int K, float* __restrict__ zero,
-                                 int64_t nz) {
+__global__ void fold_mesh_kernel(const TIN* in, float* out, int K, float* __restrict__ zero, int64_t nz) {
   const int h = K / 2;
   const int64_t n_oct = (int64_t)h * h * h;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
   for (int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; o < n_oct; o += stride) {
     const int a3 = (int)(o % h), a2 = (int)((o / h) % h), a1 = (int)(o / ((int64_t)h * h));
     const int p1[2] = {a1, K - 1 - a1}, p2[2] = {a2, K - 1 - a2}, p3[2] = {a3, K - 1 - a3};
-    double v[2][2][2];
+    df v[2][2][2];
 #pragma unroll
     for (int s1 = 0; s1 < 2; ++s1)
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
-        for (int s3 = 0; s3 < 2; ++s3) v[s1][s2][s3] = (double)in[((int64_t)p1[s1] * K + p2[s2]) * K + p3[s3]];
+        for (int s3 = 0; s3 < 2; ++s3) v[s1][s2][s3] = df_of(in[((int64_t)p1[s1] * K + p2[s2]) * K + p3[s3]]);
     // one axis after the other (each butterfly reads values the previous axis finished)
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const double a = v[i][j][0], b = v[i][j][1];
-        v[i][j][0] = a + b;
-        v[i][j][1] = a - b;
+        const df a = v[i][j][0], b = v[i][j][1];
+        v[i][j][0] = df_add(a, b);
+        v[i][j][1] = df_add(a, df_neg(b));
       }
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const double a = v[i][0][j], b = v[i][1][j];
-        v[i][0][j] = a + b;
-        v[i][1][j] = a - b;
+        const df a = v[i][0][j], b = v[i][1][j];
+        v[i][0][j] = df_add(a, b);
+        v[i][1][j] = df_add(a, df_neg(b));
       }
 #pragma unroll
     for (int i = 0; i < 2; ++i)
 #pragma unroll
       for (int j = 0; j < 2; ++j) {
-        const double a = v[0][i][j], b = v[1][i][j];
-        v[0][i][j] = a + b;
-        v[1][i][j] = a - b;
+        const df a = v[0][i][j], b = v[1][i][j];
+        v[0][i][j] = df_add(a, b);
+        v[1][i][j] = df_add(a, df_neg(b));
       }
-    const double scale = UNFOLD ? 0.125 : 1.0;
+    const float scale = UNFOLD ? 0.125f : 1.0f;   // a power of two: exact
 #pragma unroll
     for (int s1 = 0; s1 < 2; ++s1)
 #pragma unroll
       for (int s2 = 0; s2 < 2; ++s2)
 #pragma unroll
         for (int s3 = 0; s3 < 2; ++s3)
-          out[((int64_t)p1[s1] * K + p2[s2]) * K + p3[s3]] = (float)(scale * v[s1][s2][s3]);
+          out[((int64_t)p1[s1] * K + p2[s2]) * K + p3[s3]] =
+              scale * __fadd_rn(v[s1][s2][s3].hi, v[s1][s2][s3].lo);
   }
   if (zero)
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < nz; i += stride) zero[i] = 0.0f;
