@@ -385,6 +385,11 @@ kpme_status_t install_skp(kpme_plan_t P) {
   if (pi.tensor && !pi.oz && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
   if ((st = dalloc(P, &P->d_Y, (size_t)islices * r0 * k3 * ieb)) != KPME_OK) return st;
   if (pi.tensor) choose_tc_tiles(P);
+  // in the reflection basis an item can cover a whole half of the output columns when the half
+  // is 128 wide: N = 128 MMAs, half the MMA instructions per flop (KPME_BN128=0 keeps 64)
+  if (P->fold && K / 2 == 128 && getenv_flag("KPME_BN128", true) && ozt_supported(K, 128, true, true) &&
+      ozt_supported(K, 128, false, true))
+    P->tc_bn = 128;
   P->ozt_res = pi.oz && ozt_supported(K, P->tc_bn, true, P->fold);
   P->ozt_pp = pi.oz && ozt_supported(K, P->tc_bn, false, P->fold);
   if (P->fold && !(P->ozt_res && P->ozt_pp)) return KPME_ERR_UNSUPPORTED;   // excluded above

@@ -531,21 +531,21 @@ OztConfig ozt_config(int bn, int K, bool a_res) {
   const int kchunks = (K + kChunk - 1) / kChunk;
   const int bstage = kSlices * bn * 128;
   // A per pair (stage 3) streams a new float32 A for every pair from DRAM: three staging
-  // buffers keep more of it in flight; A resident across an item's pairs needs two
-  c.sf = a_res ? 2 : 3;
+  // buffers keep more of it in flight where the factor ring keeps three stages; A resident
+  // across an item's pairs needs two
+  c.sf = (!a_res && (200 * 1024 - 3 * kFStage) / bstage >= 3) ? 3 : 2;
   c.sb = (200 * 1024 - c.sf * kFStage) / bstage;
   if (c.sb > 8) c.sb = 8;
   const int acc_cols = 2 * bn;
-  if (a_res) {
-    c.at_cols = kchunks * kChunkCols;
-    c.nat = (512 - 2 * acc_cols) / c.at_cols;
-    if (c.nat > 2) c.nat = 2;
-  } else {
-    c.at_cols = kChunkCols;
-    c.nat = 2;
-  }
-  c.nacc = c.nat > 0 ? (512 - c.nat * c.at_cols) / acc_cols : 0;
+  // tensor memory: two accumulators (the epilogue drains one while the MMAs fill the other)
+  // when A fits beside them, else one (BN = 128: the N = 128 MMAs halve the instructions per
+  // flop, and the epilogue's drain of the single accumulator is short against a pair's MMAs)
+  c.at_cols = a_res ? kchunks * kChunkCols : kChunkCols;
+  const int want_nat = a_res ? 1 : 2;
+  c.nacc = (512 - want_nat * c.at_cols) / acc_cols;
   if (c.nacc > 4) c.nacc = 4;
+  c.nat = c.nacc > 0 ? (512 - c.nacc * acc_cols) / c.at_cols : 0;
+  if (c.nat > 2) c.nat = 2;
   c.a_col0 = c.nacc * acc_cols;
   c.smem = c.sb * bstage + c.sf * kFStage + kBarBytes + 4 * bn * 4 + 1024;
   return c;
@@ -563,17 +563,21 @@ cudaError_t launch_cfg(cudaStream_t st, const CUtensorMap* tmF, const CUtensorMa
 
 template <int BN>
 cudaError_t launch_bn(const OztArgs& a, cudaStream_t st, const OztParams& prm, dim3 grid, int smem) {
-  if (a.a_res) return launch_cfg<BN, 8, true>(st, a.tmF, a.tmB, prm, grid, smem);
-  return launch_cfg<BN, 8, false>(st, a.tmF, a.tmB, prm, grid, smem);
+  // BN = 128: four converter warps (one full 64-wide row per thread), so that the epilogue's
+  // 128 accumulator columns per thread fit the register file of 320 threads
+  constexpr int kConv = BN == 128 ? 4 : 8;
+  if (a.a_res) return launch_cfg<BN, kConv, true>(st, a.tmF, a.tmB, prm, grid, smem);
+  return launch_cfg<BN, kConv, false>(st, a.tmF, a.tmB, prm, grid, smem);
 }
 
 }  // namespace
 
 bool ozt_supported(int K, int bn, bool a_res, bool fold) {
-  if (K % 32 != 0 || (bn != 32 && bn != 48 && bn != 64) || K % bn != 0) return false;
+  if (K % 32 != 0 || (bn != 32 && bn != 48 && bn != 64 && bn != 128) || K % bn != 0) return false;
   if (fold && (K % 128 != 0 || (K / 2) % bn != 0)) return false;
   const OztConfig c = ozt_config(bn, fold ? K / 2 : K, a_res);
-  return c.nat >= 1 && c.nacc >= 2 && c.a_col0 + c.nat * c.at_cols <= 512 && c.sb >= 2 && c.smem <= 227 * 1024;
+  return c.nat >= 1 && c.nacc >= (bn == 128 ? 1 : 2) && c.a_col0 + c.nat * c.at_cols <= 512 && c.sb >= 2 &&
+         c.smem <= 227 * 1024;
 }
 
 cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
@@ -614,6 +618,7 @@ cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
   dim3 grid(items < P->sm_count ? items : P->sm_count);
   switch (bn) {
     case 32: return launch_bn<32>(a, P->stream, prm, grid, smem);
+    case 128: return launch_bn<128>(a, P->stream, prm, grid, smem);
     case 48: return launch_bn<48>(a, P->stream, prm, grid, smem);
     case 64: return launch_bn<64>(a, P->stream, prm, grid, smem);
     default: return cudaErrorInvalidValue;
