@@ -656,12 +656,15 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
   if (pi.oz) {
     const int64_t k2 = (int64_t)K * K;
     const bool res = P->ozt_res;
+    // N = 128 items in the reflection basis: the stage kernels take the rows' powers of two
+    // from the staged rows (over the half an item contracts), so no stage publishes row maxima
+    const bool self_max = P->fold && P->tc_bn == 128;
     if (res && P->fold) {
       // the charge mesh in the reflection basis of its three axes (float32; the same launch
       // clears Phi, which the following stages accumulate into) and its row maxima
-      StepScope sc(P, STEP_SPLIT, 2);
+      StepScope sc(P, STEP_SPLIT, self_max ? 1 : 2);
       KPME_CUDA_TRY(P, launch_fold_mesh(P, Q.p, Q.dbl, P->d_Qfold, K, (float*)Phi, k3));
-      KPME_CUDA_TRY(P, launch_rowmax_rows(P, P->d_Qfold, k2, K, P->d_rmQ));
+      if (!self_max) KPME_CUDA_TRY(P, launch_rowmax_rows(P, P->d_Qfold, k2, K, P->d_rmQ));
     } else if (res) {
       // float32 charge mesh and its row maxima (rows of stage 1)
       StepScope sc(P, STEP_SPLIT, Q.dbl ? 2 : 1);
@@ -687,11 +690,12 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       return KPME_OK;
     }
     if (res) {
-      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmY, 0, (size_t)S.r0 * k2 * sizeof(float), P->stream));
+      if (!self_max) KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmY, 0, (size_t)S.r0 * k2 * sizeof(float), P->stream));
       StepScope sc(P, STEP_SKP1, 1);
-      OztArgs a{&P->tmF_Q, &P->tm_f3, P->d_rmQ, 0, (float*)P->d_Y, k3, 0, P->d_rmY, k2, M, K, K, 2, true,
-                &P->stage1_res};
+      OztArgs a{&P->tmF_Q, &P->tm_f3, P->d_rmQ, 0, (float*)P->d_Y, k3, 0, self_max ? nullptr : P->d_rmY, k2, M, K,
+                K, 2, true, &P->stage1_res};
       a.fold = P->fold;
+      a.self_max = self_max;
       KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
     } else {
       {
@@ -705,13 +709,15 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
     }
     if (!res) KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));   // else cleared above
     for (const auto& g : P->groups) {
-      KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
+      if (!self_max)
+        KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
       {
         StepScope sc(P, STEP_SKP2, 1);
         if (res) {
-          OztArgs a{&P->tmF_Y, &P->tm_f2, P->d_rmY, k2, (float*)P->d_Z, k3, g.t0, P->d_rmZ, k2, M, K, K, 2, true,
-                    &g.stage2_res};
+          OztArgs a{&P->tmF_Y, &P->tm_f2, P->d_rmY, k2, (float*)P->d_Z, k3, g.t0, self_max ? nullptr : P->d_rmZ, k2, M,
+                    K, K, 2, true, &g.stage2_res};
           a.fold = P->fold;
+          a.self_max = self_max;
           KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
         } else {
           OzArgs a{&P->tm_f2, &P->tm_Y, S.r0, nullptr, false, 0, nullptr, 0, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K,
@@ -723,6 +729,7 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       if (P->ozt_pp) {
         OztArgs a{&P->tmF_Z, &P->tm_f1, P->d_rmZ, k2, (float*)Phi, 0, 0, nullptr, 0, M, K, K, 1, false, &g.stage3};
         a.fold = P->fold;
+        a.self_max = self_max;
         KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
       } else {
         OzArgs a{&P->tm_f1, nullptr, 0, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1,

@@ -45,6 +45,9 @@ struct OztParams {
   int M, N, Kr, kchunks;
   int kc;               // contracted values per item: Kr, or Kr / 2 with folded factors
   int fold;             // folded: items of output columns n >= Kr / 2 read A columns [Kr/2, Kr)
+  int self_max;         // the converters take each row's power of two from the staged chunks of
+                        // the row (every chunk of a unit staged at once, one thread per row);
+                        // rowmax_in is not read
   int sb, bstage;       // factor ring: stages and bytes per stage
   int sf;               // float32 staging stages
   int nacc, nat;        // accumulator buffers (2 BN columns each); A slots
@@ -308,11 +311,35 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
       const int p0 = s_start[job], p1 = s_start[job + 1];
       const int nunits = A_RES ? 1 : p1 - p0;
       // the row maximum of unit u + 1 is loaded while unit u is cut
-      float rm_next = valid ? prm.rowmax_in[(int64_t)s_pairs[p0].x * prm.rm_in_bs + row] : 0.0f;
+      float rm_next = (valid && !prm.self_max) ? prm.rowmax_in[(int64_t)s_pairs[p0].x * prm.rm_in_bs + row] : 0.0f;
       for (int u = 0; u < nunits && ok; ++u) {
-        const float rm = rm_next;
-        if (u + 1 < nunits)
+        float rm = rm_next;
+        if (u + 1 < nunits && !prm.self_max)
           rm_next = valid ? prm.rowmax_in[(int64_t)s_pairs[p0 + u + 1].x * prm.rm_in_bs + row] : 0.0f;
+        if (prm.self_max) {
+          // every chunk of this unit is staged at once (kchunks <= sf): the maximum of the
+          // thread's row over the unit's k range, read from the staging buffers, which stay
+          // held until each chunk is cut below (their phases are waited again there at once)
+          rm = 0.0f;
+          for (int c = 0; c < kchunks && ok; ++c) {
+            const int jc = jf + c, s = jc % prm.sf;
+            if (!__all_sync(0xffffffffu, mbar_wait(&full_f[s], (uint32_t)(jc / prm.sf) & 1u, wc))) {
+              ok = false;
+              break;
+            }
+            const uint8_t* stg = ring_f + s * kFStage;
+#pragma unroll
+            for (int hh = 0; hh < kHalves; ++hh) {
+              const uint8_t* rowp = stg + (h_first + hh) * kFBox + r * 128;
+#pragma unroll
+              for (int j = 0; j < 8; ++j) {
+                const float4 x = *reinterpret_cast<const float4*>(rowp + ((j ^ (r & 7)) << 4));
+                rm = fmaxf(rm, fmaxf(fmaxf(fabsf(x.x), fabsf(x.y)), fmaxf(fabsf(x.z), fabsf(x.w))));
+              }
+            }
+          }
+          if (!ok) break;
+        }
         int e = 0;
         frexpf(rm, &e);
         int slot = 0;
@@ -584,12 +611,17 @@ cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
   const int bn = P->tc_bn;
   const int kc = a.fold ? a.Kr / 2 : a.Kr;
   const OztConfig c = ozt_config(bn, kc, a.a_res);
+  // one converter thread per row (four converter warps, BN = 128) and every chunk of a unit
+  // staged at once: the converters take the rows' powers of two themselves
+  const int kchunks_ = (kc + kChunk - 1) / kChunk;
+  if (a.self_max && !(bn == 128 && kchunks_ <= c.sf)) return cudaErrorInvalidValue;
   OztParams prm{};
   prm.M = a.M;
   prm.N = a.N;
   prm.Kr = a.Kr;
   prm.kc = kc;
   prm.fold = a.fold ? 1 : 0;
+  prm.self_max = a.self_max ? 1 : 0;
   prm.kchunks = (kc + kChunk - 1) / kChunk;
   prm.sb = c.sb;
   prm.bstage = kSlices * bn * 128;

@@ -318,6 +318,8 @@ struct OztArgs {
   const JobList* jobs;
   bool fold = false;         // block-diagonal factors: an item contracts the K/2 values of its
                              // output column's half (A columns [K/2, K) for columns n >= K/2)
+  bool self_max = false;     // the kernel takes the rows' powers of two from the staged rows
+                             // (rowmax_in unused; needs BN = 128 and the unit's chunks staged)
 };
 struct OzfArgs {
   const float* Y;            // float32 Y (r0 planes x K^2 rows x K), device
