@@ -118,6 +118,9 @@ void release_skp_buffers(kpme_plan_t P) {
   dfree(P->d_rmQ);
   dfree(P->d_rmY);
   dfree(P->d_Qfold);
+  dfree(P->d_facv_oz);
+  free_joblist(P->vir_jobs);
+  P->vir_tc = false;
   free_joblist(P->stage1);
   free_joblist(P->stage1_res);
   free_joblist(P->stage23);
@@ -555,6 +558,29 @@ kpme_status_t install_skp(kpme_plan_t P) {
     }
     if (!ok) return KPME_ERR_CUDA;
   }
+  // the virial's rank-one operator V (x) V (x) V on the tensor cores where the SKP runs N = 128
+  // items in the reflection basis: its circulant's digits in the basis, one pair per stage
+  if (pi.oz && P->fold && P->tc_bn == 128 && !S.dense && !lagrange(P)) {
+    double* dg = nullptr;
+    if ((st = dalloc(P, (void**)&dg, (size_t)K * sizeof(double))) != KPME_OK) return st;
+    if ((st = dalloc(P, &P->d_facv_oz, (size_t)slices * K * kcols * eb)) != KPME_OK) {
+      cudaFree(dg);
+      return st;
+    }
+    cudaError_t e = launch_virial_generator(P, dg);
+    if (e == cudaSuccess) e = launch_materialize(P, dg, 1, P->d_facv_oz, slices, kind);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(P->stream);
+    cudaFree(dg);
+    P->scratch_bytes -= (int64_t)K * sizeof(double);
+    KPME_CUDA_TRY(P, e);
+    P->vir_jobs.h_start = {0, 1};
+    P->vir_jobs.h_pairs = {make_int2(0, 0)};
+    if ((st = upload_joblist(P, P->vir_jobs)) != KPME_OK) return st;
+    if (!encode_tmap(P, &P->tm_v, P->d_facv_oz, pi.elem_bytes, false, kcols, (uint64_t)K, slices, 128 / pi.elem_bytes,
+                     P->tc_bn))
+      return KPME_ERR_CUDA;
+    P->vir_tc = true;
+  }
   KPME_CUDA_TRY(P, cudaStreamSynchronize(P->stream));
   return KPME_OK;
 }
@@ -783,6 +809,34 @@ kpme_status_t virial_mesh(kpme_plan_t P, MeshRef Q) {
   KPME_CUDA_TRY(P, launch_mp_simt(dbl, P->d_tmp2, 0, P->d_facv, P->d_Psi, 0, M, K, K, P->single, 0, P->stream));
   KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_qpsi, 0, sizeof(double), P->stream));
   KPME_CUDA_TRY(P, launch_dot(P, Qv, P->d_Psi, k3, P->d_qpsi));
+  return KPME_OK;
+}
+
+// The same mesh part with Ψ = V (x) V (x) V Q applied as a one-term SKP by the tensor-core
+// stage kernels (reflection basis, error-free split, the SKP's own scratch planes: it runs
+// after the SKP on the plan's stream), Ψ unfolded, then ⟨Q, Ψ⟩.
+kpme_status_t virial_mesh_tc(kpme_plan_t P, MeshRef Q) {
+  const int K = P->p.K, M = K * K;
+  const int64_t k3 = K3(P), k2 = (int64_t)K * K;
+  if (Q.dbl) return KPME_ERR_UNSUPPORTED;
+  StepScope sc(P, STEP_VIRIAL, 6);
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_Psi, 0, (size_t)k3 * sizeof(float), P->stream));
+  OztArgs a1{&P->tmF_Q, &P->tm_v, nullptr, 0, (float*)P->d_Y, k3, 0, nullptr, 0, M, K, K, 2, true, &P->vir_jobs};
+  a1.fold = true;
+  a1.self_max = true;
+  KPME_CUDA_TRY(P, launch_mp_ozt(P, a1));
+  OztArgs a2{&P->tmF_Y, &P->tm_v, nullptr, 0, (float*)P->d_Z, k3, 0, nullptr, 0, M, K, K, 2, true, &P->vir_jobs};
+  a2.fold = true;
+  a2.self_max = true;
+  KPME_CUDA_TRY(P, launch_mp_ozt(P, a2));
+  OztArgs a3{&P->tmF_Z, &P->tm_v, nullptr, 0, (float*)P->d_Psi, 0, 0, nullptr, 0, M, K, K, 1, false, &P->vir_jobs};
+  a3.fold = true;
+  a3.self_max = true;
+  KPME_CUDA_TRY(P, launch_mp_ozt(P, a3));
+  KPME_CUDA_TRY(P, launch_unfold_mesh(P, (float*)P->d_Psi, K));
+  KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_qpsi, 0, sizeof(double), P->stream));
+  KPME_CUDA_TRY(P, launch_dot(P, Q.p, P->d_Psi, k3, P->d_qpsi));
+  (void)k2;
   return KPME_OK;
 }
 
@@ -1226,7 +1280,7 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
   }
   // the virial's mesh part only reads Q: outside profiling it runs on a forked branch,
   // concurrently with the SKP stages, and joins before the finalisation
-  const bool fork = vir && n > 0 && !P->profiling && P->side_stream;
+  const bool fork = vir && n > 0 && !P->profiling && P->side_stream && !P->vir_tc;
   if (fork) {
     KPME_CUDA_TRY(P, cudaEventRecord(P->ev_fork, P->stream));
     KPME_CUDA_TRY(P, cudaStreamWaitEvent(P->side_stream, P->ev_fork, 0));
@@ -1246,7 +1300,7 @@ kpme_status_t kpme::eval_energy_forces(kpme_plan_t P, int64_t n, const double* x
     if (n > 0) {
       if (fork)
         KPME_CUDA_TRY(P, cudaStreamWaitEvent(P->stream, P->ev_join, 0));
-      else if ((st = virial_mesh(P, m)) != KPME_OK)
+      else if ((st = P->vir_tc ? virial_mesh_tc(P, m) : virial_mesh(P, m)) != KPME_OK)
         return st;
       if ((st = virial_finish(P, energy, vir)) != KPME_OK) return st;
     } else {

@@ -164,6 +164,12 @@ struct kpme_plan_s {
                                    // (K % 128 == 0): block-diagonal factors, K/2 contraction
   bool allow_fold = true;          // KPME_FOLD=0 keeps the dense factors
   float* d_Qfold = nullptr;        // the charge mesh in the reflection basis (float32)
+  // the virial's rank-one mesh operator on the tensor cores (reflection basis, N = 128 items):
+  // digits of its circulant in the basis, its tensor map and the three one-pair job lists
+  bool vir_tc = false;
+  void* d_facv_oz = nullptr;
+  CUtensorMap tm_v{};
+  kpme::JobList vir_jobs;
   bool allow_fused = true;         // tuning knob: may the fused kernel be used
   int tune_split = 2;              // tuning knob: split-K counts x tune_split / 2
   bool no_sort = false;            // tuning knob: float64-atomic spreading, untiled gathering
