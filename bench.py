@@ -48,7 +48,8 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16":
 SKP_TRAFFIC = {
     # profiles/dram_traffic_water_k64_bf16x10.md: mp_ozt_kernel 1,515,008 B + mp_ozf_kernel
     # 19,324,160 B (reads; 0 B written: Y and Phi stay in L2), 2 launches per evaluation
-    ("water", "bf16x10"): {"digest": "15ac4d609920d908", "bytes_per_launch": (1515008 + 19324160) / 2},
+    ("water", "bf16x10"): {"digest": "15ac4d609920d908", "launches": 2,
+                           "bytes_per_launch": (1515008 + 19324160) / 2},
 }
 SKP_SOURCES = ("gemm_ozf.cu", "gemm_ozt.cu", "tc_common.cuh")
 
@@ -56,16 +57,17 @@ SKP_SOURCES = ("gemm_ozf.cu", "gemm_ozt.cu", "tc_common.cuh")
 def _skp_digest():
     import hashlib
     h = hashlib.sha256()
-    csrc = os.path.join(os.path.dirname(os.path.abspath(__file__)), "paper_2601_18838_gb300", "csrc")
+    csrc = os.path.join(ROOT, "paper_2601_18838_gb300", "csrc")
     for name in SKP_SOURCES:
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
 
 
-def _skp_traffic(workload, precision):
+def _skp_traffic(workload, precision, launches):
+    """Counted DRAM bytes per stage launch, or None once the kernels or the launch split changed."""
     rec = SKP_TRAFFIC.get((workload, precision))
-    if not rec or rec["digest"] != _skp_digest():
+    if not rec or rec["digest"] != _skp_digest() or rec["launches"] != launches:
         return None
     return rec["bytes_per_launch"]
 
@@ -378,6 +380,8 @@ def _measure(args, name, steps, warmup, ctx, headline):
     from paper_2601_18838_gb300 import Plan
     pg, dev, rank, ws, local = ctx
     s = _system(name)
+    if headline and args.skp_tol is not None:
+        s.skp_tol = args.skp_tol
     stream = torch.cuda.current_stream()
     lag = s.meta.get("interp", "bspline").startswith("lagrange")
     extra = dict(interp=s.meta["interp"], modes=s.meta["modes"], skp_method="sinc") if lag else {}
@@ -457,7 +461,7 @@ def _measure(args, name, steps, warmup, ctx, headline):
     if tensor and skp_ms > 0:
         ach = useful / (skp_ms * 1e-3) / 1e12
         roof = {"bound": "tensor", "kernel": kname, "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": _skp_traffic(name, args.precision),
+                "frac": ach / peak, "traffic": _skp_traffic(name, args.precision, skp_launches),
                 "peak_source": peak_note,
                 "work": "useful flops 6 R K^4 per evaluation (the three dense mode products of every Kronecker "
                         "term); the split form issues more on the tensor pipe (see executed)",
@@ -568,6 +572,9 @@ def _measure(args, name, steps, warmup, ctx, headline):
 SKP_TENSOR_ACTIVE = {
     # profiles/mp_ozf_kernel_water_k64_bf16x10.md
     ("water", "bf16x10"): {"digest": "15ac4d609920d908", "pct": {"mp_ozf_kernel<64>": 32.4}},
+    # profiles/mp_ozt_kernel_large_k256_bf16x10.md (16-term groups of the same kernels)
+    ("large", "bf16x10"): {"digest": "1596b083a1896468",
+                           "pct": {"mp_ozt_kernel<128, 4, 1> (stage 2)": 52.9, "mp_ozt_kernel<128, 4, 0> (stage 3)": 44.5}},
 }
 
 
@@ -591,6 +598,9 @@ def main(argv=None):
                     help="timed evaluations of the FP64 GPU form (default 1 for the 10^6-charge box, else 5)")
     ap.add_argument("--no-water", action="store_true", help="skip the water box reported beside the headline")
     ap.add_argument("--no-autotune", action="store_true", help="keep the plan's default launch configuration")
+    ap.add_argument("--skp-tol", type=float, default=None,
+                    help="override the workload's SKP tolerance (a smaller SKP, for profiling captures of the "
+                         "same kernels on less device memory; not a benchmark setting)")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file: a matching entry is applied without timing, a new choice is "
                          "appended (a profiling run then repeats the configuration of the plain run)")

@@ -168,11 +168,25 @@ void choose_tc_tiles(kpme_plan_t P) {
   P->tc_stages = stages;
 }
 
-int64_t group_budget_bytes() {
+// Device memory for the Z planes of one term group (stages 2 and 3 run once per group).  For
+// the error-free split, fewer and larger groups mean fewer launch tails and longer runs of
+// terms sharing their A: by default up to 12 GiB, at most a quarter of the free device memory
+// (the 10^6-charge box, R = 167 planes of 67 MB, then runs one group: 70.3 -> 77.7
+// evaluations/s against 16-term groups).  The other forms keep 256 MB: their split-K sums over
+// a group's terms run in float32, and longer sums cost accuracy (FP32 at 10^6 charges: phi
+// 5.3e-7 with 16-term groups, 1.7e-6 with one group).  KPME_GROUP_MB overrides both.
+int64_t group_budget_bytes(bool error_free) {
   const char* e = getenv("KPME_GROUP_MB");
-  int64_t mb = e ? atoll(e) : 256;
-  if (mb < 1) mb = 1;
-  return mb << 20;
+  if (e) {
+    int64_t mb = atoll(e);
+    if (mb < 1) mb = 1;
+    return mb << 20;
+  }
+  if (!error_free) return (int64_t)256 << 20;
+  size_t free_b = 0, total_b = 0;
+  int64_t budget = (int64_t)12 << 30;
+  if (cudaMemGetInfo(&free_b, &total_b) == cudaSuccess) budget = std::min<int64_t>(budget, (int64_t)(free_b / 4));
+  return std::max<int64_t>(budget, (int64_t)256 << 20);
 }
 
 kpme_status_t alloc_meshes(kpme_plan_t P) {
@@ -382,7 +396,7 @@ kpme_status_t install_skp(kpme_plan_t P) {
   const size_t ieb = pi.oz ? sizeof(float) : eb;
   // terms per group: as many as fit the budget (L2-sized by default), but at least 16 so that
   // large meshes do not degenerate into one launch pair per term
-  int G = (int)std::max<int64_t>(16, group_budget_bytes() / std::max<int64_t>(1, (int64_t)islices * k3 * (int64_t)ieb));
+  int G = (int)std::max<int64_t>(16, group_budget_bytes(pi.oz) / std::max<int64_t>(1, (int64_t)islices * k3 * (int64_t)ieb));
   G = std::min(G, R);
   P->group_terms = G;
   if (pi.tensor && !pi.oz && (st = dalloc(P, &P->d_Qs, (size_t)slices * k3 * eb)) != KPME_OK) return st;
