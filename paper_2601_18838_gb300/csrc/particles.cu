@@ -12,7 +12,20 @@ constexpr int kThreads = 256;
 struct MeshGeom {
   double c0, c1, c2, L;
   int K;
+  df cd[3], rinv;   // the centre and 1/L as double-float pairs (mesh_coord_df)
 };
+
+df split_host(double v) {
+  const float h = (float)v;
+  return {h, (float)(v - (double)h)};
+}
+
+void set_df_fields(MeshGeom& G) {
+  G.cd[0] = split_host(G.c0);
+  G.cd[1] = split_host(G.c1);
+  G.cd[2] = split_host(G.c2);
+  G.rinv = split_host(1.0 / G.L);
+}
 
 // Mesh coordinate of one component: u = K ((x - c)/L + 1/2) wrapped into [0, K), split
 // into g = floor(u) and f = u - g.  Every operation is an explicitly rounded float64
@@ -29,6 +42,33 @@ __device__ __forceinline__ void mesh_coord(double x, double c, double L, int K, 
   double fl = floor(m);
   g = (int)fl;
   f = __dsub_rn(m, fl);
+}
+
+// The same coordinate on the float32 pipe (the float64 unit of this GPU issues one warp
+// instruction per many cycles): u in double-float arithmetic (about 44 bits; within 2^-35 of
+// the float64 u of mesh_coord for |x - c| below a few box lengths), wrapped into [0, K).
+// Where u is farther than 2^-20 from a cell boundary both floors agree, so g is the cell
+// mesh_coord decides; nearer a boundary (a rare branch), or for an x the split does not
+// represent, the float64 sequence of mesh_coord decides g and f.
+__device__ __forceinline__ void mesh_coord_df(double x, int a, const MeshGeom& G, int& g, df& f) {
+  bool ok;
+  const df xd = df_bits(x, ok);
+  const df c = G.cd[a];
+  const df t = df_add(xd, {-c.hi, -c.lo});
+  df u = df_scale(df_add(df_mul(t, G.rinv), {0.5f, 0.0f}), (float)G.K);
+  const float Kf = (float)G.K;
+  if (u.hi < 0.0f)
+    u = df_add(u, {Kf, 0.0f});
+  else if (u.hi >= Kf)
+    u = df_add(u, {-Kf, 0.0f});
+  const float fl = floorf(u.hi);
+  f = df_add(u, {-fl, 0.0f});
+  g = (int)fl;
+  if (!(ok && f.hi > 0x1p-20f && f.hi < 1.0f - 0x1p-20f && g >= 0 && g < G.K)) {
+    double fd;
+    mesh_coord(x, a == 0 ? G.c0 : (a == 1 ? G.c1 : G.c2), G.L, G.K, g, fd);
+    f = df_from(fd);
+  }
 }
 
 // Weights M_n(f + j), j = 0..n-1, by the order recursion, and their derivatives
@@ -65,6 +105,56 @@ __device__ __forceinline__ T block_sum_to_thread0(T v) {
   if (threadIdx.x == 0)
     for (int i = 0; i < kThreads / 32; ++i) s += red[i];
   return s;
+}
+
+// A float64 value as a double-float pair, by its bits where df_bits represents it.
+__device__ __forceinline__ df to_df(double v) {
+  bool ok;
+  const df r = df_bits(v, ok);
+  return ok ? r : df_from(v);
+}
+
+// Block sum of double-float pairs, complete in thread 0 (as float64, one addition per block).
+__device__ __forceinline__ double block_sum_df_to_thread0(df v) {
+  __shared__ float red_hi[kThreads / 32], red_lo[kThreads / 32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1)
+    v = df_add(v, {__shfl_down_sync(0xffffffffu, v.hi, o), __shfl_down_sync(0xffffffffu, v.lo, o)});
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) {
+    red_hi[w] = v.hi;
+    red_lo[w] = v.lo;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return 0.0;
+  df s = {0.0f, 0.0f};
+  for (int i = 0; i < kThreads / 32; ++i) s = df_add(s, {red_hi[i], red_lo[i]});
+  return dbl_of(s.hi) + dbl_of(s.lo);
+}
+
+// The float32 forms' per-particle outputs without the float64 unit: phi = (p - shift) ke and
+// F = -q ke (K/L) grad in double-float arithmetic, each written as the float64 value of its
+// float32 rounding (the gathered sums are float32 already), and q phi added to a double-float
+// energy sum.
+struct GatherOut {
+  df shift, ke, gscale;
+};
+__device__ __forceinline__ GatherOut gather_out(double shift, double ke, double gscale) {
+  return {to_df(shift), to_df(ke), to_df(gscale)};
+}
+__device__ __forceinline__ void write_outputs(const GatherOut& c, float p, float g0, float g1, float g2, double qv,
+                                              int64_t i, double* __restrict__ phi_out, double* __restrict__ F_out,
+                                              df& e) {
+  const df ph = df_mul(df_add({p, 0.0f}, {-c.shift.hi, -c.shift.lo}), c.ke);
+  const df qd = to_df(qv);
+  if (phi_out) phi_out[i] = dbl_of(ph.hi);
+  if (F_out) {
+    const df s = df_mul(df_mul(qd, c.ke), c.gscale);
+    F_out[3 * i + 0] = dbl_of(-df_mul_rn(s, {g0, 0.0f}));
+    F_out[3 * i + 1] = dbl_of(-df_mul_rn(s, {g1, 0.0f}));
+    F_out[3 * i + 2] = dbl_of(-df_mul_rn(s, {g2, 0.0f}));
+  }
+  e = df_add(e, df_mul(qd, ph));
 }
 
 template <typename T, int N>
@@ -110,15 +200,19 @@ __global__ void __launch_bounds__(kThreads) spread_kernel(MeshGeom G, int64_t n,
 }
 
 template <typename T, int N>
-__global__ void __launch_bounds__(kThreads) gather_kernel(MeshGeom G, int64_t n, const double* __restrict__ x,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float) ? 2 : 1) gather_kernel(MeshGeom G, int64_t n, const double* __restrict__ x,
                                                           const double* __restrict__ q, const T* __restrict__ Phi,
                                                           double* __restrict__ phi_out, double* __restrict__ F_out,
                                                           double* __restrict__ energy, const double* __restrict__ sumq,
                                                           double corr_c, double ke, const float4* __restrict__ coords) {
+  constexpr bool kF32 = sizeof(T) == sizeof(float);
   const int K = G.K;
   const double shift = corr_c * (sumq ? *sumq : 0.0);
   const T gscale = (T)((double)K / G.L);
+  GatherOut oc{};
+  if constexpr (kF32) oc = gather_out(shift, ke, (double)K / G.L);
   double e = 0.0;
+  df e_df = {0.0f, 0.0f};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
     int g[3];
     T w[3][N], dw[3][N];
@@ -128,7 +222,11 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(MeshGeom G, int64_t n,
       if (coords) {   // the spreading's coordinates: no float64 work here
         const float4 c = coords[3 * i + a];
         g[a] = __float_as_int(c.x);
-        ft = sizeof(T) == sizeof(float) ? (T)c.y : (T)((double)c.y + (double)c.z);
+        ft = kF32 ? (T)c.y : (T)((double)c.y + (double)c.z);
+      } else if constexpr (kF32) {
+        df f;
+        mesh_coord_df(x[3 * i + a], a, G, g[a], f);
+        ft = f.hi;
       } else {
         double f;
         mesh_coord(x[3 * i + a], a == 0 ? G.c0 : (a == 1 ? G.c1 : G.c2), G.L, K, g[a], f);
@@ -165,19 +263,27 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(MeshGeom G, int64_t n,
       g1 += w[0][j0] * s_1;
       g2 += w[0][j0] * s_2;
     }
-    const double phi = ((double)p - shift) * ke;
     const double qi = q ? q[i] : 0.0;
-    if (phi_out) phi_out[i] = phi;
-    if (F_out) {
-      const double s = -qi * ke * (double)gscale;
-      F_out[3 * i + 0] = s * (double)g0;
-      F_out[3 * i + 1] = s * (double)g1;
-      F_out[3 * i + 2] = s * (double)g2;
+    if constexpr (kF32) {
+      write_outputs(oc, p, g0, g1, g2, qi, i, phi_out, F_out, e_df);
+    } else {
+      const double phi = ((double)p - shift) * ke;
+      if (phi_out) phi_out[i] = phi;
+      if (F_out) {
+        const double s = -qi * ke * (double)gscale;
+        F_out[3 * i + 0] = s * (double)g0;
+        F_out[3 * i + 1] = s * (double)g1;
+        F_out[3 * i + 2] = s * (double)g2;
+      }
+      e += 0.5 * qi * phi;
     }
-    e += 0.5 * qi * phi;
   }
   if (energy) {
-    double s = block_sum_to_thread0<double>(e);
+    double s;
+    if constexpr (kF32)
+      s = 0.5 * block_sum_df_to_thread0(e_df);
+    else
+      s = block_sum_to_thread0<double>(e);
     if (threadIdx.x == 0) atomicAdd(energy, s);
   }
 }
@@ -185,10 +291,22 @@ __global__ void __launch_bounds__(kThreads) gather_kernel(MeshGeom G, int64_t n,
 template <typename T>
 __global__ void __launch_bounds__(kThreads) dot_kernel(const T* __restrict__ a, const T* __restrict__ b,
                                                        int64_t count, double* __restrict__ out) {
-  double acc = 0.0;
-  for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
-    acc += (double)a[i] * (double)b[i];
-  double s = block_sum_to_thread0<double>(acc);
+  double s;
+  if constexpr (sizeof(T) == sizeof(float)) {
+    // float32 meshes: exact products (fma error term) summed in double-float pairs
+    df acc = {0.0f, 0.0f};
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads) {
+      const float x = a[i], y = b[i];
+      const float p = x * y;
+      acc = df_add(acc, {p, fmaf(x, y, -p)});
+    }
+    s = block_sum_df_to_thread0(acc);
+  } else {
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < count; i += (int64_t)gridDim.x * kThreads)
+      acc += (double)a[i] * (double)b[i];
+    s = block_sum_to_thread0<double>(acc);
+  }
   if (threadIdx.x == 0) atomicAdd(out, s);
 }
 
@@ -218,6 +336,7 @@ MeshGeom geom(kpme_plan_t P) {
   G.c2 = P->p.center[2];
   G.L = 2.0 * P->p.radius;
   G.K = P->p.K;
+  set_df_fields(G);
   return G;
 }
 
@@ -339,6 +458,7 @@ cudaError_t launch_spread_raw(const kpme_params_t& p, int sm_count, cudaStream_t
   G.c2 = p.center[2];
   G.L = 2.0 * p.radius;
   G.K = p.K;
+  set_df_fields(G);
   int64_t want = (n + kThreads - 1) / kThreads;
   const int64_t cap = (int64_t)sm_count * 8;
   const int grid = (int)(want > cap ? cap : (want < 1 ? 1 : want));
@@ -381,20 +501,21 @@ __device__ __forceinline__ int tile_of(const int (&g)[3], const Tiling& t) {
 
 // One sorted record per particle (two float4, 32 bytes): the mesh cell g packed 10 bits per
 // axis, the particle index, and the fractional offsets f of the three axes as float pairs
-// (hi + lo carries f to ~48 bits).  The float64 mesh coordinate is computed once, here.
+// (hi + lo carries f to ~44 bits).  The mesh coordinate is computed once, here
+// (mesh_coord_df: the cell of the float64 rounding sequence, on the float32 pipe).
 __global__ void tile_count_kernel(MeshGeom G, Tiling tl, int64_t n, const double* __restrict__ x,
                                   const double* __restrict__ q, int* __restrict__ count, int2* __restrict__ tile_slot,
                                   float4* __restrict__ rec, double* __restrict__ sumq) {
-  double qs = 0.0;
+  df qs = {0.0f, 0.0f};
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
     int g[3];
     float fh[3], fl[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-      double f;
-      mesh_coord(x[3 * i + a], a == 0 ? G.c0 : (a == 1 ? G.c1 : G.c2), G.L, G.K, g[a], f);
-      fh[a] = (float)f;
-      fl[a] = (float)(f - (double)fh[a]);
+      df f;
+      mesh_coord_df(x[3 * i + a], a, G, g[a], f);
+      fh[a] = f.hi;
+      fl[a] = f.lo;
     }
     const int t = tile_of(g, tl);
     // 8 counters per tile (chosen by the particle index) cut the contention of the returned
@@ -404,10 +525,10 @@ __global__ void tile_count_kernel(MeshGeom G, Tiling tl, int64_t n, const double
     const int gp = g[0] | (g[1] << 10) | (g[2] << 20);
     rec[2 * i] = make_float4(__int_as_float(gp), __int_as_float((int)i), fh[0], fl[0]);
     rec[2 * i + 1] = make_float4(fh[1], fl[1], fh[2], fl[2]);
-    if (sumq) qs += q[i];
+    if (sumq) qs = df_add(qs, to_df(q[i]));
   }
   if (sumq) {
-    const double s = block_sum_to_thread0<double>(qs);
+    const double s = block_sum_df_to_thread0(qs);
     if (threadIdx.x == 0 && s != 0.0) atomicAdd(sumq, s);
   }
 }
@@ -469,6 +590,15 @@ __device__ __forceinline__ void bspline_df(df f, df* w) {
   }
 }
 
+// Spreading passes: a warp takes PP particles, 3 PP lanes compute their weights (one axis
+// each), then n lanes per particle (PW = 32 / n particles per round) add the contributions.
+template <int N>
+struct SpreadPass {
+  static constexpr int PP = N == 6 ? 10 : 8;   // particles per warp pass (3 PP <= 32)
+  static constexpr int PW = 32 / N;            // particles per contribution round
+  static constexpr int ROUNDS = (PP + PW - 1) / PW;
+};
+
 // Lanes per particle: one lane per j0 plane of the n^3 stencil (4 for order 4, 8 for 6 / 8).
 template <int N>
 struct Lanes {
@@ -518,14 +648,15 @@ __device__ __forceinline__ Rec load_rec(const float4* __restrict__ rec, int p) {
 
 // Tile-staged spreading: one CTA per tile of T^3 cells accumulates its particles' n^3
 // stencils into a shared (T + n - 1)^3 region, then adds the region's nonzeros to Q.
-// Each particle is handled by a group of LG lanes, one j0 plane of its stencil per lane.
+// Each warp takes PP sorted particles per pass with the lane roles of spread_nosort_kernel
+// (3 PP weight lanes, then n lanes per particle writing n consecutive points of a region row).
 template <int N>
 __global__ void __launch_bounds__(kThreads) spread_tile_kernel(Tiling tl, const double* __restrict__ q,
                                                                const int* __restrict__ start,
                                                                const float4* __restrict__ rec, float* __restrict__ Q) {
   extern __shared__ float region[];
   constexpr int H = N - 1;
-  constexpr int LG = Lanes<N>::value;
+  constexpr int PP = SpreadPass<N>::PP, PW = SpreadPass<N>::PW;
   const int D = tl.T + H;
   const int K = tl.K;
   const int t = blockIdx.x;
@@ -535,41 +666,63 @@ __global__ void __launch_bounds__(kThreads) spread_tile_kernel(Tiling tl, const 
   if (p1 == p0) return;
   for (int i = threadIdx.x; i < D * D * D; i += kThreads) region[i] = 0.0f;
   __syncthreads();
-  const int gl = threadIdx.x % LG;
-  const int base = (threadIdx.x & 31) - gl;
-  for (int pb = p0; pb < p1; pb += kThreads / LG) {
-    const int p = pb + threadIdx.x / LG;
-    const bool active = p < p1;
-    const unsigned mask = __ballot_sync(0xffffffffu, active);
-    if (!active) continue;
-    const Rec r = load_rec(rec, p);
-    df mine[N], w[3][N];
-    bspline_df<N>(gl == 0 ? r.f[0] : (gl == 1 ? r.f[1] : r.f[2]), mine);
-    share_axes<N>(mine, w, base, mask);
-    if (gl >= N) continue;
-    const df qw0 = df_mul(df_from(q[r.i]), pick<N>(w[0], gl));
-    const int b0 = r.g[0] - t0 * tl.T + H - gl, b1 = r.g[1] - t1 * tl.T + H, b2 = r.g[2] - t2 * tl.T + H;
+  const int lane = threadIdx.x & 31;
+  const int wp = lane / 3, wa = lane - 3 * wp;
+  for (int pb = p0 + (threadIdx.x >> 5) * PP; pb < p1; pb += (kThreads / 32) * PP) {
+    // weight phase: the record's cell and offset of axis wa (cells relative to the region)
+    int myb = 0, myi = 0;
+    df mine[N];
 #pragma unroll
-    for (int j1 = 0; j1 < N; ++j1) {
-      const df w01 = df_mul(qw0, w[1][j1]);
-      float* row = region + (b0 * D + (b1 - j1)) * D + b2;
+    for (int j = 0; j < N; ++j) mine[j] = {0.0f, 0.0f};
+    if (wp < PP && pb + wp < p1) {
+      const Rec r = load_rec(rec, pb + wp);
+      const int lo = wa == 0 ? lo0 : (wa == 1 ? lo1 : lo2);
+      myb = r.g[wa] - lo;   // in [H, D): g - t T + H
+      myi = r.i;
+      bspline_df<N>(wa == 0 ? r.f[0] : (wa == 1 ? r.f[1] : r.f[2]), mine);
+    }
 #pragma unroll
-      for (int j2 = 0; j2 < N; ++j2) {
-        const df c = df_mul(w01, w[2][j2]);   // rounded once to float32 below
-        atomicAdd(row - j2, c.hi + c.lo);
+    for (int rd = 0; rd < SpreadPass<N>::ROUNDS; ++rd) {
+      const int pl = rd * PW + lane / N;
+      const int gl = lane - (lane / N) * N;   // j2
+      const int src = 3 * (pl < PP ? pl : 0);
+      const int b0 = __shfl_sync(0xffffffffu, myb, src), b1 = __shfl_sync(0xffffffffu, myb, src + 1),
+                b2 = __shfl_sync(0xffffffffu, myb, src + 2);
+      const int pi = __shfl_sync(0xffffffffu, myi, src);
+      df w0[N], w1[N], w2[N];
+#pragma unroll
+      for (int j = 0; j < N; ++j) {
+        w0[j] = shfl_w(0xffffffffu, mine[j], src);
+        w1[j] = shfl_w(0xffffffffu, mine[j], src + 1);
+        w2[j] = shfl_w(0xffffffffu, mine[j], src + 2);
+      }
+      if (lane >= PW * N || pl >= PP || pb + pl >= p1) continue;
+      const df c2 = df_mul(to_df(q[pi]), pick<N>(w2, gl));
+      float* col = region + b2 - gl;
+#pragma unroll
+      for (int j0 = 0; j0 < N; ++j0) {
+        const df c02 = df_mul(c2, w0[j0]);
+        float* plane = col + (b0 - j0) * D * D;
+#pragma unroll
+        for (int j1 = 0; j1 < N; ++j1) atomicAdd(plane + (b1 - j1) * D, df_mul_rn(c02, w1[j1]));
       }
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < D * D * D; idx += kThreads) {
-    const float v = region[idx];
-    if (v == 0.0f) continue;
-    const int l2 = idx % D, l1 = (idx / D) % D, l0 = idx / (D * D);
-    int k0 = lo0 + l0, k1 = lo1 + l1, k2 = lo2 + l2;
+  // the region's nonzeros into Q, one (l0, l1) row per warp and pass, l2 along the lanes
+  for (int row = threadIdx.x >> 5; row < D * D; row += kThreads / 32) {
+    const int l0 = row / D, l1 = row - l0 * D;
+    int k0 = lo0 + l0, k1 = lo1 + l1;
     k0 += k0 < 0 ? K : 0;
     k1 += k1 < 0 ? K : 0;
-    k2 += k2 < 0 ? K : 0;
-    atomicAdd(Q + ((int64_t)k0 * K + k1) * K + k2, v);
+    float* dst = Q + ((int64_t)k0 * K + k1) * K;
+    for (int l2 = lane; l2 < D; l2 += 32) {
+      const float v = region[row * D + l2];
+      if (v == 0.0f) continue;
+      int k2 = lo2 + l2;
+      k2 += k2 < 0 ? K : 0;
+      atomicAdd(dst + k2, v);
+    }
   }
 }
 
@@ -594,20 +747,27 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
   const int lo0 = t0 * tl.T - H, lo1 = t1 * tl.T - H, lo2 = t2 * tl.T - H;
   const int p0 = start[t * kTileSub], p1 = start[(t + 1) * kTileSub];
   if (p1 == p0) return;
-  for (int idx = threadIdx.x; idx < D * D * D; idx += kThreads) {
-    const int l2 = idx % D, l1 = (idx / D) % D, l0 = idx / (D * D);
-    int k0 = lo0 + l0, k1 = lo1 + l1, k2 = lo2 + l2;
-    k0 += k0 < 0 ? K : 0;
-    k1 += k1 < 0 ? K : 0;
-    k2 += k2 < 0 ? K : 0;
-    region[idx] = Phi[((int64_t)k0 * K + k1) * K + k2];
+  {
+    // one (l0, l1) row of the region per warp and pass, l2 along the lanes (coalesced)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int row = warp; row < D * D; row += kThreads / 32) {
+      const int l0 = row / D, l1 = row - l0 * D;
+      int k0 = lo0 + l0, k1 = lo1 + l1;
+      k0 += k0 < 0 ? K : 0;
+      k1 += k1 < 0 ? K : 0;
+      const float* src = Phi + ((int64_t)k0 * K + k1) * K;
+      for (int l2 = lane; l2 < D; l2 += 32) {
+        int k2 = lo2 + l2;
+        k2 += k2 < 0 ? K : 0;
+        region[row * D + l2] = src[k2];
+      }
+    }
   }
   __syncthreads();
-  const double shift = corr_c * (sumq ? *sumq : 0.0);
-  const double gscale = (double)K / G.L;
+  const GatherOut oc = gather_out(corr_c * (sumq ? *sumq : 0.0), ke, (double)K / G.L);
   const int gl = threadIdx.x % LG;
   const int base = (threadIdx.x & 31) - gl;
-  double e = 0.0;
+  df e = {0.0f, 0.0f};
   for (int pb = p0; pb < p1; pb += kThreads / LG) {
     const int p = pb + threadIdx.x / LG;
     const bool active = p < p1;
@@ -650,85 +810,88 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
       g2 += __shfl_xor_sync(mask, g2, o);
     }
     if (gl != 0) continue;
-    const double phi = ((double)pv - shift) * ke;
-    const double qi = q ? q[r.i] : 0.0;
-    if (phi_out) phi_out[r.i] = phi;
-    if (F_out) {
-      const double s = -qi * ke * gscale;
-      F_out[3 * (int64_t)r.i + 0] = s * (double)g0;
-      F_out[3 * (int64_t)r.i + 1] = s * (double)g1;
-      F_out[3 * (int64_t)r.i + 2] = s * (double)g2;
-    }
-    e += 0.5 * qi * phi;
+    write_outputs(oc, pv, g0, g1, g2, q ? q[r.i] : 0.0, r.i, phi_out, F_out, e);
   }
   if (energy) {
-    double s = block_sum_to_thread0<double>(e);
+    const double s = 0.5 * block_sum_df_to_thread0(e);
     if (threadIdx.x == 0 && s != 0.0) atomicAdd(energy, s);
   }
 }
 
 // ---- spreading with no cell sort ----
-// A group of LG lanes per particle: lanes 0..2 take the float64 mesh coordinate of one axis
-// each and its double-float B-spline weights, shared with the group by shuffles; lane l then
-// adds the n^2 stencil values of column j2 = l, so at every (j0, j1) the lanes of a group
-// write n consecutive mesh points of one row (n^2 short coalesced segments per particle
-// instead of n^3 scattered words).  Products are rounded once to float32 and added by
-// float32 atomics: the arithmetic of the tile-staged kernel.  (Gathering with no sort is
-// gather_kernel<float>: one thread per particle measured faster than lane groups.)
+// A warp takes PP particles per pass (10 for order 6, else 8).  Weight phase: lane 3p + a
+// (p < PP) takes the mesh coordinate of axis a of particle p (double-float, mesh_coord_df) and
+// its n double-float B-spline weights, so the float32 pipe does this work on 3 PP of the 32
+// lanes.  Contribution rounds: n lanes per particle, PW = 32 / n particles per round; lane j2 of
+// a particle gets the cells and the weights of axes 0 and 1 and its own axis-2 weight by
+// shuffles and adds the n^2 stencil values of mesh column g2 - j2, so at every (j0, j1) the
+// lanes of a particle write n consecutive points of one mesh row.  Products are rounded once
+// to float32 and added by float32 atomics: the arithmetic of the tile-staged kernel.
+// (Gathering with no sort is gather_kernel<float>: one thread per particle measured faster
+// than lane groups.)
 template <int N>
 __global__ void __launch_bounds__(kThreads) spread_nosort_kernel(MeshGeom G, int64_t n, const double* __restrict__ x,
                                                                  const double* __restrict__ q, float* __restrict__ Q,
                                                                  double* __restrict__ sumq,
                                                                  float4* __restrict__ coords) {
-  constexpr int LG = Lanes<N>::value;
-  constexpr int PB = kThreads / LG;   // particles per block and pass
+  constexpr int PP = SpreadPass<N>::PP, PW = SpreadPass<N>::PW;
   const int K = G.K;
-  const int gl = threadIdx.x % LG;
-  const int base = (threadIdx.x & 31) - gl;
-  double qs = 0.0;
-  for (int64_t pb = blockIdx.x * (int64_t)PB; pb < n; pb += (int64_t)gridDim.x * PB) {
-    const int64_t i = pb + threadIdx.x / LG;
-    const bool active = i < n;
-    const unsigned mask = __ballot_sync(0xffffffffu, active);
-    if (!active) continue;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nwarps = ((int64_t)gridDim.x * kThreads) >> 5;
+  const int wp = lane / 3, wa = lane - 3 * wp;   // weight phase: particle and axis of this lane
+  df qs = {0.0f, 0.0f};
+  for (int64_t base = warp * PP; base < n; base += nwarps * PP) {
     int myg = 0;
     df mine[N];
 #pragma unroll
     for (int j = 0; j < N; ++j) mine[j] = {0.0f, 0.0f};
-    if (gl < 3) {
-      double f;
-      mesh_coord(x[3 * i + gl], gl == 0 ? G.c0 : (gl == 1 ? G.c1 : G.c2), G.L, K, myg, f);
-      const df fd = df_from(f);
-      bspline_df<N>(fd, mine);
-      if (coords) coords[3 * i + gl] = make_float4(__int_as_float(myg), fd.hi, fd.lo, 0.0f);
+    const int64_t iw = base + wp;
+    if (wp < PP && iw < n) {
+      df f;
+      mesh_coord_df(x[3 * iw + wa], wa, G, myg, f);
+      bspline_df<N>(f, mine);
+      if (coords) coords[3 * iw + wa] = make_float4(__int_as_float(myg), f.hi, f.lo, 0.0f);
     }
-    int g[3];
 #pragma unroll
-    for (int a = 0; a < 3; ++a) g[a] = __shfl_sync(mask, myg, base + a);
-    df w[3][N];
-    share_axes<N>(mine, w, base, mask);
-    if (gl >= N) continue;
-    const double qi = q[i];
-    if (gl == 0) qs += qi;
-    const df c2 = df_mul(df_from(qi), pick<N>(w[2], gl));
-    int k2 = g[2] - gl;
-    k2 += k2 < 0 ? K : 0;
+    for (int r = 0; r < SpreadPass<N>::ROUNDS; ++r) {
+      const int pl = r * PW + lane / N;
+      const int gl = lane - (lane / N) * N;   // j2
+      const int src = 3 * (pl < PP ? pl : 0);
+      int g[3];
 #pragma unroll
-    for (int j0 = 0; j0 < N; ++j0) {
-      int k0 = g[0] - j0;
-      k0 += k0 < 0 ? K : 0;
-      const df c02 = df_mul(c2, w[0][j0]);
+      for (int a = 0; a < 3; ++a) g[a] = __shfl_sync(0xffffffffu, myg, src + a);
+      df w0[N], w1[N], w2[N];
 #pragma unroll
-      for (int j1 = 0; j1 < N; ++j1) {
-        int k1 = g[1] - j1;
-        k1 += k1 < 0 ? K : 0;
-        const df v = df_mul(c02, w[1][j1]);   // rounded once to float32 below
-        atomicAdd(Q + ((int64_t)k0 * K + k1) * K + k2, v.hi + v.lo);
+      for (int j = 0; j < N; ++j) {
+        w0[j] = shfl_w(0xffffffffu, mine[j], src);
+        w1[j] = shfl_w(0xffffffffu, mine[j], src + 1);
+        w2[j] = shfl_w(0xffffffffu, mine[j], src + 2);
+      }
+      const int64_t i = base + pl;
+      if (lane >= PW * N || pl >= PP || i >= n) continue;
+      const df qd = to_df(q[i]);
+      if (gl == 0) qs = df_add(qs, qd);
+      const df c2 = df_mul(qd, pick<N>(w2, gl));
+      int k2 = g[2] - gl;
+      k2 += k2 < 0 ? K : 0;
+#pragma unroll
+      for (int j0 = 0; j0 < N; ++j0) {
+        int k0 = g[0] - j0;
+        k0 += k0 < 0 ? K : 0;
+        const df c02 = df_mul(c2, w0[j0]);
+        float* plane = Q + (int64_t)k0 * K * K + k2;
+#pragma unroll
+        for (int j1 = 0; j1 < N; ++j1) {
+          int k1 = g[1] - j1;
+          k1 += k1 < 0 ? K : 0;
+          atomicAdd(plane + (int64_t)k1 * K, df_mul_rn(c02, w1[j1]));
+        }
       }
     }
   }
   if (sumq) {
-    const double sq = block_sum_to_thread0<double>(qs);
+    const double sq = block_sum_df_to_thread0(qs);
     if (threadIdx.x == 0 && sq != 0.0) atomicAdd(sumq, sq);
   }
 }
@@ -988,8 +1151,8 @@ __global__ void __launch_bounds__(kLagThreads) lagrange_gather_cell_kernel(
   }
 }
 
-int grid_groups(kpme_plan_t P, int64_t n, int lg) {
-  const int64_t pb = kThreads / lg;
+// blocks for n particles at pb particles per block and pass, at most 8 per SM
+int grid_groups(kpme_plan_t P, int64_t n, int pb) {
   int64_t want = (n + pb - 1) / pb;
   const int64_t cap = (int64_t)P->sm_count * 8;
   if (want > cap) want = cap;
@@ -1167,11 +1330,20 @@ cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, cons
                                  float4* coords) {
   if (n <= 0) return cudaSuccess;
   const MeshGeom G = geom(P);
-  const int grid = grid_groups(P, n, P->p.order <= 4 ? 4 : 8);
+  constexpr int kWarps = kThreads / 32;
   switch (P->p.order) {
-    case 4: spread_nosort_kernel<4><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq, coords); break;
-    case 6: spread_nosort_kernel<6><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq, coords); break;
-    case 8: spread_nosort_kernel<8><<<grid, kThreads, 0, P->stream>>>(G, n, x, q, Q, P->d_sumq, coords); break;
+    case 4:
+      spread_nosort_kernel<4><<<grid_groups(P, n, kWarps * SpreadPass<4>::PP), kThreads, 0, P->stream>>>(
+          G, n, x, q, Q, P->d_sumq, coords);
+      break;
+    case 6:
+      spread_nosort_kernel<6><<<grid_groups(P, n, kWarps * SpreadPass<6>::PP), kThreads, 0, P->stream>>>(
+          G, n, x, q, Q, P->d_sumq, coords);
+      break;
+    case 8:
+      spread_nosort_kernel<8><<<grid_groups(P, n, kWarps * SpreadPass<8>::PP), kThreads, 0, P->stream>>>(
+          G, n, x, q, Q, P->d_sumq, coords);
+      break;
     default: return cudaErrorInvalidValue;
   }
   return cudaGetLastError();

@@ -116,6 +116,36 @@ def test_spread_boundary_particles(torch):
     np.testing.assert_allclose(Q, spme.spread(x, q, L, K, 4), atol=1e-15)
 
 
+@pytest.mark.parametrize("prec,sort", [("fp32", True), ("fp32", False), ("bf16x10", True)])
+def test_mesh_coordinates_near_cell_boundaries(torch, prec, sort):
+    """The float32 forms take the mesh coordinate in double-float arithmetic and fall back to
+    the float64 rounding sequence within 2^-20 of a cell boundary: positions on the mesh
+    points, one float64 ulp either side, at the box faces, outside the box (one and several
+    periods) and just inside 1e-12 of a boundary spread and gather as the oracle does."""
+    L, K, order = 19.0, 32, 6
+    rng = np.random.default_rng(11)
+    h = L / K
+    cands = [k * h for k in range(-K, 2 * K + 1)]
+    cands += [np.nextafter(v, np.inf) for v in cands] + [np.nextafter(v, -np.inf) for v in cands]
+    cands += [v + 1e-12 for v in cands[:3 * K]] + [0.0, -0.0, L, -L, 2.5 * L, -3.25 * L, 7.0 * L + h]
+    cands = np.array(cands)
+    n = 601
+    x = np.stack([rng.choice(cands, n) for _ in range(3)], axis=1)
+    x[::3] = rng.uniform(-L, 2 * L, size=x[::3].shape)   # and ordinary positions between them
+    q = np.where(np.arange(n) % 2 == 0, 1.0, -1.0)
+    s = wl.System("edges", x, q, L, K, order)
+    plan = _plan(s, prec)
+    if not sort:
+        plan.set_tune(-1, 1, 2)
+    Q = host(plan.spread(dev(torch, x), dev(torch, q)))
+    ref = spme.spread(x, q, L, K, order)
+    assert np.abs(Q - ref).max() <= 2e-6 * np.abs(ref).max()
+    Phi = rng.standard_normal((K, K, K))
+    phi, F = plan.gather(dev(torch, x), dev(torch, q), dev(torch, Phi))
+    phi_r, F_r = spme.gather(x, q, L, K, order, Phi)
+    assert rel(host(phi), phi_r) < 2e-6 and rel(host(F), F_r) < 2e-6
+
+
 def test_skp_build_matches_oracle(torch):
     s = wl.small()
     plan = _plan(s, "fp64")
