@@ -502,6 +502,25 @@ def _measure(args, name, steps, warmup, ctx, headline):
         gbs = nbytes / (ms_k * 1e-3) / 1e9 if ms_k > 0 else None
         part[kn] = {"bytes_per_eval": nbytes, "ms_per_eval": ms_k, "GB/s": gbs, "frac_hbm": (gbs / hbm) if gbs else None}
     part["hbm_peak_gbs"] = hbm
+    if not lag and ("spread" in prof or "gather" in prof):
+        # the bound of the B-spline kernels is the rate of their n^3 float32 updates (atomics)
+        # and stencil reads per particle, not their bytes: measured live, same pattern
+        from paper_2601_18838_gb300._binding import measure_update_rate
+        rates = measure_update_rate(K, s.order, min(s.n, 1 << 20))
+        sorted_path = tune.get("tile") not in (-1, None) or tune.get("autotune") == "off"
+        upd = s.n * s.order ** 3
+        for kn, peak_k, what in (("spread", "shared_atomic" if sorted_path else "global_atomic",
+                                  "float32 atomic adds of the stencils (tile region in shared memory)" if sorted_path
+                                  else "float32 atomic adds of the stencils into the mesh in device memory"),
+                                 ("gather", "read", "stencil reads of the float32 mesh, one thread per particle")):
+            ms_k = part[kn]["ms_per_eval"]
+            if ms_k > 0:
+                ach = upd / (ms_k * 1e-3)
+                part[kn]["roofline"] = {"bound": "atomics" if kn == "spread" else "loads", "achieved": ach,
+                                        "peak": rates[peak_k], "unit": "updates/s" if kn == "spread" else "reads/s",
+                                        "frac": ach / rates[peak_k] if rates[peak_k] else None,
+                                        "work": f"n order^3 = {upd} per evaluation: {what}",
+                                        "peak_source": "kpme_measure_update_rate (same access pattern, live)"}
     part["note"] = ("per-cell Lagrange: spread = counting sort by cell (clear, count, scan, scatter) + one CTA "
                     "per cell writing its Ln^3 node block once (no atomics), gather = one CTA per cell with the "
                     "block in shared memory, one warp per particle"

@@ -342,6 +342,21 @@ typedef struct {
 
 kpme_status_t kpme_get_info(kpme_plan_t plan, kpme_info_t* info);
 
+/* Measurement helper (no counterpart in the paper): the device's float32 atomic-add rate in
+ * the access pattern of B-spline spreading (§2.2, Eq. interpkrons: every particle adds its
+ * order^3 stencil, rows of `order` consecutive points along the last axis, order lanes per
+ * row) for n_particles hashed cells of a K^3 mesh, into (a) a float32 mesh in device memory
+ * (global atomics, as the spreading with no cell sort) and (b) a (15 + order)^3-point
+ * shared-memory region per CTA (shared atomics, as the tile-staged spreading), and (c) the
+ * read rate of the gathering's pattern (one thread per particle reads its order^3 stencil
+ * values of the float32 mesh).  Allocates and frees a K^3 float32 scratch mesh, synchronises
+ * the device, and writes the best of three timed runs of each as updates (reads) per second,
+ * n_particles * order^3 / seconds, to *global_rate, *shared_rate and *read_rate (any may be
+ * NULL).  order: 4, 6 or 8; K >= 16 and a multiple of 4; n_particles >= 1 (else
+ * KPME_ERR_INVALID_ARG). */
+kpme_status_t kpme_measure_update_rate(int K, int order, int64_t n_particles, double* global_rate,
+                                       double* shared_rate, double* read_rate);
+
 const char* kpme_status_string(kpme_status_t status);
 
 /* Text of the last CUDA error seen by this plan ("" if none). */

@@ -25,6 +25,7 @@ EXPORTS = [
     "kpme_batch_create", "kpme_batch_destroy", "kpme_batch_set_stream", "kpme_batch_build_skp",
     "kpme_batch_energy_forces", "kpme_batch_last_error", "kpme_autotune", "kpme_set_tune",
     "kpme_batch_autotune",
+    "kpme_measure_update_rate",
 ]
 
 
@@ -110,6 +111,7 @@ def lib():
         "kpme_autotune": (st, [_vp, _i64, _vp, _vp, C.c_char_p, C.POINTER(Tune)]),
         "kpme_set_tune": (st, [_vp, C.POINTER(Tune)]),
         "kpme_batch_autotune": (st, [_vp, C.POINTER(C.c_int64), _vp, _vp, C.c_char_p, _ip]),
+        "kpme_measure_update_rate": (st, [C.c_int, C.c_int, _i64] + [C.POINTER(C.c_double)] * 3),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -117,6 +119,16 @@ def lib():
         f.argtypes = args
     _LIB = L
     return L
+
+
+def measure_update_rate(K: int, order: int, n_particles: int) -> dict:
+    """kpme_measure_update_rate: float32 atomic adds per second in the spreading's pattern
+    (global mesh and shared-memory tile region) and reads per second in the gathering's."""
+    g, s, r = C.c_double(), C.c_double(), C.c_double()
+    st = lib().kpme_measure_update_rate(int(K), int(order), int(n_particles), C.byref(g), C.byref(s), C.byref(r))
+    if st != 0:
+        raise KpmeError("kpme_measure_update_rate", st)
+    return {"global_atomic": g.value, "shared_atomic": s.value, "read": r.value}
 
 
 def _ptr(t):

@@ -533,27 +533,63 @@ __global__ void tile_count_kernel(MeshGeom G, Tiling tl, int64_t n, const double
   }
 }
 
-// exclusive scan of count[0..nt) into start[0..nt] (one block of 1024 threads)
-__global__ void tile_scan_kernel(const int* __restrict__ count, int nt, int* __restrict__ start) {
-  __shared__ int part[1024];
+// exclusive scan of count[0..nt) into start[0..nt] (one block of 1024 threads).  Thread t
+// takes `per` consecutive counters (int4 loads and stores where nt allows), the block scans the
+// per-thread sums with warp shuffles, and each thread writes its range's prefix sums.
+__global__ void __launch_bounds__(1024) tile_scan_kernel(const int* __restrict__ count, int nt, int* __restrict__ start) {
+  __shared__ int wsum[32];
   const int per = (nt + 1023) / 1024;
   const int b = threadIdx.x * per;
+  const int e = min(b + per, nt);
+  const bool vec = per % 4 == 0 && nt % 4 == 0;   // every range starts and ends on an int4 boundary
   int s = 0;
-  for (int i = 0; i < per && b + i < nt; ++i) s += count[b + i];
-  part[threadIdx.x] = s;
+  if (vec) {
+    for (int i = b; i < e; i += 4) {
+      const int4 v = *reinterpret_cast<const int4*>(count + i);
+      s += v.x + v.y + v.z + v.w;
+    }
+  } else {
+    for (int i = b; i < e; ++i) s += count[i];
+  }
+  // inclusive scan of the thread sums: within each warp, then over the warps' totals
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = s;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += v;
+  }
+  if (lane == 31) wsum[w] = inc;
   __syncthreads();
-  for (int o = 1; o < 1024; o <<= 1) {
-    const int v = threadIdx.x >= o ? part[threadIdx.x - o] : 0;
-    __syncthreads();
-    part[threadIdx.x] += v;
-    __syncthreads();
+  if (w == 0) {
+    int t = wsum[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, t, o);
+      if (lane >= o) t += v;
+    }
+    wsum[lane] = t;
   }
-  int run = threadIdx.x ? part[threadIdx.x - 1] : 0;
-  for (int i = 0; i < per && b + i < nt; ++i) {
-    start[b + i] = run;
-    run += count[b + i];
+  __syncthreads();
+  int run = inc - s + (w ? wsum[w - 1] : 0);   // exclusive prefix of this thread's range
+  if (vec) {
+    for (int i = b; i < e; i += 4) {
+      const int4 v = *reinterpret_cast<const int4*>(count + i);
+      int4 o;
+      o.x = run;
+      o.y = o.x + v.x;
+      o.z = o.y + v.y;
+      o.w = o.z + v.z;
+      run = o.w + v.w;
+      *reinterpret_cast<int4*>(start + i) = o;
+    }
+  } else {
+    for (int i = b; i < e; ++i) {
+      start[i] = run;
+      run += count[i];
+    }
   }
-  if (threadIdx.x == 1023) start[nt] = part[1023];
+  if (threadIdx.x == 1023) start[nt] = wsum[31];
 }
 
 __global__ void tile_scatter_kernel(int64_t n, const int2* __restrict__ tile_slot, const int* __restrict__ start,
@@ -727,7 +763,7 @@ __global__ void __launch_bounds__(kThreads) spread_tile_kernel(Tiling tl, const 
 }
 
 // Tile-staged gathering: the CTA stages its (T + n - 1)^3 region of Phi in shared memory;
-// each particle's lane group sums one j0 plane per lane and reduces with shuffles.
+// each particle's lane group sums one mesh column j2 of its stencil per lane and reduces with shuffles.
 template <int N>
 __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tiling tl, const double* __restrict__ q,
                                                                const int* __restrict__ start,
@@ -779,28 +815,32 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
     share_axes<N>(mw, w, base, mask);
     share_axes<N>(mdw, dw, base, mask);
     float pv = 0.f, g0 = 0.f, g1 = 0.f, g2 = 0.f;
-    if (gl < N) {   // this lane's j0 plane of the stencil
-      const int b0 = r.g[0] - t0 * tl.T + H - gl, b1 = r.g[1] - t1 * tl.T + H, b2 = r.g[2] - t2 * tl.T + H;
-      float s_p = 0.f, s_1 = 0.f, s_2 = 0.f;
+    if (gl < N) {
+      // this lane's mesh column j2 = gl of the stencil: at every (j0, j1) the lanes of the
+      // particle read N consecutive points of one region row (distinct banks); the column's
+      // weight and derivative factor out of the lane's sums
+      const int b0 = r.g[0] - t0 * tl.T + H, b1 = r.g[1] - t1 * tl.T + H, b2 = r.g[2] - t2 * tl.T + H - gl;
+      const float* col = region + b2;
+      float a = 0.f, b = 0.f, c = 0.f;   // sums of w0 w1 v, dw0 w1 v, w0 dw1 v
 #pragma unroll
-      for (int j1 = 0; j1 < N; ++j1) {
-        const float* row = region + (b0 * D + (b1 - j1)) * D + b2;
-        float tv = 0.f, td = 0.f;
+      for (int j0 = 0; j0 < N; ++j0) {
+        const float* plane = col + (b0 - j0) * D * D;
+        float s_p = 0.f, s_1 = 0.f;
 #pragma unroll
-        for (int j2 = 0; j2 < N; ++j2) {
-          const float v = row[-j2];
-          tv = fmaf(w[2][j2], v, tv);
-          td = fmaf(dw[2][j2], v, td);
+        for (int j1 = 0; j1 < N; ++j1) {
+          const float v = plane[(b1 - j1) * D];
+          s_p = fmaf(w[1][j1], v, s_p);
+          s_1 = fmaf(dw[1][j1], v, s_1);
         }
-        s_p = fmaf(w[1][j1], tv, s_p);
-        s_1 = fmaf(dw[1][j1], tv, s_1);
-        s_2 = fmaf(w[1][j1], td, s_2);
+        a = fmaf(w[0][j0], s_p, a);
+        b = fmaf(dw[0][j0], s_p, b);
+        c = fmaf(w[0][j0], s_1, c);
       }
-      const float w0 = pick<N>(w[0], gl), d0 = pick<N>(dw[0], gl);
-      pv = w0 * s_p;
-      g0 = d0 * s_p;
-      g1 = w0 * s_1;
-      g2 = w0 * s_2;
+      const float w2 = pick<N>(w[2], gl), d2 = pick<N>(dw[2], gl);
+      pv = w2 * a;
+      g0 = w2 * b;
+      g1 = w2 * c;
+      g2 = d2 * a;
     }
 #pragma unroll
     for (int o = LG / 2; o > 0; o >>= 1) {
@@ -1348,6 +1388,180 @@ cudaError_t launch_spread_nosort(kpme_plan_t P, int64_t n, const double* x, cons
   }
   return cudaGetLastError();
 }
+
+// ---- atomic-add rate of the spreading access pattern (measurement helper) ----
+// Particle p sits in a hashed cell (g0, g1, g2); lane j2 < n of its group adds to mesh column
+// g2 - j2 of the n^2 rows (g0 - j0, g1 - j1), as spread_nosort_kernel's contribution lanes do
+// (32 / n particles per warp instruction).  The shared variant adds into a 21^3 region per
+// CTA ((16 + n - 1)^3 points) at the cell's offset inside a 16^3 tile, as spread_tile_kernel
+// does.
+namespace {
+
+__device__ __forceinline__ uint32_t rate_hash(uint32_t x) {
+  x ^= x >> 16;
+  x *= 0x7feb352dU;
+  x ^= x >> 15;
+  x *= 0x846ca68bU;
+  x ^= x >> 16;
+  return x;
+}
+
+template <int N, bool SHARED>
+__global__ void __launch_bounds__(kThreads) update_rate_kernel(int K, int64_t n, float* __restrict__ Q,
+                                                               float* __restrict__ sink) {
+  extern __shared__ float reg[];
+  constexpr int D = 16 + N - 1;   // a 16^3 tile and its stencil halo
+  constexpr int PW = 32 / N;
+  if (SHARED) {
+    for (int t = threadIdx.x; t < D * D * D; t += kThreads) reg[t] = 0.0f;
+    __syncthreads();
+  }
+  const int lane = threadIdx.x & 31, pl = lane / N, j2 = lane - pl * N;
+  const int64_t warp = (blockIdx.x * (int64_t)kThreads + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * kThreads) >> 5;
+  if (pl < PW) {
+    for (int64_t p = warp * PW + pl; p < n; p += nw * PW) {
+      const uint32_t h = rate_hash((uint32_t)p * 2654435761U + 12345U);
+      if (SHARED) {
+        const int b0 = N - 1 + (int)(h & 15u), b1 = N - 1 + (int)((h >> 4) & 15u), b2 = N - 1 + (int)((h >> 8) & 15u);
+        float* col = reg + b2 - j2;
+#pragma unroll
+        for (int j0 = 0; j0 < N; ++j0)
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1) atomicAdd(col + ((b0 - j0) * D + (b1 - j1)) * D, 1e-3f);
+      } else {
+        const int g0 = (int)(h % (uint32_t)K), g1 = (int)((h >> 10) % (uint32_t)K), g2 = (int)((h >> 20) % (uint32_t)K);
+        int k2 = g2 - j2;
+        k2 += k2 < 0 ? K : 0;
+#pragma unroll
+        for (int j0 = 0; j0 < N; ++j0) {
+          int k0 = g0 - j0;
+          k0 += k0 < 0 ? K : 0;
+#pragma unroll
+          for (int j1 = 0; j1 < N; ++j1) {
+            int k1 = g1 - j1;
+            k1 += k1 < 0 ? K : 0;
+            atomicAdd(Q + ((int64_t)k0 * K + k1) * K + k2, 1e-3f);
+          }
+        }
+      }
+    }
+  }
+  if (SHARED) {
+    __syncthreads();
+    if (threadIdx.x == 0) sink[blockIdx.x] = reg[blockIdx.x % (D * D * D)];
+  }
+}
+
+// The gathering's access pattern: one thread per particle reads its n^3 stencil values from a
+// float32 mesh in device memory (rows of n consecutive points), as gather_kernel<float> does.
+template <int N>
+__global__ void __launch_bounds__(kThreads) stencil_read_kernel(int K, int64_t n, const float* __restrict__ Q,
+                                                                float* __restrict__ sink) {
+  float acc = 0.0f;
+  for (int64_t p = blockIdx.x * (int64_t)kThreads + threadIdx.x; p < n; p += (int64_t)gridDim.x * kThreads) {
+    const uint32_t h = rate_hash((uint32_t)p * 2654435761U + 12345U);
+    const int g0 = (int)(h % (uint32_t)K), g1 = (int)((h >> 10) % (uint32_t)K), g2 = (int)((h >> 20) % (uint32_t)K);
+#pragma unroll
+    for (int j0 = 0; j0 < N; ++j0) {
+      int k0 = g0 - j0;
+      k0 += k0 < 0 ? K : 0;
+#pragma unroll
+      for (int j1 = 0; j1 < N; ++j1) {
+        int k1 = g1 - j1;
+        k1 += k1 < 0 ? K : 0;
+        const float* row = Q + ((int64_t)k0 * K + k1) * K;
+#pragma unroll
+        for (int j2 = 0; j2 < N; ++j2) {
+          int k2 = g2 - j2;
+          k2 += k2 < 0 ? K : 0;
+          acc += row[k2];
+        }
+      }
+    }
+  }
+  if (acc == 1234.5f) sink[0] = acc;   // a data-dependent store keeps the loads
+}
+
+template <int N>
+cudaError_t time_update_rate(int K, int64_t n, int sms, float* Q, float* sink, cudaEvent_t e0, cudaEvent_t e1,
+                             double* g_rate, double* s_rate, double* l_rate) {
+  constexpr int D = 16 + N - 1;
+  const size_t smem = (size_t)D * D * D * sizeof(float);
+  cudaError_t e = cudaFuncSetAttribute(update_rate_kernel<N, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const int per_block = (kThreads / 32) * (32 / N);
+  int64_t want = (n + per_block - 1) / per_block;
+  const int grid_g = (int)std::min<int64_t>(want, (int64_t)sms * 8);
+  const int grid_s = (int)std::min<int64_t>(want, 4096);   // at most one sink entry per block
+  const int grid_l = (int)std::min<int64_t>((n + kThreads - 1) / kThreads, (int64_t)sms * 8);
+  for (int v = 0; v < 3; ++v) {
+    float best = 0.0f;
+    for (int rep = 0; rep < 4; ++rep) {
+      cudaEventRecord(e0);
+      if (v == 0)
+        update_rate_kernel<N, false><<<grid_g, kThreads>>>(K, n, Q, sink);
+      else if (v == 1)
+        update_rate_kernel<N, true><<<grid_s, kThreads, smem>>>(K, n, Q, sink);
+      else
+        stencil_read_kernel<N><<<grid_l, kThreads>>>(K, n, Q, sink);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      cudaEventRecord(e1);
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return e;
+      float ms = 0.0f;
+      if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) return e;
+      if (rep > 0 && (best == 0.0f || ms < best)) best = ms;   // the first run warms up
+    }
+    const double rate = best > 0.0f ? (double)n * N * N * N / (best * 1e-3) : 0.0;
+    *(v == 0 ? g_rate : (v == 1 ? s_rate : l_rate)) = rate;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace kpme
+
+extern "C" kpme_status_t kpme_measure_update_rate(int K, int order, int64_t n_particles, double* global_rate,
+                                                  double* shared_rate, double* read_rate) {
+  if (K < 16 || K % 4 != 0 || n_particles < 1 || (order != 4 && order != 6 && order != 8))
+    return KPME_ERR_INVALID_ARG;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return KPME_ERR_CUDA;
+  float* Q = nullptr;
+  float* sink = nullptr;
+  const size_t mesh = (size_t)K * K * K * sizeof(float);
+  if (cudaMalloc(&Q, mesh) != cudaSuccess) return KPME_ERR_OOM;
+  if (cudaMalloc(&sink, 4096 * sizeof(float)) != cudaSuccess) {
+    cudaFree(Q);
+    return KPME_ERR_OOM;
+  }
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  double g = 0.0, s = 0.0, l = 0.0;
+  cudaError_t e = cudaMemset(Q, 0, mesh);
+  if (e == cudaSuccess) e = cudaEventCreate(&e0);
+  if (e == cudaSuccess) e = cudaEventCreate(&e1);
+  if (e == cudaSuccess) {
+    switch (order) {
+      case 4: e = kpme::time_update_rate<4>(K, n_particles, sms, Q, sink, e0, e1, &g, &s, &l); break;
+      case 6: e = kpme::time_update_rate<6>(K, n_particles, sms, Q, sink, e0, e1, &g, &s, &l); break;
+      default: e = kpme::time_update_rate<8>(K, n_particles, sms, Q, sink, e0, e1, &g, &s, &l); break;
+    }
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  cudaFree(Q);
+  cudaFree(sink);
+  if (e != cudaSuccess) return e == cudaErrorMemoryAllocation ? KPME_ERR_OOM : KPME_ERR_CUDA;
+  if (global_rate) *global_rate = g;
+  if (shared_rate) *shared_rate = s;
+  if (read_rate) *read_rate = l;
+  return KPME_OK;
+}
+
+namespace kpme {
 
 cudaError_t launch_gather_tiled(kpme_plan_t P, int64_t n, const double* q, const float* Phi, double* phi, double* F,
                                 double* energy, bool correct) {
