@@ -748,16 +748,23 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       KPME_CUDA_TRY(P, launch_slice_rows(P, P->d_Y, false, k2, S.r0, K, P->d_Ysl));
     }
     if (!res) KPME_CUDA_TRY(P, cudaMemsetAsync(Phi, 0, (size_t)k3 * sizeof(float), P->stream));   // else cleared above
+    // K = 256 in the reflection basis: a stage-3 half-row is one column of one 128 x 128 tile
+    // of stage 2, which stores each tile's max |value| (plain stores, no clearing) for the
+    // power of two of the rows that read it; stage 3 then needs no pass over its staged rows
+    const bool tile_max = self_max && P->allow_tile_max && P->ozt_pp && P->d_rmZ && K == 256;
+    const int64_t tm_bs = (int64_t)(k2 / 128) * (K / 128);   // tiles per plane
     for (const auto& g : P->groups) {
       if (!self_max)
         KPME_CUDA_TRY(P, cudaMemsetAsync(P->d_rmZ, 0, (size_t)(g.t1 - g.t0) * k2 * sizeof(float), P->stream));
       {
         StepScope sc(P, STEP_SKP2, 1);
         if (res) {
-          OztArgs a{&P->tmF_Y, &P->tm_f2, P->d_rmY, k2, (float*)P->d_Z, k3, g.t0, self_max ? nullptr : P->d_rmZ, k2, M,
-                    K, K, 2, true, &g.stage2_res};
+          OztArgs a{&P->tmF_Y, &P->tm_f2, P->d_rmY, k2, (float*)P->d_Z, k3, g.t0,
+                    tile_max ? P->d_rmZ : (self_max ? nullptr : P->d_rmZ), tile_max ? tm_bs : k2, M, K, K, 2, true,
+                    &g.stage2_res};
           a.fold = P->fold;
           a.self_max = self_max;
+          a.tile_max = tile_max;
           KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
         } else {
           OzArgs a{&P->tm_f2, &P->tm_Y, S.r0, nullptr, false, 0, nullptr, 0, (float*)P->d_Z, k3, P->d_rmZ, k2, M, K,
@@ -767,9 +774,11 @@ kpme_status_t contract(kpme_plan_t P, MeshRef Q, void* Phi) {
       }
       StepScope sc(P, STEP_SKP3, 1);
       if (P->ozt_pp) {
-        OztArgs a{&P->tmF_Z, &P->tm_f1, P->d_rmZ, k2, (float*)Phi, 0, 0, nullptr, 0, M, K, K, 1, false, &g.stage3};
+        OztArgs a{&P->tmF_Z, &P->tm_f1, P->d_rmZ, tile_max ? tm_bs : k2, (float*)Phi, 0, 0, nullptr, 0, M, K, K, 1,
+                  false, &g.stage3};
         a.fold = P->fold;
-        a.self_max = self_max;
+        a.self_max = self_max && !tile_max;
+        a.tile_max = tile_max;
         KPME_CUDA_TRY(P, launch_mp_ozt(P, a));
       } else {
         OzArgs a{&P->tm_f1, nullptr, 0, P->d_Z, false, k3, P->d_rmZ, k2, (float*)Phi, 0, nullptr, 0, M, K, K, 1,
@@ -1088,6 +1097,7 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   }
   P->allow_fused = getenv_flag("KPME_FUSED", true);
   P->allow_fold = getenv_flag("KPME_FOLD", true);
+  P->allow_tile_max = getenv_flag("KPME_TILE_MAX", true);
   P->tile = 0;
   if (lag) {   // the cell sort of the per-cell form: counters and records
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);

@@ -48,6 +48,9 @@ struct OztParams {
   int self_max;         // the converters take each row's power of two from the staged chunks of
                         // the row (every chunk of a unit staged at once, one thread per row);
                         // rowmax_in is not read
+  int tile_max;         // mode 2: rowmax_out receives one max |value| per (plane, item tile);
+                        // A per pair: rowmax_in holds those maxima and a row takes the one of
+                        // the tile its half-row was written in (K = 2 kBM, BN = 128, fold)
   int sb, bstage;       // factor ring: stages and bytes per stage
   int sf;               // float32 staging stages
   int nacc, nat;        // accumulator buffers (2 BN columns each); A slots
@@ -310,12 +313,20 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
       const bool valid = row < prm.M;
       const int p0 = s_start[job], p1 = s_start[job + 1];
       const int nunits = A_RES ? 1 : p1 - p0;
+      // entry of this row in the unit's maxima: the row itself, or (tile_max) the stage-2 tile
+      // holding its half-row: row = n (M / Kr) + g is column n of the rows g Kr + [k0, k0 + kc)
+      int64_t rm_entry = row;
+      if (prm.tile_max) {
+        const int rows_per_col = prm.M / prm.Kr;
+        const int n = row / rows_per_col, g = row - n * rows_per_col;
+        rm_entry = (int64_t)((g * prm.Kr + a_k0(n0)) / kBM) * (prm.Kr / BN) + n / BN;
+      }
       // the row maximum of unit u + 1 is loaded while unit u is cut
-      float rm_next = (valid && !prm.self_max) ? prm.rowmax_in[(int64_t)s_pairs[p0].x * prm.rm_in_bs + row] : 0.0f;
+      float rm_next = (valid && !prm.self_max) ? prm.rowmax_in[(int64_t)s_pairs[p0].x * prm.rm_in_bs + rm_entry] : 0.0f;
       for (int u = 0; u < nunits && ok; ++u) {
         float rm = rm_next;
         if (u + 1 < nunits && !prm.self_max)
-          rm_next = valid ? prm.rowmax_in[(int64_t)s_pairs[p0 + u + 1].x * prm.rm_in_bs + row] : 0.0f;
+          rm_next = valid ? prm.rowmax_in[(int64_t)s_pairs[p0 + u + 1].x * prm.rm_in_bs + rm_entry] : 0.0f;
         if (prm.self_max) {
           // every chunk of this unit is staged at once (kchunks <= sf): the maximum of the
           // thread's row over the unit's k range, read from the staging buffers, which stay
@@ -483,6 +494,21 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
           for (int c = 0; c < BN; ++c) o[(int64_t)c * prm.M] = acc[c];
         }
         if (prm.rowmax_out == nullptr) continue;
+        if (prm.tile_max) {
+          // one max |value| of this pair's 128 x BN tile (a plain store: each tile is written
+          // by one pair), for the power of two of the next stage's rows that read it
+          float tm = 0.0f;
+#pragma unroll
+          for (int c = 0; c < BN; ++c) tm = fmaxf(tm, fabsf(acc[c]));
+          const unsigned int wm = __reduce_max_sync(0xffffffffu, live ? __float_as_uint(tm) : 0u);
+          if (lane == 0) red[wq] = wm;
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          if (wq == 0 && lane == 0 && live)
+            prm.rowmax_out[(int64_t)plane * prm.rm_out_bs + (int64_t)(m0 / kBM) * n_tiles + n0 / BN] =
+                __uint_as_float(max(max(red[0], red[1]), max(red[2], red[3])));
+          asm volatile("bar.sync 1, 128;" ::: "memory");
+          continue;
+        }
         // the consuming row (n, row / K) spans K consecutive rows of column n (K % 32 == 0)
         const int K = prm.Kr;
         const int64_t rows_next = prm.M / K;
@@ -622,6 +648,9 @@ cudaError_t launch_mp_ozt(kpme_plan_t P, const OztArgs& a) {
   prm.kc = kc;
   prm.fold = a.fold ? 1 : 0;
   prm.self_max = a.self_max ? 1 : 0;
+  prm.tile_max = a.tile_max ? 1 : 0;
+  if (a.tile_max && !(bn == 128 && a.fold && a.Kr == 2 * kBM && (a.a_res ? a.rowmax_out : a.rowmax_in)))
+    return cudaErrorInvalidValue;
   prm.kchunks = (kc + kChunk - 1) / kChunk;
   prm.sb = c.sb;
   prm.bstage = kSlices * bn * 128;

@@ -163,6 +163,7 @@ struct kpme_plan_s {
   bool fold = false;               // error-free split on the reflection basis of every axis
                                    // (K % 128 == 0): block-diagonal factors, K/2 contraction
   bool allow_fold = true;          // KPME_FOLD=0 keeps the dense factors
+  bool allow_tile_max = true;      // KPME_TILE_MAX=0: stage 3 rows take their own row maxima
   float* d_Qfold = nullptr;        // the charge mesh in the reflection basis (float32)
   // the virial's rank-one mesh operator on the tensor cores (reflection basis, N = 128 items):
   // digits of its circulant in the basis, its tensor map and the three one-pair job lists
@@ -326,6 +327,8 @@ struct OztArgs {
                              // output column's half (A columns [K/2, K) for columns n >= K/2)
   bool self_max = false;     // the kernel takes the rows' powers of two from the staged rows
                              // (rowmax_in unused; needs BN = 128 and the unit's chunks staged)
+  bool tile_max = false;     // mode 2: rowmax_out gets one max |value| per (plane, 128 x 128
+                             // tile); A per pair: rowmax_in holds them (K = 256 folded, BN = 128)
 };
 struct OzfArgs {
   const float* Y;            // float32 Y (r0 planes x K^2 rows x K), device
