@@ -3,13 +3,15 @@
 // The knobs are the ones whose best value depends on the workload rather than on the
 // mathematics (every setting gives the same result up to summation order):
 //   tile   - edge T of the cell-sort tiles of spreading and gathering (T^3 cells per CTA),
-//            or -1: no cell sort (float64 atomics on the mesh, untiled gathering);
+//            or -1: no cell sort (float32 atomics on the mesh, untiled gathering);
 //   fused  - stages 2 and 3 of the SKP fused on the SM (K = 32, 64) or run separately;
 //   split  - split-K multiplier of the term ranges (x split / 2 of the cost-model choice);
 //            for the fused stages, the grid of the static schedule (x split / 2 of the SMs).
 // kpme_autotune times kpme_energy_forces (graph replay, CUDA events on the plan's stream,
-// after warm-ups) by coordinate descent over the knobs and keeps the fastest; an optional
-// text cache (one line per problem key) stores the choice for later plans.
+// after warm-ups) by coordinate descent over the knobs and keeps the fastest; the tile knob,
+// which changes only the spreading and gathering steps, is judged on those steps' own event
+// times (a few percent of a large evaluation, below the noise of whole evaluations).  An
+// optional text cache (one line per problem key) stores the choice for later plans.
 #include "kpme_internal.cuh"
 
 #include <algorithm>
@@ -78,6 +80,25 @@ kpme_status_t time_config(kpme_plan_t P, int64_t n, const double* x, const doubl
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
+  return st;
+}
+
+// Milliseconds of the spreading and gathering steps of one evaluation: the plan's step events
+// (eager evaluations), ten evaluations after two warm-ups.
+kpme_status_t time_particles(kpme_plan_t P, int64_t n, const double* x, const double* q, const Buffers& b,
+                             double* ms) {
+  double* W = kpme::lagrange(P) ? nullptr : b.W;
+  double steps[kpme::NUM_STEPS] = {};
+  int n_out = 0;
+  P->profiling = true;
+  kpme_status_t st = KPME_OK;
+  for (int i = 0; i < 2 && st == KPME_OK; ++i) st = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, W);
+  if (st == KPME_OK) st = kpme_get_profile(P, steps, nullptr, kpme::NUM_STEPS, &n_out, 1);
+  constexpr int kReps = 10;
+  for (int i = 0; i < kReps && st == KPME_OK; ++i) st = kpme_energy_forces(P, n, x, q, b.E, b.F, b.dq, W);
+  if (st == KPME_OK) st = kpme_get_profile(P, steps, nullptr, kpme::NUM_STEPS, &n_out, 1);
+  P->profiling = false;
+  *ms = (steps[kpme::STEP_SPREAD] + steps[kpme::STEP_GATHER]) / kReps;
   return st;
 }
 
@@ -166,12 +187,26 @@ kpme_status_t kpme_autotune(kpme_plan_t P, int64_t n, const double* x, const dou
   };
   // knob 1: fused stages 2-3 where the kernel exists
   if (P->ozt_res && P->tc_bn == P->p.K && (P->p.K == 32 || P->p.K == 64)) trial(Config{best.tile, 1 - best.fused, best.split});
-  // knob 2: spreading tile edge, or no cell sort (plans that can tile)
-  if (P->tile > 0) {
+  // knob 2: spreading tile edge, or no cell sort (plans that can tile), on the particle steps
+  if (P->tile > 0 && st == KPME_OK) {
+    double part_ms = 0.0;
+    st = time_particles(P, n, x, q, b, &part_ms);
     const int base = best.tile;
+    auto trial_p = [&](Config c) {
+      if (st != KPME_OK) return;
+      double ms = 0.0;
+      if ((st = apply_config(P, c)) != KPME_OK) return;
+      if ((st = time_particles(P, n, x, q, b, &ms)) != KPME_OK) return;
+      if (ms < 0.99 * part_ms) {
+        best = c;
+        part_ms = ms;
+      }
+    };
     for (int T : {4, 8, 16, 32})
-      if (T != base && kpme::tile_ok(P->p.K, P->p.order, T)) trial(Config{T, best.fused, best.split});
-    if (base != -1) trial(Config{-1, best.fused, best.split});
+      if (T != base && kpme::tile_ok(P->p.K, P->p.order, T)) trial_p(Config{T, best.fused, best.split});
+    if (base != -1) trial_p(Config{-1, best.fused, best.split});
+    // the evaluation time of the choice, against which the split knob is judged
+    if (st == KPME_OK && (st = apply_config(P, best)) == KPME_OK) st = time_config(P, n, x, q, b, &best_ms);
   }
   // knob 3: split-K multiplier
   const int base_split = best.split;
