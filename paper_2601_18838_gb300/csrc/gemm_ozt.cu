@@ -372,23 +372,6 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
             ok = false;
             break;
           }
-          float v[kHalves][32];
-          const uint8_t* stg = ring_f + s * kFStage;
-#pragma unroll
-          for (int hh = 0; hh < kHalves; ++hh) {
-            const int h = h_first + hh;
-            const uint8_t* rowp = stg + h * kFBox + r * 128;
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 x = *reinterpret_cast<const float4*>(rowp + ((j ^ (r & 7)) << 4));
-              v[hh][4 * j] = x.x;
-              v[hh][4 * j + 1] = x.y;
-              v[hh][4 * j + 2] = x.z;
-              v[hh][4 * j + 3] = x.w;
-            }
-          }
-          mbar_arrive(&empty_f[s]);
-          ++jf;
           uint32_t col;
           if constexpr (A_RES) {
             col = col_unit + (uint32_t)(c * kChunkCols);
@@ -403,13 +386,28 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
             fence_after();
             col = (uint32_t)(prm.a_col0 + slot * prm.at_cols);
           }
-#pragma unroll
+          // the thread's 32-wide k halves one at a time, in a loop that is not unrolled: the
+          // unrolled cut of a whole chunk made the converters' code so long that instruction
+          // fetch stalled the warps sharing their SM sub-partitions, the MMA issuer among them
+          // (stage 3 of the 10^6-charge box: 6.44 -> 5.23 ms)
+          const uint8_t* stg = ring_f + s * kFStage;
+#pragma unroll 1
           for (int hh = 0; hh < kHalves; ++hh) {
             const int h = h_first + hh;
             if (c * kChunk + 32 * h >= prm.kc) continue;   // warp-uniform: k half past the end
+            float v[32];
+            const uint8_t* rowp = stg + h * kFBox + r * 128;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+              const float4 x = *reinterpret_cast<const float4*>(rowp + ((j ^ (r & 7)) << 4));
+              v[4 * j] = x.x;
+              v[4 * j + 1] = x.y;
+              v[4 * j + 2] = x.z;
+              v[4 * j + 3] = x.w;
+            }
             uint4 o[4][kSlices];
 #pragma unroll
-            for (int g = 0; g < 4; ++g) slice8(v[hh] + 8 * g, e, o[g]);
+            for (int g = 0; g < 4; ++g) slice8(v + 8 * g, e, o[g]);
 #pragma unroll
             for (int sl = 0; sl < kSlices; ++sl) {
               uint32_t words[16];
@@ -423,6 +421,8 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
               tmem_st16(lane_base + col + (uint32_t)(sl * (kChunk / 2) + 16 * h), words);
             }
           }
+          mbar_arrive(&empty_f[s]);
+          ++jf;
           if constexpr (!A_RES) {
             tmem_wait_st();
             fence_before();

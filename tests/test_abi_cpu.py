@@ -56,6 +56,13 @@ def test_plan_rejects_invalid_parameters_without_gpu(L, field, value):
     assert not h.value
 
 
+@pytest.mark.parametrize("K,order,n", [(15, 6, 1000), (34, 6, 1000), (32, 5, 1000), (32, 6, 0)])
+def test_update_rate_rejects_invalid_arguments_without_gpu(L, K, order, n):
+    g = C.c_double(-1.0)
+    assert L.kpme_measure_update_rate(K, order, n, C.byref(g), None, None) == 1   # KPME_ERR_INVALID_ARG
+    assert g.value == -1.0
+
+
 def test_null_plan_is_rejected(L):
     assert L.kpme_energy_forces(None, 0, None, None, None, None, None, None) == 1
     assert L.kpme_set_profiling(None, 1) == 1

@@ -70,3 +70,15 @@ def test_batch_autotune_per_class(torch):
     np.testing.assert_allclose(host(after["energy"]), host(before["energy"]), rtol=1e-6)
     assert rel(host(after["forces"]), host(before["forces"])) < 1e-5
     batch.close()
+
+
+@pytest.mark.parametrize("order", [4, 6, 8])
+def test_measured_update_rates_are_finite_and_positive(torch, order):
+    """kpme_measure_update_rate (the ceilings the bench reports the particle kernels against):
+    three positive finite rates, and the device still usable afterwards."""
+    from paper_2601_18838_gb300._binding import measure_update_rate
+    r = measure_update_rate(32, order, 20000)
+    for k in ("global_atomic", "shared_atomic", "read"):
+        assert np.isfinite(r[k]) and r[k] > 1e9, (k, r[k])
+    x = torch.ones(4, device="cuda")
+    assert float((x * 2).sum().item()) == 8.0
