@@ -386,39 +386,27 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
             fence_after();
             col = (uint32_t)(prm.a_col0 + slot * prm.at_cols);
           }
-          // the thread's 32-wide k halves one at a time, in a loop that is not unrolled: the
-          // unrolled cut of a whole chunk made the converters' code so long that instruction
-          // fetch stalled the warps sharing their SM sub-partitions, the MMA issuer among them
-          // (stage 3 of the 10^6-charge box: 6.44 -> 5.23 ms)
+          // the thread's 32-wide k halves and their groups of 8 values one at a time, in loops
+          // that are not unrolled: the unrolled cut of a whole chunk made the converters' code so
+          // long that instruction fetch stalled the warps sharing their SM sub-partitions, the
+          // MMA issuer among them (stage 3 of the 10^6-charge box: 6.44 -> 5.23 ms with the
+          // halves rolled, -> 5.08 ms with the groups too)
           const uint8_t* stg = ring_f + s * kFStage;
 #pragma unroll 1
           for (int hh = 0; hh < kHalves; ++hh) {
             const int h = h_first + hh;
             if (c * kChunk + 32 * h >= prm.kc) continue;   // warp-uniform: k half past the end
-            float v[32];
             const uint8_t* rowp = stg + h * kFBox + r * 128;
+#pragma unroll 1
+            for (int g = 0; g < 4; ++g) {
+              const float4 x0 = *reinterpret_cast<const float4*>(rowp + (((2 * g) ^ (r & 7)) << 4));
+              const float4 x1 = *reinterpret_cast<const float4*>(rowp + (((2 * g + 1) ^ (r & 7)) << 4));
+              const float v[8] = {x0.x, x0.y, x0.z, x0.w, x1.x, x1.y, x1.z, x1.w};
+              uint4 o[kSlices];
+              slice8(v, e, o);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-              const float4 x = *reinterpret_cast<const float4*>(rowp + ((j ^ (r & 7)) << 4));
-              v[4 * j] = x.x;
-              v[4 * j + 1] = x.y;
-              v[4 * j + 2] = x.z;
-              v[4 * j + 3] = x.w;
-            }
-            uint4 o[4][kSlices];
-#pragma unroll
-            for (int g = 0; g < 4; ++g) slice8(v + 8 * g, e, o[g]);
-#pragma unroll
-            for (int sl = 0; sl < kSlices; ++sl) {
-              uint32_t words[16];
-#pragma unroll
-              for (int g = 0; g < 4; ++g) {
-                words[4 * g] = o[g][sl].x;
-                words[4 * g + 1] = o[g][sl].y;
-                words[4 * g + 2] = o[g][sl].z;
-                words[4 * g + 3] = o[g][sl].w;
-              }
-              tmem_st16(lane_base + col + (uint32_t)(sl * (kChunk / 2) + 16 * h), words);
+              for (int sl = 0; sl < kSlices; ++sl)
+                tmem_st4(lane_base + col + (uint32_t)(sl * (kChunk / 2) + 16 * h + 4 * g), o[sl]);
             }
           }
           mbar_arrive(&empty_f[s]);
