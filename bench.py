@@ -339,11 +339,72 @@ def run_batched(args):
     if pg:
         pg.barrier()
     clocks = clk.stop()
+    # end to end through the public API: the step's positions and charges from pinned host
+    # memory, the batch, then forces, potentials, energies and virials back to pinned host memory
+    e_ms = 0.0
+    h2d = d2h = 0
+    if mine:
+        xh, qh = x.cpu().pin_memory(), q.cpu().pin_memory()
+        xd, qd = torch.empty_like(x), torch.empty_like(q)
+        n_tot = int(offsets[-1])
+        Fh = torch.empty((n_tot, 3), dtype=torch.float64).pin_memory()
+        Ph = torch.empty(n_tot, dtype=torch.float64).pin_memory()
+        Eh = torch.empty((2, len(mine)), dtype=torch.float64).pin_memory()
+        h2d, d2h = n_tot * 32, n_tot * 32 + 16 * len(mine)
+
+        def e2e_step():
+            xd.copy_(xh, non_blocking=True)
+            qd.copy_(qh, non_blocking=True)
+            o = batch.energy_forces(xd, qd, offsets, virial=True)
+            Fh.copy_(o["forces"], non_blocking=True)
+            Ph.copy_(o["dEdq"], non_blocking=True)
+            Eh[0].copy_(o["energy"], non_blocking=True)
+            Eh[1].copy_(o["virial"], non_blocking=True)
+
+        for _ in range(3):
+            e2e_step()
+        torch.cuda.synchronize()
+        for _ in range(args.steps):
+            flush.zero_()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            e2e_step()
+            b.record(stream)
+            b.synchronize()
+            e_ms += a.elapsed_time(b)
     if pg:
-        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        t = torch.tensor([ms, e_ms], dtype=torch.float64, device=dev)
         pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        ms = t.item()
+        ms, e_ms = t[0].item(), t[1].item()
     n_sys = len(systems)
+    # useful flops: 6 R K^4 per system (its Kronecker terms' three dense mode products), over
+    # the whole batch evaluation (particle work and reductions included: the batch is one
+    # graph launch, so its kernels are not timed apart)
+    useful = sum(6.0 * r * float(s.K) ** 4 for r, s in zip(ranks, mine))
+    peak, peak_note, _ = _tensor_peak(args.precision)
+    roof = None
+    if mine and ms > 0:
+        ach = useful / (ms / args.steps * 1e-3) / 1e12
+        roof = {"bound": "tensor", "kernel": "the whole batch evaluation (one graph launch: every system's "
+                "spreading, SKP mode products, gathering and reductions)", "achieved": ach, "peak": peak,
+                "unit": "TFLOP/s", "frac": ach / peak, "traffic": None, "peak_source": peak_note,
+                "work": "useful flops sum over this rank's systems of 6 R K^4 per evaluation",
+                "flops_per_step": useful}
+    cb = None
+    if rank == 0 and mine and not args.no_cpu_baseline:
+        # the float64 oracle on a sample of this rank's systems (four spread over its list),
+        # one full evaluation each; value in system-evaluations per second
+        sample = mine[::max(1, len(mine) // 4)][:4]
+        t_eval = 0.0
+        for s in sample:
+            _, ev, _ = _oracle_eval(s)
+            a = time.perf_counter()
+            ev()
+            t_eval += time.perf_counter() - a
+        cb = {"value": len(sample) / t_eval, "unit": "system-evals/s", "cores": os.cpu_count(), "kind": "oracle",
+              "sample": f"one full float64 oracle evaluation each of {len(sample)} of the {len(mine)} systems "
+                        f"(K = {', '.join(str(s.K) for s in sample)}; n = {', '.join(str(s.n) for s in sample)}), "
+                        f"mean time per system (SKP builds not timed)"}
     line = {"metric": METRIC, "value": n_sys * args.steps / (ms * 1e-3), "unit": "system-evals/s", "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": DTYPE.get(args.precision, args.precision),
@@ -354,7 +415,10 @@ def run_batched(args):
                        "parallelism": f"systems sharded over {ws} ranks (longest processing time first)"
                        if ws > 1 else "single GPU",
                        "l2": "flushed between steps (256 MB write outside the timed events)"},
-            "clocks": clocks}
+            "roofline": roof,
+            "e2e": {"value": n_sys * args.steps / (e_ms * 1e-3), "unit": "system-evals/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": d2h} if e_ms > 0 else None,
+            "cpu_baseline": cb, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line), flush=True)
     if mine:
