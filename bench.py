@@ -50,12 +50,12 @@ SKP_TRAFFIC = {
     # 19,324,160 B (reads; 0 B written: Y and Phi stay in L2), 2 launches per evaluation
     ("water", "bf16x10"): {"digest": "15ac4d609920d908", "launches": 2,
                            "bytes_per_launch": (1515008 + 19324160) / 2},
-    # profiles/launches_large_k256_bf16x10.md: one evaluation's stage 1 (93,000,192 B read +
-    # 879,249,408 B written), stage 2 (1,059,233,280 + 11,178,970,368), stage 3 (11,837,063,168
-    # + 273,167,616) and the unfold of Phi (67,152,640 + 4,255,488): 4 launches
-    ("large", "bf16x10"): {"digest": "04d1af663883165d", "launches": 4,
-                           "bytes_per_launch": (93000192 + 879249408 + 1059233280 + 11178970368 + 11837063168
-                                                + 273167616 + 67152640 + 4255488) / 4},
+    # profiles/launches_large_k256_bf16x10.md: one evaluation's stage 1 (93,060,608 B read +
+    # 880,000,000 B written), stage 2 (1,066,170,880 + 11,189,232,384), stage 3 (11,840,929,792
+    # + 277,398,784) and the unfold of Phi (67,126,272 + 4,329,472): 4 launches
+    ("large", "bf16x10"): {"digest": "21bc207300527025", "launches": 4,
+                           "bytes_per_launch": (93060608 + 880000000 + 1066170880 + 11189232384 + 11840929792
+                                                + 277398784 + 67126272 + 4329472) / 4},
 }
 SKP_SOURCES = ("gemm_ozf.cu", "gemm_ozt.cu", "tc_common.cuh")
 
@@ -662,10 +662,10 @@ SKP_TENSOR_ACTIVE = {
     # profiles/mp_ozf_kernel_water_k64_bf16x10.md
     ("water", "bf16x10"): {"digest": "15ac4d609920d908", "pct": {"mp_ozf_kernel<64>": 32.4}},
     # profiles/mp_ozt_kernel_large_k256_bf16x10.md (16-term groups of the same kernels; mean of
-    # the captured launches: stage 1 59.7, stage 2 60.7 / 54.9, stage 3 58.9 / 59.0)
-    ("large", "bf16x10"): {"digest": "04d1af663883165d",
-                           "pct": {"mp_ozt_kernel<128, 4, 1> (stages 1, 2)": 58.4,
-                                   "mp_ozt_kernel<128, 4, 0> (stage 3)": 59.0}},
+    # the captured launches: stage 1 59.7, stage 2 60.7 / 55.1, stage 3 59.1 / 59.2)
+    ("large", "bf16x10"): {"digest": "21bc207300527025",
+                           "pct": {"mp_ozt_kernel<128, 4, 1> (stages 1, 2)": 58.5,
+                                   "mp_ozt_kernel<128, 4, 0> (stage 3)": 59.1}},
 }
 
 

@@ -355,7 +355,7 @@ kpme_status_t install_skp(kpme_plan_t P) {
   kpme_status_t st;
   // error-free split on circulant factors with K/2 a multiple of the 64-wide k chunk: the
   // factors in the reflection basis (two K/2 x K/2 blocks each), half the digit products
-  P->fold = pi.oz && P->allow_fold && !S.dense && K % 128 == 0 && ozt_supported(K, 64, true, true);
+  P->fold = pi.oz && P->allow_fold && P->ozt_mode > 0 && !S.dense && K % 128 == 0 && ozt_supported(K, 64, true, true);
   const int kcols = P->fold ? K / 2 : K;   // stored columns of a factor row
 
   // factors
@@ -407,8 +407,12 @@ kpme_status_t install_skp(kpme_plan_t P) {
   if (P->fold && K / 2 == 128 && getenv_flag("KPME_BN128", true) && ozt_supported(K, 128, true, true) &&
       ozt_supported(K, 128, false, true))
     P->tc_bn = 128;
-  P->ozt_res = pi.oz && ozt_supported(K, P->tc_bn, true, P->fold);
-  P->ozt_pp = pi.oz && ozt_supported(K, P->tc_bn, false, P->fold);
+  // the tensor-memory-A kernel where K % 32 == 0; at other K % 16 == 0 (e.g. 48) it is correct
+  // but the shared-memory-A kernel stays the default: a K = 48 system alone ran 3-5% faster on
+  // it, the 64-system batch (26 systems at K = 48) 3% slower (5.72 against 5.56 ms)
+  const bool ozt_k = P->ozt_mode >= 2 || (P->ozt_mode == 1 && K % 32 == 0);
+  P->ozt_res = pi.oz && ozt_k && ozt_supported(K, P->tc_bn, true, P->fold);
+  P->ozt_pp = pi.oz && ozt_k && ozt_supported(K, P->tc_bn, false, P->fold);
   if (P->fold && !(P->ozt_res && P->ozt_pp)) return KPME_ERR_UNSUPPORTED;   // excluded above
   P->ozf = P->ozt_res && ozf_supported(K) && P->tc_bn == K && P->allow_fused;
   if (pi.oz) {
@@ -1098,6 +1102,10 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
   P->allow_fused = getenv_flag("KPME_FUSED", true);
   P->allow_fold = getenv_flag("KPME_FOLD", true);
   P->allow_tile_max = getenv_flag("KPME_TILE_MAX", true);
+  {
+    const char* e = getenv("KPME_OZT");
+    P->ozt_mode = e ? atoi(e) : 1;
+  }
   P->tile = 0;
   if (lag) {   // the cell sort of the per-cell form: counters and records
     const size_t nmax = (size_t)std::max<int64_t>(1, p.max_n);

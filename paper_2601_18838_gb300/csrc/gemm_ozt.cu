@@ -1,4 +1,4 @@
-// Error-free split mode products with the A operand in tensor memory (KPME_BF16X10, K % 32 == 0).
+// Error-free split mode products with the A operand in tensor memory (KPME_BF16X10, K % 16 == 0, K >= 32).
 //
 // Same contraction and arithmetic as gemm_oz.cu (each operand row cut into four fixed-point
 // bf16 digits relative to a common power of two, ten digit products per multiply, the leading
@@ -497,12 +497,40 @@ __global__ void __launch_bounds__(ozt_threads<NCONV>(), 1)
           asm volatile("bar.sync 1, 128;" ::: "memory");
           continue;
         }
-        // the consuming row (n, row / K) spans K consecutive rows of column n (K % 32 == 0)
+        // the consuming row (n, row / K) spans K consecutive rows of column n
         const int K = prm.Kr;
         const int64_t rows_next = prm.M / K;
         unsigned int* dst = reinterpret_cast<unsigned int*>(prm.rowmax_out + (int64_t)plane * prm.rm_out_bs) +
                             (int64_t)n0 * rows_next;
         constexpr int kJ = (BN + 31) / 32;
+        if (K % 32 != 0) {
+          // (K % 32 != 0, K > 32) a warp's 32 rows reach at most two consuming rows g_w and
+          // g_w + 1: the warp's maximum of each part, one atomic per column and part (the same
+          // branch for every epilogue thread: no named barrier here)
+          const int gw = (m0 + 32 * wq) / K;
+          const bool upper = row / K != gw;
+          unsigned int lo[kJ], hi[kJ];
+#pragma unroll
+          for (int j = 0; j < kJ; ++j) lo[j] = hi[j] = 0u;
+#pragma unroll
+          for (int c = 0; c < BN; ++c) {
+            const unsigned int b = live ? __float_as_uint(fabsf(acc[c])) : 0u;
+            const unsigned int ml = __reduce_max_sync(0xffffffffu, upper ? 0u : b);
+            const unsigned int mh = __reduce_max_sync(0xffffffffu, upper ? b : 0u);
+            if ((c & 31) == lane) {
+              lo[c >> 5] = ml;
+              hi[c >> 5] = mh;
+            }
+          }
+#pragma unroll
+          for (int j = 0; j < kJ; ++j) {
+            const int c = 32 * j + lane;
+            if (c >= BN) continue;
+            if (lo[j] != 0u) atomicMax(dst + (int64_t)c * rows_next + gw, lo[j]);
+            if (hi[j] != 0u) atomicMax(dst + (int64_t)c * rows_next + gw + 1, hi[j]);
+          }
+          continue;
+        }
         unsigned int mx[kJ];
 #pragma unroll
         for (int j = 0; j < kJ; ++j) mx[j] = 0u;
@@ -614,7 +642,10 @@ cudaError_t launch_bn(const OztArgs& a, cudaStream_t st, const OztParams& prm, d
 }  // namespace
 
 bool ozt_supported(int K, int bn, bool a_res, bool fold) {
-  if (K % 32 != 0 || (bn != 32 && bn != 48 && bn != 64 && bn != 128) || K % bn != 0) return false;
+  // K % 16: whole 16-wide MMA k steps (the float32 boxes past K read zeros); K > 32 when K is
+  // not a multiple of 32: a warp's rows then reach at most two rows of the next stage
+  if (K % 16 != 0 || (K % 32 != 0 && K < 48) || (bn != 32 && bn != 48 && bn != 64 && bn != 128) || K % bn != 0)
+    return false;
   if (fold && (K % 128 != 0 || (K / 2) % bn != 0)) return false;
   const OztConfig c = ozt_config(bn, fold ? K / 2 : K, a_res);
   return c.nat >= 1 && c.nacc >= (bn == 128 ? 1 : 2) && c.a_col0 + c.nat * c.at_cols <= 512 && c.sb >= 2 &&

@@ -164,6 +164,8 @@ struct kpme_plan_s {
                                    // (K % 128 == 0): block-diagonal factors, K/2 contraction
   bool allow_fold = true;          // KPME_FOLD=0 keeps the dense factors
   bool allow_tile_max = true;      // KPME_TILE_MAX=0: stage 3 rows take their own row maxima
+  int ozt_mode = 1;                // KPME_OZT: 0 the shared-memory-A kernel for every stage, 1 the
+                                   // tensor-memory-A kernel where K % 32 == 0, 2 also K % 16 == 0
   float* d_Qfold = nullptr;        // the charge mesh in the reflection basis (float32)
   // the virial's rank-one mesh operator on the tensor cores (reflection basis, N = 128 items):
   // digits of its circulant in the basis, its tensor map and the three one-pair job lists

@@ -247,21 +247,24 @@ def test_energy_forces_water_box(torch, water_ref, prec):
     assert e_phi < tp and e_f < tf
 
 
-@pytest.mark.parametrize("K,order,n,L,fused,fold", [
-    (32, 4, 1001, 18.0, "1", "1"),     # fused stages 2-3, BN = 32 (four k3' per tile)
-    (32, 4, 1001, 18.0, "0", "1"),     # tensor-memory A, resident and per pair
-    (48, 4, 2050, 30.0, "1", "1"),     # K % 32 != 0: shared-memory A kernel, row maxima across warps
-    (64, 4, 3001, 40.0, "1", "1"),     # fused, BN = 64
-    (64, 4, 3001, 40.0, "0", "1"),
-    (96, 6, 4003, 70.0, "1", "1"),     # tensor-memory A, two 64-wide chunks (second half empty)
-    (128, 4, 5003, 90.0, "1", "0"),    # tensor-memory A, two full chunks, two column tiles
-    (128, 4, 5003, 90.0, "1", "1"),    # reflection basis: one 64-wide chunk per half
-    (256, 6, 20011, 150.0, "1", "1"),  # reflection basis, two chunks per half, four column tiles
+@pytest.mark.parametrize("K,order,n,L,fused,fold,ozt", [
+    (32, 4, 1001, 18.0, "1", "1", "1"),     # fused stages 2-3, BN = 32 (four k3' per tile)
+    (32, 4, 1001, 18.0, "0", "1", "1"),     # tensor-memory A, resident and per pair
+    (48, 4, 2050, 30.0, "1", "1", "2"),     # K % 32 != 0 on tensor-memory A: one 64-wide chunk holding
+                                            # 48 values; a warp's rows reach two next-stage rows
+    (48, 4, 2050, 30.0, "1", "1", "1"),     # (default) the shared-memory A kernel, row maxima across warps
+    (64, 4, 3001, 40.0, "1", "1", "1"),     # fused, BN = 64
+    (64, 4, 3001, 40.0, "0", "1", "1"),
+    (96, 6, 4003, 70.0, "1", "1", "1"),     # tensor-memory A, two 64-wide chunks (second half empty)
+    (128, 4, 5003, 90.0, "1", "0", "1"),    # tensor-memory A, two full chunks, two column tiles
+    (128, 4, 5003, 90.0, "1", "1", "1"),    # reflection basis: one 64-wide chunk per half
+    (256, 6, 20011, 150.0, "1", "1", "1"),  # reflection basis, two chunks per half, four column tiles
 ])
-def test_error_free_split_sizes(torch, monkeypatch, K, order, n, L, fused, fold):
+def test_error_free_split_sizes(torch, monkeypatch, K, order, n, L, fused, fold, ozt):
     # ragged particle counts and the kernel variants of the error-free split
     monkeypatch.setenv("KPME_FUSED", fused)
     monkeypatch.setenv("KPME_FOLD", fold)
+    monkeypatch.setenv("KPME_OZT", ozt)
     s = wl.random_system(n, L, K, order, seed=K + n)
     o = _oracle_skp(s)
     ref = skp.reciprocal(s.x, s.q, s.box, K, order, s.beta, s.skp_tol, skp=o)
@@ -271,7 +274,7 @@ def test_error_free_split_sizes(torch, monkeypatch, K, order, n, L, fused, fold)
     e_phi, e_f = rel(host(out["dEdq"]), ref["phi"]), rel(host(out["forces"]), ref["F"])
     e_E = abs(host(out["energy"])[0] - ref["E"]) / abs(ref["E"])
     e_W = abs(host(out["virial"])[0] - ref["W"]) / abs(ref["W"])
-    print(f"bf16x10 K={K} fused={fused} fold={fold}: phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e} W {e_W:.2e}")
+    print(f"bf16x10 K={K} fused={fused} fold={fold} ozt={ozt}: phi {e_phi:.2e} F {e_f:.2e} E {e_E:.2e} W {e_W:.2e}")
     assert e_phi < 1e-6 and e_f < 1e-5 and e_E < 1e-6 and e_W < 1e-5
     # the stage entry point on the same mesh: the operator alone, float64 in and out
     Q = spme.spread(s.x, s.q, s.box, K, order)
