@@ -182,6 +182,21 @@ kpme_status_t kpme_build_skp(kpme_plan_t plan, int* rank_out, double* rel_err_ou
 kpme_status_t kpme_set_skp(kpme_plan_t plan, int r0, const int* r1, const double* gen3,
                            const double* gen2, const double* gen1, double c);
 
+/* Store the plan's SKP in a binary file at path, so that another plan of the same mesh and
+ * box can install it without building it (the SKP build is the plan-time cost of §2.1, the
+ * two-level truncated SVD of the influence function of Eq. VtV and Theorem 1).  The file holds
+ * the generator form of kpme_get_skp (sizes, inner counts, the three sets of circulant
+ * generators, the correction constant c) with the plan's K, order, box radius, beta and SKP
+ * tolerance, in the host's byte order.  Synchronises nothing; KPME_ERR_NOT_BUILT before an SKP
+ * exists, KPME_ERR_UNSUPPORTED for the per-cell form (dense factors), KPME_ERR_INVALID_ARG for a
+ * NULL argument or a file that cannot be written. */
+kpme_status_t kpme_save_skp(kpme_plan_t plan, const char* path);
+
+/* Install an SKP stored by kpme_save_skp (as kpme_set_skp does).  The file's K, order, box
+ * radius and beta must equal the plan's (KPME_ERR_INVALID_ARG otherwise, and for a missing,
+ * short or foreign file); kpme_last_error says which.  Synchronises the stream. */
+kpme_status_t kpme_load_skp(kpme_plan_t plan, const char* path);
+
 /* Copy the plan's SKP to HOST arrays.  Any output pointer may be NULL.
  * *r0_out, *R_out: sizes; r1 (capacity r0): inner counts; gen3 (r0 x K),
  * gen2 (R x K), gen1 (R x K): generators as in kpme_set_skp; sigma_outer (r0),

@@ -25,7 +25,7 @@ EXPORTS = [
     "kpme_batch_create", "kpme_batch_destroy", "kpme_batch_set_stream", "kpme_batch_build_skp",
     "kpme_batch_energy_forces", "kpme_batch_last_error", "kpme_autotune", "kpme_set_tune",
     "kpme_batch_autotune",
-    "kpme_measure_update_rate",
+    "kpme_measure_update_rate", "kpme_save_skp", "kpme_load_skp",
 ]
 
 
@@ -112,6 +112,8 @@ def lib():
         "kpme_set_tune": (st, [_vp, C.POINTER(Tune)]),
         "kpme_batch_autotune": (st, [_vp, C.POINTER(C.c_int64), _vp, _vp, C.c_char_p, _ip]),
         "kpme_measure_update_rate": (st, [C.c_int, C.c_int, _i64] + [C.POINTER(C.c_double)] * 3),
+        "kpme_save_skp": (st, [_vp, C.c_char_p]),
+        "kpme_load_skp": (st, [_vp, C.c_char_p]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)
@@ -265,6 +267,14 @@ class Plan:
         t = Tune()
         self._call("kpme_autotune", C.c_int64(n), _ptr(x), _ptr(q), cache.encode() if cache else None, C.byref(t))
         return _tune_dict(t)
+
+    def save_skp(self, path: str):
+        """kpme_save_skp: store this plan's SKP in a file (generator form, with K, order, box, beta)."""
+        self._call("kpme_save_skp", os.fspath(path).encode())
+
+    def load_skp(self, path: str):
+        """kpme_load_skp: install an SKP stored by save_skp on a plan of the same mesh and box."""
+        self._call("kpme_load_skp", os.fspath(path).encode())
 
     def set_tune(self, tile: int, fused: int, split: int):
         t = Tune(tile, fused, split, 0, 0.0)

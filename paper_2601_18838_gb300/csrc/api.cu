@@ -3,6 +3,10 @@
 // float64 reductions), with the mode products ordered as the three reshaped steps of
 // Algorithm 2.
 #include "kpme_internal.cuh"
+
+#include <nvtx3/nvToolsExt.h>
+
+#include <cstdio>
 #include <climits>
 
 #include <algorithm>
@@ -62,6 +66,15 @@ kpme_status_t dalloc(kpme_plan_t P, void** p, size_t bytes) {
     return e == cudaErrorMemoryAllocation ? KPME_ERR_OOM : KPME_ERR_CUDA;
   }
   P->scratch_bytes += (int64_t)bytes;
+  if (P->poison) {
+    // a check that no kernel reads scratch it has not written: every byte starts as 0xFF, a
+    // NaN in float32 and float64 and -1 in integers, so such a read spoils the results
+    e = cudaMemsetAsync(*p, 0xff, bytes, P->stream);
+    if (e != cudaSuccess) {
+      P->last_error = std::string("cudaMemsetAsync: ") + cudaGetErrorString(e);
+      return KPME_ERR_CUDA;
+    }
+  }
   return KPME_OK;
 }
 
@@ -615,18 +628,26 @@ cudaEvent_t take_event(kpme_plan_t P) {
   return e;
 }
 
+// Every step is also an NVTX range (header-only NVTX3: without an attached tool a range costs a
+// branch), so timeline tools show the steps of the eager evaluations and of graph capture.
+const char* const kStepNames[kpme::NUM_STEPS] = {"kpme spread", "kpme split", "kpme SKP stage 1",
+                                                 "kpme SKP stage 2", "kpme SKP stage 3", "kpme gather",
+                                                 "kpme virial"};
+
 struct StepScope {
   kpme_plan_t P;
   int step;
   cudaEvent_t a = nullptr;
   int launches;
   StepScope(kpme_plan_t p, int s, int nl) : P(p), step(s), launches(nl) {
+    nvtxRangePushA(kStepNames[step]);
     if (P->profiling) {
       a = take_event(P);
       cudaEventRecord(a, P->stream);
     }
   }
   ~StepScope() {
+    nvtxRangePop();
     P->launches += launches;
     if (P->profiling) {
       cudaEvent_t b = take_event(P);
@@ -1056,6 +1077,7 @@ kpme_status_t kpme_plan(const kpme_params_t* params, void* stream, kpme_plan_t* 
     const char* g = getenv("KPME_GRAPHS");
     P->use_graphs = !(g && g[0] == '0');
   }
+  P->poison = getenv_flag("KPME_POISON", false);
   auto fail = [&](kpme_status_t s) {
     kpme_destroy(P);
     return s;
@@ -1251,6 +1273,79 @@ kpme_status_t kpme_get_skp(kpme_plan_t P, int* r0_out, int* R_out, int* r1, doub
   if (si) std::copy(S.sig_inner.begin(), S.sig_inner.end(), si);
   if (c_out) *c_out = S.c;
   return KPME_OK;
+}
+
+// SKP file: 8-byte tag, int32 K, order, r0, R, float64 radius, beta, tolerance, c, int32 r1[r0],
+// float64 gen3[r0 K], gen2[R K], gen1[R K] (host byte order)
+static const char kSkpTag[8] = {'K', 'P', 'M', 'E', 'S', 'K', 'P', '1'};
+
+kpme_status_t kpme_save_skp(kpme_plan_t P, const char* path) {
+  if (!plan_ok(P) || !path) return KPME_ERR_INVALID_ARG;
+  const SkpHost& S = P->skp;
+  if (!S.valid) return KPME_ERR_NOT_BUILT;
+  if (S.dense || lagrange(P)) return KPME_ERR_UNSUPPORTED;
+  FILE* f = fopen(path, "wb");
+  if (!f) {
+    P->last_error = std::string("kpme_save_skp: cannot open ") + path;
+    return KPME_ERR_INVALID_ARG;
+  }
+  const int32_t hdr[4] = {P->p.K, P->p.order, S.r0, S.R};
+  const double geo[4] = {P->p.radius, P->p.beta, P->p.skp_tol, S.c};
+  std::vector<int32_t> r1(S.r1.begin(), S.r1.end());
+  bool ok = fwrite(kSkpTag, 1, 8, f) == 8 && fwrite(hdr, sizeof(int32_t), 4, f) == 4 &&
+            fwrite(geo, sizeof(double), 4, f) == 4 && fwrite(r1.data(), sizeof(int32_t), r1.size(), f) == r1.size() &&
+            fwrite(S.gen3.data(), sizeof(double), S.gen3.size(), f) == S.gen3.size() &&
+            fwrite(S.gen2.data(), sizeof(double), S.gen2.size(), f) == S.gen2.size() &&
+            fwrite(S.gen1.data(), sizeof(double), S.gen1.size(), f) == S.gen1.size();
+  ok = (fclose(f) == 0) && ok;
+  if (!ok) {
+    P->last_error = std::string("kpme_save_skp: write failed: ") + path;
+    return KPME_ERR_INVALID_ARG;
+  }
+  return KPME_OK;
+}
+
+kpme_status_t kpme_load_skp(kpme_plan_t P, const char* path) {
+  if (!plan_ok(P) || !path) return KPME_ERR_INVALID_ARG;
+  if (lagrange(P)) return KPME_ERR_UNSUPPORTED;
+  FILE* f = fopen(path, "rb");
+  if (!f) {
+    P->last_error = std::string("kpme_load_skp: cannot open ") + path;
+    return KPME_ERR_INVALID_ARG;
+  }
+  char tag[8];
+  int32_t hdr[4];
+  double geo[4];
+  bool ok = fread(tag, 1, 8, f) == 8 && memcmp(tag, kSkpTag, 8) == 0 && fread(hdr, sizeof(int32_t), 4, f) == 4 &&
+            fread(geo, sizeof(double), 4, f) == 4;
+  const int K = P->p.K;
+  std::string why = ok ? "" : "not an SKP file";
+  if (ok && (hdr[0] != K || hdr[1] != P->p.order)) why = "K or order differs from the plan's";
+  else if (ok && (geo[0] != P->p.radius || geo[1] != P->p.beta)) why = "box radius or beta differs from the plan's";
+  else if (ok && (hdr[2] <= 0 || hdr[3] < hdr[2] || hdr[3] > (1 << 20))) why = "bad sizes";
+  std::vector<int32_t> r1;
+  std::vector<double> g3, g2, g1;
+  if (why.empty()) {
+    r1.resize(hdr[2]);
+    g3.resize((size_t)hdr[2] * K);
+    g2.resize((size_t)hdr[3] * K);
+    g1.resize((size_t)hdr[3] * K);
+    ok = fread(r1.data(), sizeof(int32_t), r1.size(), f) == r1.size() &&
+         fread(g3.data(), sizeof(double), g3.size(), f) == g3.size() &&
+         fread(g2.data(), sizeof(double), g2.size(), f) == g2.size() &&
+         fread(g1.data(), sizeof(double), g1.size(), f) == g1.size();
+    int64_t sum = 0;
+    for (int32_t v : r1) sum += v;
+    if (!ok) why = "file is short";
+    else if (sum != hdr[3]) why = "inner counts do not add up to R";
+  }
+  fclose(f);
+  if (!why.empty()) {
+    P->last_error = std::string("kpme_load_skp: ") + path + ": " + why;
+    return KPME_ERR_INVALID_ARG;
+  }
+  std::vector<int> r1i(r1.begin(), r1.end());
+  return kpme_set_skp(P, hdr[2], r1i.data(), g3.data(), g2.data(), g1.data(), geo[3]);
 }
 
 kpme_status_t kpme_spread(kpme_plan_t P, int64_t n, const double* x, const double* q, double* Q) {

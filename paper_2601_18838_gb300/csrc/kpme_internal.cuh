@@ -164,6 +164,7 @@ struct kpme_plan_s {
                                    // (K % 128 == 0): block-diagonal factors, K/2 contraction
   bool allow_fold = true;          // KPME_FOLD=0 keeps the dense factors
   bool allow_tile_max = true;      // KPME_TILE_MAX=0: stage 3 rows take their own row maxima
+  bool poison = false;             // KPME_POISON=1: every plan allocation starts as 0xFF bytes (NaN)
   int ozt_mode = 1;                // KPME_OZT: 0 the shared-memory-A kernel for every stage, 1 the
                                    // tensor-memory-A kernel where K % 32 == 0, 2 also K % 16 == 0
   float* d_Qfold = nullptr;        // the charge mesh in the reflection basis (float32)

@@ -63,6 +63,11 @@ def test_update_rate_rejects_invalid_arguments_without_gpu(L, K, order, n):
     assert g.value == -1.0
 
 
+def test_skp_file_calls_reject_null_arguments_without_gpu(L):
+    assert L.kpme_save_skp(None, b"/tmp/x.bin") == 1   # KPME_ERR_INVALID_ARG
+    assert L.kpme_load_skp(None, b"/tmp/x.bin") == 1
+
+
 def test_null_plan_is_rejected(L):
     assert L.kpme_energy_forces(None, 0, None, None, None, None, None, None) == 1
     assert L.kpme_set_profiling(None, 1) == 1
