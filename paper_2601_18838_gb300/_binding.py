@@ -11,7 +11,8 @@ import ctypes as C
 import os
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libkpme.so")
+# KPME_LIB=debug loads the checked build (libkpme_debug.so, `build(debug=True)`)
+LIB_PATH = os.path.join(PKG, "libkpme_debug.so" if os.environ.get("KPME_LIB") == "debug" else "libkpme.so")
 
 PRECISIONS = {"fp64": 0, "fp32": 1, "tf32": 2, "tf32x3": 3, "bf16": 4, "bf16x3": 5, "bf16x6": 6, "bf16x10": 7}
 SKP_METHODS = {"svd": 0, "sinc": 1}

@@ -21,6 +21,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libkpme.so")
+LIB_DEBUG = os.path.join(PKG, "libkpme_debug.so")   # the checked build (-DKPME_DEBUG)
 SOURCES = ["api.cu", "particles.cu", "skp_build.cu", "gemm_simt.cu", "gemm_tc.cu", "gemm_oz.cu", "gemm_ozt.cu", "gemm_ozf.cu", "noalloc.cu", "batch.cu", "tune.cu", "virial_tensor.cu", "lagrange_modes.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
@@ -36,39 +37,45 @@ def _cuda_lib_dir(nvcc: str) -> str:
     return os.path.join(os.path.dirname(os.path.dirname(os.path.realpath(nvcc))), "lib64")
 
 
-def _flags(extra_debug: bool = False) -> list[str]:
+def _flags(debug: bool = False) -> list[str]:
     f = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                 "--expt-relaxed-constexpr"]
+    if debug:
+        f += ["-DKPME_DEBUG"]
     if os.environ.get("KPME_PTXAS_VERBOSE"):
         f += ["-Xptxas", "-v"]
     return f
 
 
-def _digest(paths) -> str:
+def _digest(paths, debug: bool = False) -> str:
     h = hashlib.sha256()
     for p in paths:
         with open(p, "rb") as fh:
             h.update(fh.read())
-    h.update(" ".join(_flags()).encode())
+    h.update(" ".join(_flags(debug)).encode())
     return h.hexdigest()
 
 
-def build(verbose: bool = False, force: bool = False) -> str:
+def build(verbose: bool = False, force: bool = False, debug: bool = False) -> str:
+    """Compile and link libkpme.so (or, debug=True, the checked build libkpme_debug.so, whose
+    particle and mesh kernels check their indices; see in_bounds in kpme_internal.cuh)."""
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    bdir = os.path.join(BUILD, "debug") if debug else BUILD
+    lib = LIB_DEBUG if debug else LIB
+    os.makedirs(bdir, exist_ok=True)
     srcs = [os.path.join(CSRC, s) for s in SOURCES]
     headers = sorted(os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh"))
     deps = srcs + headers + [os.path.join(INCLUDE, "kpme.h")]
-    stamp = os.path.join(BUILD, "libkpme.stamp")
-    dig = _digest(deps)
-    if not force and os.path.exists(LIB) and os.path.exists(stamp):
+    stamp = os.path.join(bdir, "libkpme.stamp")
+    dig = _digest(deps, debug)
+    if not force and os.path.exists(lib) and os.path.exists(stamp):
         with open(stamp) as fh:
             if fh.read().strip() == dig:
-                return LIB
+                return lib
 
     def compile_one(src: str) -> str:
-        obj = os.path.join(BUILD, os.path.basename(src).replace(".cu", ".o"))
-        cmd = [nvcc, "-c", src, "-o", obj] + _flags()
+        obj = os.path.join(bdir, os.path.basename(src).replace(".cu", ".o"))
+        cmd = [nvcc, "-c", src, "-o", obj] + _flags(debug)
         if verbose:
             print(" ".join(cmd), flush=True)
         r = subprocess.run(cmd, capture_output=True, text=True)
@@ -81,25 +88,26 @@ def build(verbose: bool = False, force: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=len(srcs)) as ex:
         objs = list(ex.map(compile_one, srcs))
     libdir = _cuda_lib_dir(nvcc)
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [nvcc, "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "shared", "-Xlinker", f"-rpath={libdir}"]
     if verbose:
         print(" ".join(cmd), flush=True)
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
+    os.replace(tmp, lib)
     with open(stamp, "w") as fh:
         fh.write(dig)
-    return LIB
+    return lib
 
 
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("-v", "--verbose", action="store_true")
     ap.add_argument("--force", action="store_true")
+    ap.add_argument("--debug", action="store_true", help="the checked build, libkpme_debug.so")
     a = ap.parse_args(argv)
-    print(build(a.verbose, a.force))
+    print(build(a.verbose, a.force, a.debug))
     return 0
 
 

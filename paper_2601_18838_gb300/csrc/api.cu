@@ -661,6 +661,14 @@ struct StepScope {
 kpme_status_t check_device_status(kpme_plan_t P) {
   // the status word lives in mapped pinned host memory: readable without a synchronisation
   volatile int* h = reinterpret_cast<volatile int*>(P->d_status);
+  if (h && *h >= kDevBounds) {
+    static const char* const names[NUM_SITES] = {"", "no-sort spreading", "tile spreading", "tile region merge",
+                                                 "gathering", "tile gathering", "cell count", "cell scatter"};
+    const int site = *h - kDevBounds;
+    *h = DEV_OK;
+    P->last_error = std::string("device index check failed: ") + (site > 0 && site < NUM_SITES ? names[site] : "?");
+    return KPME_ERR_CUDA;
+  }
   if (h && *h != DEV_OK) {
     *h = DEV_OK;
     P->last_error = "a bounded device wait gave up";

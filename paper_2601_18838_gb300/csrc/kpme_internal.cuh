@@ -15,8 +15,30 @@
 
 namespace kpme {
 
-// Device status word values (written by bounded waits that give up).
+// Device status word values (written by bounded waits that give up, and by the index checks of
+// the checked build: kDevBounds + the first failing site).
 enum DeviceStatus : int { DEV_OK = 0, DEV_TIMEOUT = 1 };
+enum BoundsSite : int {
+  SITE_SPREAD_NOSORT = 1, SITE_SPREAD_TILE, SITE_TILE_MERGE, SITE_GATHER, SITE_GATHER_TILE, SITE_TILE_COUNT,
+  SITE_TILE_SCATTER, NUM_SITES
+};
+constexpr int kDevBounds = 16;
+
+// Checked build (compiled with -DKPME_DEBUG: `build(debug=True)`, libkpme_debug.so): the particle
+// and mesh kernels check every computed index against its buffer; a failed check records the
+// first failing site in the status word (the next call on the plan reports it) and the access
+// is skipped.  The release build compiles the checks away.
+__device__ __forceinline__ bool in_bounds(int* status, bool ok, int site) {
+#ifdef KPME_DEBUG
+  if (!ok && status) atomicCAS(status, 0, kDevBounds + site);
+  return ok;
+#else
+  (void)status;
+  (void)ok;
+  (void)site;
+  return true;
+#endif
+}
 
 // Bounded spin budget for every device-side wait (~1 s at 2 GHz).
 constexpr long long kWaitCycles = 2000000000LL;

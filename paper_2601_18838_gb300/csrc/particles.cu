@@ -12,7 +12,8 @@ constexpr int kThreads = 256;
 struct MeshGeom {
   double c0, c1, c2, L;
   int K;
-  df cd[3], rinv;   // the centre and 1/L as double-float pairs (mesh_coord_df)
+  df cd[3], rinv;         // the centre and 1/L as double-float pairs (mesh_coord_df)
+  int* status = nullptr;  // device status word (index checks of the checked build)
 };
 
 df split_host(double v) {
@@ -250,7 +251,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == sizeof(float) ? 2 : 1) 
         for (int j2 = 0; j2 < N; ++j2) {
           int k2 = g[2] - j2;
           k2 += (k2 < 0) ? K : 0;
-          const T v = row[k2];
+          const T v = in_bounds(G.status, k0 >= 0 && k0 < K && k1 >= 0 && k1 < K && k2 >= 0 && k2 < K, SITE_GATHER)
+                          ? row[k2]
+                          : T(0);
           t += w[2][j2] * v;
           td += dw[2][j2] * v;
         }
@@ -337,6 +340,7 @@ MeshGeom geom(kpme_plan_t P) {
   G.L = 2.0 * P->p.radius;
   G.K = P->p.K;
   set_df_fields(G);
+  G.status = P->d_status;
   return G;
 }
 
@@ -491,7 +495,8 @@ namespace kpme {
 namespace {
 
 struct Tiling {
-  int K, T, KT;   // mesh, tile edge (cells), tiles per axis
+  int K, T, KT;           // mesh, tile edge (cells), tiles per axis
+  int* status = nullptr;  // device status word (index checks of the checked build)
 };
 constexpr int kTileSub = kTileCounters;
 
@@ -521,7 +526,8 @@ __global__ void tile_count_kernel(MeshGeom G, Tiling tl, int64_t n, const double
     // 8 counters per tile (chosen by the particle index) cut the contention of the returned
     // atomics 8-fold; the sub-ranges of a tile are adjacent after the scan
     const int c = t * kTileSub + (int)(i & (kTileSub - 1));
-    tile_slot[i] = make_int2(c, atomicAdd(count + c, 1));
+    const bool ok = in_bounds(tl.status, t >= 0 && t < tl.KT * tl.KT * tl.KT, SITE_TILE_COUNT);
+    tile_slot[i] = make_int2(ok ? c : 0, ok ? atomicAdd(count + c, 1) : 0);
     const int gp = g[0] | (g[1] << 10) | (g[2] << 20);
     rec[2 * i] = make_float4(__int_as_float(gp), __int_as_float((int)i), fh[0], fl[0]);
     rec[2 * i + 1] = make_float4(fh[1], fl[1], fh[2], fl[2]);
@@ -593,10 +599,12 @@ __global__ void __launch_bounds__(1024) tile_scan_kernel(const int* __restrict__
 }
 
 __global__ void tile_scatter_kernel(int64_t n, const int2* __restrict__ tile_slot, const int* __restrict__ start,
-                                    const float4* __restrict__ rec_in, float4* __restrict__ rec_out) {
+                                    const float4* __restrict__ rec_in, float4* __restrict__ rec_out,
+                                    int* __restrict__ status) {
   for (int64_t i = blockIdx.x * (int64_t)kThreads + threadIdx.x; i < n; i += (int64_t)gridDim.x * kThreads) {
     const int2 ts = tile_slot[i];
     const int64_t d = start[ts.x] + ts.y;
+    if (!in_bounds(status, d >= 0 && d < n, SITE_TILE_SCATTER)) continue;
     rec_out[2 * d] = rec_in[2 * i];
     rec_out[2 * d + 1] = rec_in[2 * i + 1];
   }
@@ -740,7 +748,10 @@ __global__ void __launch_bounds__(kThreads) spread_tile_kernel(Tiling tl, const 
         const df c02 = df_mul(c2, w0[j0]);
         float* plane = col + (b0 - j0) * D * D;
 #pragma unroll
-        for (int j1 = 0; j1 < N; ++j1) atomicAdd(plane + (b1 - j1) * D, df_mul_rn(c02, w1[j1]));
+        for (int j1 = 0; j1 < N; ++j1)
+          if (in_bounds(tl.status, b0 - j0 >= 0 && b0 - j0 < D && b1 - j1 >= 0 && b1 - j1 < D && b2 - gl >= 0 &&
+                                       b2 - gl < D, SITE_SPREAD_TILE))
+            atomicAdd(plane + (b1 - j1) * D, df_mul_rn(c02, w1[j1]));
       }
     }
   }
@@ -757,7 +768,8 @@ __global__ void __launch_bounds__(kThreads) spread_tile_kernel(Tiling tl, const 
       if (v == 0.0f) continue;
       int k2 = lo2 + l2;
       k2 += k2 < 0 ? K : 0;
-      atomicAdd(dst + k2, v);
+      if (in_bounds(tl.status, k0 >= 0 && k0 < K && k1 >= 0 && k1 < K && k2 >= 0 && k2 < K, SITE_TILE_MERGE))
+        atomicAdd(dst + k2, v);
     }
   }
 }
@@ -795,7 +807,10 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
       for (int l2 = lane; l2 < D; l2 += 32) {
         int k2 = lo2 + l2;
         k2 += k2 < 0 ? K : 0;
-        region[row * D + l2] = src[k2];
+        region[row * D + l2] =
+            in_bounds(tl.status, k0 >= 0 && k0 < K && k1 >= 0 && k1 < K && k2 >= 0 && k2 < K, SITE_GATHER_TILE)
+                ? src[k2]
+                : 0.0f;
       }
     }
   }
@@ -828,7 +843,10 @@ __global__ void __launch_bounds__(kThreads) gather_tile_kernel(MeshGeom G, Tilin
         float s_p = 0.f, s_1 = 0.f;
 #pragma unroll
         for (int j1 = 0; j1 < N; ++j1) {
-          const float v = plane[(b1 - j1) * D];
+          const float v = in_bounds(tl.status, b0 - j0 >= 0 && b0 - j0 < D && b1 - j1 >= 0 && b1 - j1 < D &&
+                                                   b2 >= 0 && b2 < D, SITE_GATHER_TILE)
+                              ? plane[(b1 - j1) * D]
+                              : 0.0f;
           s_p = fmaf(w[1][j1], v, s_p);
           s_1 = fmaf(dw[1][j1], v, s_1);
         }
@@ -925,7 +943,8 @@ __global__ void __launch_bounds__(kThreads) spread_nosort_kernel(MeshGeom G, int
         for (int j1 = 0; j1 < N; ++j1) {
           int k1 = g[1] - j1;
           k1 += k1 < 0 ? K : 0;
-          atomicAdd(plane + (int64_t)k1 * K, df_mul_rn(c02, w1[j1]));
+          if (in_bounds(G.status, k0 >= 0 && k0 < K && k1 >= 0 && k1 < K && k2 >= 0 && k2 < K, SITE_SPREAD_NOSORT))
+            atomicAdd(plane + (int64_t)k1 * K, df_mul_rn(c02, w1[j1]));
         }
       }
     }
@@ -1204,6 +1223,7 @@ Tiling tiling_of(kpme_plan_t P) {
   t.K = P->p.K;
   t.T = P->tile;
   t.KT = P->p.K / P->tile;
+  t.status = P->d_status;
   return t;
 }
 
@@ -1226,7 +1246,8 @@ cudaError_t launch_sort(kpme_plan_t P, int64_t n, const double* x, const double*
   tile_count_kernel<<<grid, kThreads, 0, P->stream>>>(geom(P), tl, n, x, q, P->d_tcount, P->d_tslot, P->d_rec_in,
                                                       sumq);
   tile_scan_kernel<<<1, 1024, 0, P->stream>>>(P->d_tcount, nt, P->d_tstart);
-  tile_scatter_kernel<<<grid, kThreads, 0, P->stream>>>(n, P->d_tslot, P->d_tstart, P->d_rec_in, P->d_rec);
+  tile_scatter_kernel<<<grid, kThreads, 0, P->stream>>>(n, P->d_tslot, P->d_tstart, P->d_rec_in, P->d_rec,
+                                                        P->d_status);
   return cudaGetLastError();
 }
 
@@ -1350,7 +1371,9 @@ cudaError_t launch_lagrange_sort(kpme_plan_t P, int64_t n, const double* x, doub
                                                               rec_in);
   }
   tile_scan_kernel<<<1, 1024, 0, P->stream>>>(P->d_tcount, (int)ncnt, P->d_tstart);
-  if (n > 0) tile_scatter_kernel<<<grid, kThreads, 0, P->stream>>>(n, P->d_tslot, P->d_tstart, P->d_rec_in, P->d_rec);
+  if (n > 0)
+    tile_scatter_kernel<<<grid, kThreads, 0, P->stream>>>(n, P->d_tslot, P->d_tstart, P->d_rec_in, P->d_rec,
+                                                          P->d_status);
   return cudaGetLastError();
 }
 
