@@ -278,8 +278,8 @@ kpme_status_t kpme::set_tile(kpme_plan_t P, int T) {
   return KPME_OK;
 }
 
-// Cell-sorted, tile-staged spreading and gathering (sorted) or float64 atomics on the mesh
-// and untiled gathering with no sort (faster for few particles per mesh point).
+// Cell-sorted, tile-staged spreading and gathering (sorted) or float32 atomics on the mesh and
+// untiled gathering with no sort (the autotuner's choice on every workload measured here).
 kpme_status_t kpme::set_sorted(kpme_plan_t P, bool sorted) {
   if (sorted && P->tile <= 0) return KPME_ERR_INVALID_ARG;
   if (P->no_sort != !sorted) {
@@ -912,7 +912,7 @@ bool lagrange(kpme_plan_t P) {
 bool lagrange_modes(kpme_plan_t P) { return P->p.interp == KPME_INTERP_LAGRANGE_MODES; }
 
 // Charge mesh of n particles: cell sort + tile-staged float32 spreading, float32 spreading
-// with no sort (lane groups, float32 atomics), or float64 atomics for the FP64 form.
+// with no sort (lane passes, float32 atomics), or float64 atomics for the FP64 form.
 // also_zero (may be NULL): a float64 accumulator of the caller cleared in the same launch.
 kpme_status_t spread_mesh(kpme_plan_t P, int64_t n, const double* x, const double* q, MeshRef& out,
                           double* also_zero = nullptr) {

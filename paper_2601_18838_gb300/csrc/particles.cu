@@ -643,7 +643,8 @@ struct SpreadPass {
   static constexpr int ROUNDS = (PP + PW - 1) / PW;
 };
 
-// Lanes per particle: one lane per j0 plane of the n^3 stencil (4 for order 4, 8 for 6 / 8).
+// Lanes per particle of the tile gathering: one lane per mesh column j2 of the n^3 stencil (4 for
+// order 4, 8 for 6 / 8; lanes j2 >= n only join the reductions).
 template <int N>
 struct Lanes {
   static constexpr int value = N <= 4 ? 4 : 8;
