@@ -1344,8 +1344,12 @@ kpme_status_t kpme_load_skp(kpme_plan_t P, const char* path) {
          fread(g1.data(), sizeof(double), g1.size(), f) == g1.size();
     int64_t sum = 0;
     for (int32_t v : r1) sum += v;
+    bool finite = std::isfinite(geo[3]);
+    for (const auto* g : {&g3, &g2, &g1})
+      for (double v : *g) finite = finite && std::isfinite(v);
     if (!ok) why = "file is short";
     else if (sum != hdr[3]) why = "inner counts do not add up to R";
+    else if (!finite) why = "non-finite generator values";
   }
   fclose(f);
   if (!why.empty()) {
