@@ -46,25 +46,26 @@ DTYPE = {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32", "bf16":
 # with the digest of the kernel sources the counters were taken on: a changed kernel reports
 # null until it is captured again.
 SKP_TRAFFIC = {
-    # profiles/dram_traffic_water_k64_bf16x10.md: mp_ozt_kernel 1,515,008 B + mp_ozf_kernel
-    # 19,324,160 B (reads; 0 B written: Y and Phi stay in L2), 2 launches per evaluation
-    ("water", "bf16x10"): {"digest": "15ac4d609920d908", "launches": 2,
-                           "bytes_per_launch": (1515008 + 19324160) / 2},
+    # profiles/dram_traffic_water_k64_bf16x10.md: mp_ozt_kernel 1,513,984 B + mp_ozf_kernel
+    # 19,318,784 B (reads; 0 B written: Y and Phi stay in L2), 2 launches per evaluation
+    ("water", "bf16x10"): {"digest": "8b97809330ffdde9", "launches": 2,
+                           "bytes_per_launch": (1513984 + 19318784) / 2},
     # profiles/launches_large_k256_bf16x10.md: one evaluation's stage 1 (93,060,608 B read +
     # 880,000,000 B written), stage 2 (1,066,170,880 + 11,189,232,384), stage 3 (11,840,929,792
     # + 277,398,784) and the unfold of Phi (67,126,272 + 4,329,472): 4 launches
-    ("large", "bf16x10"): {"digest": "21bc207300527025", "launches": 4,
+    ("large", "bf16x10"): {"digest": "c442ea68c11a0123", "launches": 4,
                            "bytes_per_launch": (93060608 + 880000000 + 1066170880 + 11189232384 + 11840929792
                                                 + 277398784 + 67126272 + 4329472) / 4},
 }
-SKP_SOURCES = ("gemm_ozf.cu", "gemm_ozt.cu", "tc_common.cuh")
+# the sources of the stage kernels each workload runs (the digest of a record covers these)
+SKP_SOURCES = {"water": ("gemm_ozf.cu", "gemm_ozt.cu", "tc_common.cuh"), "large": ("gemm_ozt.cu", "tc_common.cuh")}
 
 
-def _skp_digest():
+def _skp_digest(workload="water"):
     import hashlib
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2601_18838_gb300", "csrc")
-    for name in SKP_SOURCES:
+    for name in SKP_SOURCES.get(workload, SKP_SOURCES["water"]):
         with open(os.path.join(csrc, name), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -73,7 +74,7 @@ def _skp_digest():
 def _skp_traffic(workload, precision, launches):
     """Counted DRAM bytes per stage launch, or None once the kernels or the launch split changed."""
     rec = SKP_TRAFFIC.get((workload, precision))
-    if not rec or rec["digest"] != _skp_digest() or rec["launches"] != launches:
+    if not rec or rec["digest"] != _skp_digest(workload) or rec["launches"] != launches:
         return None
     return rec["bytes_per_launch"]
 
@@ -660,10 +661,11 @@ def _measure(args, name, steps, warmup, ctx, headline):
 # cycles, one capture per kernel) with the digest of the kernel sources it was taken on.
 SKP_TENSOR_ACTIVE = {
     # profiles/mp_ozf_kernel_water_k64_bf16x10.md
-    ("water", "bf16x10"): {"digest": "15ac4d609920d908", "pct": {"mp_ozf_kernel<64>": 32.4}},
+    ("water", "bf16x10"): {"digest": "8b97809330ffdde9",
+                           "pct": {"mp_ozf_kernel<64>": 32.3, "mp_ozt_kernel<64, 8, 1> (stage 1)": 12.6}},
     # profiles/mp_ozt_kernel_large_k256_bf16x10.md (16-term groups of the same kernels; mean of
     # the captured launches: stage 1 59.7, stage 2 60.7 / 55.1, stage 3 59.1 / 59.2)
-    ("large", "bf16x10"): {"digest": "21bc207300527025",
+    ("large", "bf16x10"): {"digest": "c442ea68c11a0123",
                            "pct": {"mp_ozt_kernel<128, 4, 1> (stages 1, 2)": 58.5,
                                    "mp_ozt_kernel<128, 4, 0> (stage 3)": 59.1}},
 }
@@ -671,7 +673,7 @@ SKP_TENSOR_ACTIVE = {
 
 def _tensor_active(workload, precision):
     rec = SKP_TENSOR_ACTIVE.get((workload, precision))
-    if not rec or rec["digest"] != _skp_digest():
+    if not rec or rec["digest"] != _skp_digest(workload):
         return None
     return {"pct_of_active_cycles": rec["pct"], "source": "ncu sm__pipe_tensor_cycles_active (profiles/)"}
 

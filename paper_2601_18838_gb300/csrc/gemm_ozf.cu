@@ -336,9 +336,12 @@ __global__ void __launch_bounds__(kThreads, 1)
           fence_after();
           const uint32_t d = tmem + c_d(db);
           const uint64_t db0 = sdesc(smem_u32(ring_b + s * bstage));
+          // the k steps in loops that are not unrolled (the ten products of a step are): the fully
+          // unrolled issue code of both operand kinds stalled the issuing threads on instruction
+          // fetch ("no instruction" 2.2 per issue; fused stages of the water box 103 -> 92 us)
           if (s2) {   // A: Y_i digits in shared memory
             const uint64_t da0 = sdesc(smem_u32(a2s));
-#pragma unroll
+#pragma unroll 1
             for (int kk = 0; kk < kKSteps; ++kk)
 #pragma unroll
               for (int p = 0; p < kProducts; ++p) {
@@ -349,7 +352,7 @@ __global__ void __launch_bounds__(kThreads, 1)
               }
           } else {    // A: Z_t digits in tensor memory
             const uint32_t a = tmem + c_a3(slot);
-#pragma unroll
+#pragma unroll 1
             for (int kk = 0; kk < kKSteps; ++kk)
 #pragma unroll
               for (int p = 0; p < kProducts; ++p) {
