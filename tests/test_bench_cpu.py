@@ -29,3 +29,18 @@ def test_every_bench_workload_is_defined():
         if name != "batched":   # a list of systems, built by the batched runner
             s = workloads.by_name(name)
             assert s.n > 0 and s.K > 0
+
+
+def test_measured_records_follow_their_kernels():
+    """The DRAM-traffic and tensor-activity records of bench.py carry the digest of the kernel
+    sources they were measured on: a record reports only while its own workload's kernels are
+    unchanged and its launch split matches, and the 10^6-charge box's digest does not cover the
+    fused kernel it never runs."""
+    sys.path.insert(0, ROOT)
+    import bench
+    assert "gemm_ozf.cu" not in bench.SKP_SOURCES["large"]
+    for (w, prec), rec in bench.SKP_TRAFFIC.items():
+        ok = rec["digest"] == bench._skp_digest(w)
+        assert (bench._skp_traffic(w, prec, rec["launches"]) is not None) == ok
+        assert bench._skp_traffic(w, prec, rec["launches"] + 1) is None
+    assert bench._skp_traffic("large", "fp32", 4) is None
